@@ -1,0 +1,106 @@
+"""Pins for the oracle's velocity Verlet + SHAKE/RATTLE dynamics and parareal (Secs. 2 and 4).
+
+  * velocity Verlet is time reversible: N steps forward, velocities negated,
+    N steps back returns to the start;
+  * its energy error is second order: halving dt cuts the total-energy
+    fluctuation about four-fold;
+  * rigid bonds stay at their lengths and bond-relative velocities vanish;
+  * parareal: zero iterations is the sequential G sweep; after k iterations the
+    first k+1 slice ends equal the serial fine trajectory bitwise; with G = F
+    one iteration reproduces the serial trajectory to rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_1889_gb300 import inputs
+
+FINE = dict(a=1.2, h=0.25, levels=2)
+
+
+@pytest.fixture(scope="module")
+def small_water():
+    return inputs.water_box(24, 0.9, margin=0.5, seed=3, vel_seed=4)
+
+
+def _bonds(x, n_mol):
+    m = x[: 3 * n_mol].reshape(n_mol, 3, 3)
+    return (np.linalg.norm(m[:, 0] - m[:, 1], axis=1), np.linalg.norm(m[:, 0] - m[:, 2], axis=1),
+            np.linalg.norm(m[:, 1] - m[:, 2], axis=1))
+
+
+def test_rigid_geometry_is_kept(small_water):
+    s = small_water
+    x, v, uk = oracle.md_run(s, dt=0.002, n_steps=10, **FINE)
+    oh1, oh2, hh = _bonds(x, s.n_mol)
+    assert np.allclose(oh1, inputs.D_OH, rtol=1e-11) and np.allclose(oh2, inputs.D_OH, rtol=1e-11)
+    assert np.allclose(hh, inputs.d_hh(), rtol=1e-11)
+    m = x[: 3 * s.n_mol].reshape(s.n_mol, 3, 3); w = v[: 3 * s.n_mol].reshape(s.n_mol, 3, 3)
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        assert np.abs(((m[:, i] - m[:, j]) * (w[:, i] - w[:, j])).sum(-1)).max() < 1e-12
+    assert np.all(np.isfinite(uk))
+
+
+def test_velocity_verlet_is_time_reversible(small_water):
+    s = small_water
+    x1, v1, _ = oracle.md_run(s, dt=0.002, n_steps=15, **FINE)
+    x2, v2, _ = oracle.md_run(s, dt=0.002, n_steps=15, x=x1, v=-v1, **FINE)
+    assert np.abs(x2 - s.pos).max() < 1e-9
+    assert np.abs(-v2 - s.vel).max() < 1e-6
+
+
+def test_energy_error_is_second_order(small_water):
+    s = small_water
+    flucts = []
+    for dt, n in ((0.002, 10), (0.001, 20)):
+        _, _, uk = oracle.md_run(s, dt=dt, n_steps=n, **FINE)
+        e = uk.sum(1)
+        flucts.append(np.abs(e - e[0]).max())
+    assert flucts[1] < flucts[0] / 2.5
+
+
+def _run_serial(s, p, n_slices):
+    xs = [s.pos.copy()]; vs = [s.vel.copy()]
+    for _ in range(n_slices):
+        x, v, _ = oracle.md_run(s, a=p["a"], h=p["h"], levels=p["levels"], dt=p["dt"], n_steps=p["steps"],
+                                x=xs[-1], v=vs[-1])
+        xs.append(x); vs.append(v)
+    return np.array(xs), np.array(vs)
+
+
+@pytest.fixture(scope="module")
+def pr_setup():
+    s = inputs.water_box(15, 0.8, margin=0.5, seed=5, vel_seed=6)
+    F = dict(a=1.2, h=0.25, levels=2, dt=0.002, steps=4)
+    G = dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=2)
+    return s, F, G
+
+
+def test_parareal_zero_iterations_is_the_coarse_sweep(pr_setup):
+    s, F, G = pr_setup
+    xs, vs, it, dx, rc = oracle.parareal(s, G, F, n_slices=3, max_iter=0, tol=0.0)
+    gx, gv = _run_serial(s, G, 3)
+    assert it == 0
+    assert np.array_equal(xs, gx) and np.array_equal(vs, gv)
+
+
+def test_parareal_exact_slices_after_k_iterations(pr_setup):
+    s, F, G = pr_setup
+    n_slices = 4
+    fx, fv = _run_serial(s, F, n_slices)
+    for k in (1, 2):
+        xs, vs, it, dx, rc = oracle.parareal(s, G, F, n_slices=n_slices, max_iter=k, tol=0.0)
+        assert it == k
+        assert np.array_equal(xs[: k + 1], fx[: k + 1]) and np.array_equal(vs[: k + 1], fv[: k + 1])
+        if k < n_slices:
+            assert not np.array_equal(xs[-1], fx[-1])
+    xs, vs, it, dx, rc = oracle.parareal(s, G, F, n_slices=n_slices, max_iter=n_slices, tol=0.0)
+    assert np.array_equal(xs, fx) and np.array_equal(vs, fv)
+
+
+def test_parareal_with_fine_as_coarse_converges_in_one_iteration(pr_setup):
+    s, F, _ = pr_setup
+    fx, fv = _run_serial(s, F, 3)
+    xs, vs, it, dx, rc = oracle.parareal(s, F, F, n_slices=3, max_iter=2, tol=1e-12)
+    assert np.abs(xs - fx).max() < 1e-12
+    assert it <= 2 and rc == 0
