@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput of the MSM velocity-Verlet step on GB300.
+
+One step = one velocity-Verlet step of the rigid-water workload through the
+whole hot path: bit-exact binning and sort, short-range g* sum (+ O-O LJ of the
+water completion), anterpolation, restriction and lattice cutoff on every
+level, FP64 top level, prolongation, interpolation, exclusions, FP64 energy
+reductions, half kicks and SHAKE/RATTLE.
+
+Workload: 1,000,000 atoms (333,333 rigid 3-site water-like molecules + 1
+filler site) in a 21.5 nm cube (+1 nm margin), a = 1.2 nm, h = 0.25 nm, 5
+levels, dt = 2 fs, NVE.  Inputs are resident in HBM when the timed region
+starts; the working set (~0.3 GB) is larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica
+of the workload (the path does not shard; "replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MSM atom-steps/s @1M atoms, FP32 batched vs plain FP64 GPU at force err ≤1e-4"
+UNIT = "atom-steps/s"
+A, H, DT = 1.2, 0.25, 0.002
+FLOPS_PER_PAIR = 29          # algorithmic FP32 flops per ordered in-cutoff pair (FMA = 2)
+FP32_LANES_PER_SM = 128
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="water1M")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--no-oracle", action="store_true", help="skip the oracle force error and CPU baseline")
+    return p.parse_args()
+
+
+def workload_config(name):
+    from paper_1309_1889_gb300 import inputs
+    cfg = dict(inputs.WORKLOADS[name])
+    region = cfg["region"]
+    return cfg, {
+        "workload": f"{name}: {cfg['n_atoms']:,} atoms of rigid 3-site water-like molecules "
+                    f"(O -0.834 e, H +0.417 e) in a {region} nm box + 1 nm margin, open boundaries",
+        "a_nm": A, "h_nm": H, "levels": cfg["levels"], "dt_ps": DT, "ensemble": "NVE",
+        "precision": "FP32 pair/grid/stencil arithmetic, FP64 state, top level and reductions",
+        "l2": "no flush: working set (~0.3 GB) larger than the 129 MB L2",
+        "parallelism": "replicas",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd += ["--id=" + bus_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in Path(self.f.name).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append(dict(t=ts, sm=float(parts[2]), smax=float(parts[3]),
+                                 reasons={"hw_slowdown": parts[6], "hw_thermal_slowdown": parts[7],
+                                          "sw_thermal_slowdown": parts[8], "sw_power_cap": parts[9]}))
+            except (ValueError, IndexError):
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 1.0 <= r["t"] <= self.t1 + 1.0] or rows
+        reasons = sorted({k for r in inside for k, v in r["reasons"].items() if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r["sm"] for r in inside), "sm_max_mhz": max(r["smax"] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {}
+
+
+def short_range_traffic(n_launch_atoms):
+    """Per-launch DRAM traffic of the short-range kernel from the committed ncu summary,
+    or None if the kernel source changed since the counters were taken."""
+    f = ROOT / "profiles" / "short_range_water1M_traffic.json"
+    if not f.exists():
+        return None
+    rec = json.loads(f.read_text())
+    src = ROOT / "paper_1309_1889_gb300" / "csrc" / "k_short.cu"
+    if hashlib.sha256(src.read_bytes()).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_per_atom"] * n_launch_atoms
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dev_system(torch, s, dev):
+    from paper_1309_1889_gb300 import inputs
+    t = lambda x: torch.tensor(np.asarray(x), dtype=torch.float64, device=dev)
+    return inputs.System(pos=t(s.pos), q=t(s.q), mass=t(s.mass), box=s.box, vel=t(s.vel), n_mol=s.n_mol,
+                         lj=torch.tensor(s.lj, device=dev))
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1309_1889_gb300 import api, inputs
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, config = workload_config(a.workload)
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=1.0, seed=0, vel_seed=1)
+    n = s.n
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- FP32 path: the timed run
+    m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water")
+    d = dev_system(torch, s, dev)
+    m32.md_run(d, DT, a.warmup, record=False)
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id if hasattr(torch.cuda.get_device_properties(dev), "pci_bus_id") else None
+    except Exception:
+        bus = None
+    clocks = ClockSampler(bus) if rank == 0 else None
+    time.sleep(0.5 if clocks else 0)
+    m32.profile(True)
+    m32.profile_read(reset=True)
+    l0 = api.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark_start()
+    ev0.record(stream)
+    uk = m32.md_run(d, DT, a.steps, record=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    if clocks:
+        clocks.mark_end()
+    launches = api.kernel_launches() - l0
+    t_ms = ev0.elapsed_time(ev1)
+    m32.profile(False)
+    prof = m32.profile_read(reset=True)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    clk = clocks.stop() if clocks else None
+    uk = uk.cpu().numpy()
+    etot = uk.sum(1)
+    pairs = m32.count_pairs()
+
+    value = n * a.steps * world / (t_ms / 1e3)
+
+    # ---- FP64 path on the same start state
+    m64 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp64", model="water")
+    d64 = dev_system(torch, s, dev)
+    m64.md_run(d64, DT, 1, record=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m64.md_run(d64, DT, a.fp64_steps, record=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+    value64 = n * a.fp64_steps / (t64 / 1e3)
+
+    # ---- forces at t = 0: FP32 and FP64 GPU paths against the FP64 oracle
+    d0 = dev_system(torch, s, dev)
+    _, f32, _ = m32.system_forces(d0)
+    _, f64, _ = m64.system_forces(d0)
+    f32 = f32.cpu().numpy(); f64 = f64.cpu().numpy()
+    err = {"fp32_vs_fp64_gpu": float(np.sqrt(((f32 - f64) ** 2).sum() / (f64 ** 2).sum()))}
+    cpu_baseline = None
+    if rank == 0 and not a.no_oracle:
+        import oracle
+        oracle.build()
+        t = time.perf_counter()
+        ref = oracle.model_forces(s, A, H, cfg["levels"])
+        t_cpu = time.perf_counter() - t
+        fo = ref["forces"]
+        den = np.sqrt((fo ** 2).sum())
+        err["fp32_vs_oracle"] = float(np.sqrt(((f32 - fo) ** 2).sum()) / den)
+        err["fp64_vs_oracle"] = float(np.sqrt(((f64 - fo) ** 2).sum()) / den)
+        cpu_baseline = {"value": n / t_cpu, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                        "sample": f"one oracle force evaluation (MSM + water completion, FP64, plain C) of the "
+                                  f"full {n:,}-atom box at t = 0 ({t_cpu:.1f} s); a step is this evaluation plus "
+                                  f"O(N) integrator work"}
+
+    # ---- end to end: public API with pinned host buffers, forces carried between calls
+    hx = torch.tensor(s.pos).pin_memory().numpy()
+    hv = torch.tensor(s.vel).pin_memory().numpy()
+    hf = torch.zeros((n, 3), dtype=torch.float64).pin_memory().numpy()
+    hq = torch.tensor(s.q).pin_memory().numpy()
+    hm = torch.tensor(s.mass).pin_memory().numpy()
+    hl = torch.tensor(s.lj).pin_memory().numpy()
+    hs = inputs.System(pos=hx, q=hq, mass=hm, box=s.box, vel=hv, n_mol=s.n_mol, lj=hl)
+    hs.force = hf
+    m32.md_run(hs, DT, 1, record=True)            # warm: forces of the start state
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        m32.md_run(hs, DT, 1, record=True)
+    t_e2e = time.perf_counter() - t
+    e2e = {"value": n * a.e2e_steps * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes + hf.nbytes + hq.nbytes + hm.nbytes + hl.nbytes),
+           "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes + hf.nbytes + 2 * 2 * 8)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (short range): FP32 ALU bound
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sr_ms, sr_n = prof["short_range"]
+    sr_avg_s = sr_ms / sr_n / 1e3
+    achieved = pairs * FLOPS_PER_PAIR / sr_avg_s / 1e12
+    traffic = short_range_traffic(n)
+    stage_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]}
+    step_share = {k: round(v[0] / t_ms, 4) for k, v in prof.items() if v[1]}
+    drift = float(etot[-1] - etot[0])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "k_short (short-range g* sum)",
+                     "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                    "(max SM clock from MEASURED_PEAKS.json)",
+                     "work": f"{pairs} ordered pairs within a per launch x {FLOPS_PER_PAIR} flops"},
+        "cpu_baseline": cpu_baseline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fp64_gpu": {"value": value64, "unit": UNIT, "steps": a.fp64_steps, "ms_per_step": t64 / a.fp64_steps,
+                     "fp32_speedup": value / world / value64},
+        "force_error": err,
+        "nve": {"steps": a.steps, "energy_drift_kj_mol": drift,
+                "max_abs_dev_kj_mol": float(np.abs(etot - etot[0]).max()), "kinetic_kj_mol": float(uk[-1, 1])},
+        "stage_ms_per_launch": stage_ms,
+        "stage_share_of_step": step_share,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(a):
+    """The FP64 CPU oracle, as it stands, timed on this machine's host cores."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1309_1889_gb300 import inputs
+
+    oracle.build()
+    cfg, config = workload_config(a.workload)
+    # Each step is a bounded sample of the workload: one oracle force evaluation of a smaller
+    # box of the same density and parameters (the cost per atom does not depend on the size).
+    budget_s = 150.0
+    n_s = 20_000
+    L = cfg["region"] if np.isscalar(cfg["region"]) else float(np.prod(cfg["region"])) ** (1 / 3)
+    dens = cfg["n_atoms"] / (L ** 3)
+
+    def make(n):
+        return inputs.water_box(n, (n / dens) ** (1 / 3), margin=1.0, seed=0, vel_seed=1)
+
+    s = make(n_s)
+    t = time.perf_counter()
+    oracle.model_forces(s, A, H, cfg["levels"])
+    t1 = time.perf_counter() - t
+    steps = a.steps + a.warmup
+    if t1 * steps > budget_s:
+        n_s = max(3000, int(n_s * budget_s / (t1 * steps)))
+        s = make(n_s)
+    for _ in range(a.warmup):
+        oracle.model_forces(s, A, H, cfg["levels"])
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.model_forces(s, A, H, cfg["levels"])
+    dt = time.perf_counter() - t
+    value = s.n * a.steps / dt
+    sample = (f"one oracle force evaluation per step (MSM + water completion, FP64, plain C) of a "
+              f"{s.n:,}-atom box of the workload's density and parameters")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

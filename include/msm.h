@@ -1,0 +1,212 @@
+/*
+ * msm.h -- C ABI of libmsm_gb300.so: the multilevel summation method (MSM)
+ * for Coulomb energies and forces, velocity Verlet dynamics around it and the
+ * parareal time-parallel driver, as hand-written sm_103a CUDA kernels.
+ *
+ * Source of the method: J. Pazurikova and L. Matyska, "Parallel-in-time
+ * method for calculation of long-range electrostatic interactions"
+ * (arXiv:1309.1889).  Sec. 2 states the problem (inputs q_i, r_i, v_i;
+ * outputs trajectories, forces, energy), Sec. 3 the MSM, Sec. 4 parareal.
+ *
+ * Conventions shared by every entry point
+ *   - Units: nm, ps, e, amu, kJ/mol; k_e = 1/(4 pi eps0) = 138.935458 kJ mol^-1 nm e^-2.
+ *   - Arrays are plain C-contiguous FP64 (atoms x 3 for vectors).  Array
+ *     arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library detects which and stages host data through its
+ *     own device buffers.  The caller keeps ownership of every array; the
+ *     library only borrows it for the duration of the call.
+ *   - box[6] = {x0, y0, z0, Lx, Ly, Lz} (host memory): the open,
+ *     non-periodic domain of the grids.  An atom is inside when, on every
+ *     axis, t = (x - x0) * (1/h) (IEEE FP64, 1/h rounded once) satisfies
+ *     0 <= t < floor(L/h) + 1, i.e. [x0, x0 + L) rounded up to whole cells of
+ *     the finest spacing h; any other atom makes the call fail with MSM_ERANGE.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Every entry
+ *     point returns after its results are complete and readable: it
+ *     synchronises the stream once at the end to read the device status word.
+ *   - Return 0 on success, a negative MSM_E* code on failure;
+ *     msm_last_error() gives a message for the calling thread.  No error
+ *     leaves a kernel running; no kernel traps.
+ */
+#ifndef MSM_GB300_H
+#define MSM_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSM_API __attribute__((visibility("default")))
+#else
+#define MSM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSM_OK        0
+#define MSM_EINVAL   -1   /* bad parameters, n < 0, NaN/Inf coordinates        */
+#define MSM_ERANGE   -2   /* an atom outside box (detected on the device)      */
+#define MSM_ENOMEM   -3   /* device allocation failed                          */
+#define MSM_ECUDA    -4   /* a CUDA runtime call failed                        */
+#define MSM_ETIMEOUT -5   /* a bounded device-side wait ran out                */
+#define MSM_ENOCONV  -6   /* SHAKE/RATTLE or parareal did not converge         */
+
+#define MSM_FP64 0        /* every stage in FP64                               */
+#define MSM_FP32 1        /* FP32 pair/grid/stencil arithmetic; FP64 state,
+                             energy/virial reductions and top level            */
+
+#define MSM_MODEL_CHARGES 0  /* bare point charges: the paper's Coulomb sum     */
+#define MSM_MODEL_WATER   1  /* + rigid 3-site water completion (see msm_system) */
+
+/* Method parameters (Sec. 3).
+ *   a          cutoff of the short-range part g* (nm); the level-k lattice
+ *              cutoff is 2^{k+1} a (eq. split and the g^k definitions)
+ *   h          finest grid spacing (nm); level k has spacing 2^k h
+ *   n_levels   number of grids l (levels 0..l-1); level l-1 is summed densely
+ *   precision  MSM_FP64 or MSM_FP32
+ *   coulomb_k  k_e (0 selects 138.935458)
+ *   gamma_kind 0 = C^2 Taylor smoothing (the only one the paper writes out)
+ *   basis_kind 0 = cubic C1 numerical Hermite Phi (the paper's p = 3 choice)
+ *   model      MSM_MODEL_CHARGES or MSM_MODEL_WATER
+ *   lj_sigma, lj_epsilon   O-O Lennard-Jones of the water completion
+ *   d_oh, d_hh rigid O-H and H-H distances of the water completion (nm)  */
+typedef struct msm_params {
+    double  a;
+    double  h;
+    int32_t n_levels;
+    int32_t precision;
+    double  coulomb_k;
+    int32_t gamma_kind;
+    int32_t basis_kind;
+    int32_t model;
+    int32_t reserved0;
+    double  lj_sigma;
+    double  lj_epsilon;
+    double  d_oh;
+    double  d_hh;
+} msm_params;
+
+/* An MD system in the library's layout.  Rigid water occupies the first
+ * 3*n_mol atoms as (O, H, H) triples; any further atoms are single sites.
+ * x, v are updated in place by md_run.  q, m are per-atom; lj (nullable)
+ * flags the Lennard-Jones sites (1) of the water completion.  If f is
+ * non-NULL, md_run starts from f/energy when f_valid is 1 (skipping the
+ * evaluation at the start positions) and leaves F, U of the final positions
+ * there with f_valid = 1, so a run split over several calls costs one
+ * evaluation per step. */
+typedef struct msm_system {
+    int64_t        n;
+    int64_t        n_mol;
+    double        *x;      /* n*3 */
+    double        *v;      /* n*3 */
+    const double  *q;      /* n   */
+    const double  *m;      /* n   */
+    const uint8_t *lj;     /* n, nullable */
+    double         box[6];
+    double        *f;      /* n*3, nullable: forces carried between md_run calls */
+    int32_t        f_valid;/* 1: f and energy hold F(x) and U(x) for the current x */
+    int32_t        reserved0;
+    double         energy; /* U(x) when f_valid (host field) */
+} msm_system;
+
+typedef struct msm_handle msm_handle;
+
+/* Fill *p with the defaults: a = 1.2, h = 0.25, 3 levels, FP32, k_e, C^2
+ * gamma, cubic Phi, point charges, TIP3P-like O-O LJ and geometry. */
+MSM_API void msm_default_params(msm_params *p);
+
+/* Create a handle (validates *p; allocates nothing on the device until the
+ * first evaluation).  The handle owns its scratch: sorted atoms, cell lists,
+ * grids for every level, stencil and top-level tables.  Not thread-safe:
+ * one handle per host thread / stream.  Errors: MSM_EINVAL. */
+MSM_API int  msm_create(const msm_params *p, msm_handle **out);
+MSM_API void msm_destroy(msm_handle *h);
+
+/* One MSM energy/force evaluation (Sec. 3, worked example steps 1-9):
+ * short range, anterpolation, restriction and lattice cutoff on levels
+ * 0..l-2, top level, prolongation, interpolation.
+ *   pos[n*3], q[n]       inputs (device or host)
+ *   energy[1]            U = 1/2 sum_i q_i phi_i (device or host, nullable)
+ *   forces[n*3]          F_i = -dU/dr_i (nullable)
+ *   potentials[n]        phi_i = dU/dq_i, self-interaction removed (nullable)
+ *   virial[1]            sum_i r_i . F_i (nullable)
+ * Errors: MSM_EINVAL (n < 0, non-finite coordinate), MSM_ERANGE (atom
+ * outside box), MSM_ENOMEM, MSM_ECUDA. */
+MSM_API int  msm_energy_forces(msm_handle *h, int64_t n, const double *pos, const double *q,
+                       const double box[6], double *energy, double *forces,
+                       double *potentials, double *virial, void *stream);
+
+/* Same evaluation for independent systems of uneven sizes in one call:
+ * system s owns atoms offsets[s] .. offsets[s+1]-1 (host array of n_sys+1)
+ * and box boxes[6*s .. 6*s+5] (host).  energies[n_sys]; other arrays are
+ * concatenated per atom.  Each system is evaluated exactly as by
+ * msm_energy_forces. */
+MSM_API int  msm_energy_forces_batched(msm_handle *h, int32_t n_sys, const int64_t *offsets,
+                               const double *pos, const double *q, const double *boxes,
+                               double *energies, double *forces, double *potentials,
+                               void *stream);
+
+/* Energy, forces and potentials of an msm_system under the handle's model
+ * (MSM plus, for MSM_MODEL_WATER, intramolecular exclusions and O-O LJ).
+ * Same outputs and errors as msm_energy_forces. */
+MSM_API int  msm_system_forces(msm_handle *h, const msm_system *sys, double *energy,
+                       double *forces, double *potentials, void *stream);
+
+/* Velocity Verlet (Sec. 2: forces F = -dU/dr, move the atoms), with
+ * SHAKE/RATTLE for the rigid triples: n_steps steps of length dt (ps) on
+ * sys->x, sys->v (device, updated in place).  uk (nullable, device or
+ * host) receives (U, K) before the first step and after every step:
+ * 2*(n_steps+1) values.  Errors as above plus MSM_ENOCONV (constraints). */
+MSM_API int  md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps, double *uk, void *stream);
+
+/* Parareal (Sec. 4): lambda^{k+1}_{n+1} = G(lambda^{k+1}_n) + F(lambda^k_n) - G(lambda^k_n),
+ * evaluated as F + (G_new - G_old) in FP64; F and G are md_run with their own
+ * parameters, time steps and step counts (dtG*stepsG must equal dtF*stepsF).
+ * state0 gives the system and lambda_0 = (x, v).  slices_x/slices_v
+ * (device or host, (n_slices+1)*n*3 each) receive lambda_0..lambda_{n_slices}
+ * of the last iterate.  Stops when max |x^{k+1} - x^k| <= tol (nm) or after
+ * max_iter iterations; *iters_done and *last_dx (host) report the outcome.
+ * Returns MSM_ENOCONV if tol was not met (results still written). */
+MSM_API int  parareal_run(const msm_params *G, double dtG, int32_t stepsG,
+                  const msm_params *F, double dtF, int32_t stepsF,
+                  const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
+                  double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx,
+                  void *stream);
+
+/* Inspection of the last evaluation on h (host outputs, synchronous).
+ * msm_grid_shape: level k's point counts (nx, ny, nz) and index origin
+ * (lo_x, lo_y, lo_z): grid point mu sits at x0 + mu * 2^k h.
+ * msm_stage_grid: which = 0 charges q^k, 1 lattice-cutoff potential
+ * u^{k,cut} (k < l-1), 2 potential u^k; out[nx*ny*nz] as FP64, x fastest.
+ * msm_cell_list: the bit-exact cell binning of the last evaluation: perm[n]
+ * (atoms ordered by finest-grid cell, then index) and cell_start[ncells+1],
+ * *ncells receiving the cell count (cells floor(L/h)+1 per axis, x fastest).
+ * msm_stage_atoms: which = 0 short-range potential sum_j q_j g*(r_ij) (n),
+ * 1 short-range force sum (n*3), both before k_e, in original atom order. */
+MSM_API int  msm_grid_shape(msm_handle *h, int32_t level, int64_t shape[3], int64_t lo[3]);
+MSM_API int  msm_stage_grid(msm_handle *h, int32_t level, int32_t which, double *out, int64_t count);
+MSM_API int  msm_cell_list(msm_handle *h, int64_t *perm, int64_t *cell_start, int64_t *ncells);
+MSM_API int  msm_stage_atoms(msm_handle *h, int32_t which, double *out, int64_t count);
+
+/* Per-stage timing with CUDA events recorded on the caller's stream around
+ * every stage of every evaluation and step while enabled (off by default).
+ * msm_profile_read copies up to max stages' accumulated milliseconds and
+ * launch counts (stage i is named by msm_stage_name(i)) and, if reset != 0,
+ * clears them.  Returns the number of stages. */
+MSM_API int  msm_profile_enable(msm_handle *h, int32_t on);
+MSM_API int  msm_profile_read(msm_handle *h, double *ms, int64_t *launches, int32_t max, int32_t reset);
+MSM_API const char *msm_stage_name(int32_t stage);
+
+/* Exact number of ordered pairs (i, j), j != i, with r_ij < a in the last
+ * evaluation on h: the algorithmic work unit of the short-range sum. */
+MSM_API int  msm_count_pairs(msm_handle *h, int64_t *ordered_pairs);
+
+/* Number of kernels this library launched since load (all handles). */
+MSM_API int64_t msm_kernel_launches(void);
+
+/* Message for the last error on the calling thread ("" if none). */
+MSM_API const char *msm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSM_GB300_H */

@@ -163,7 +163,8 @@ static int64_t gidx(const glevel *g, int64_t mx, int64_t my, int64_t mz)
 /* Binning (bit-exact contract for the cell lists)                           */
 /* ------------------------------------------------------------------------ */
 
-/* Finest-grid cell of every atom: t = (x - x0)/h (IEEE division), c = floor(t).
+/* Finest-grid cell of every atom: t = (x - x0) * (1/h) with 1/h rounded once
+ * to FP64 (IEEE subtract, IEEE multiply, no contraction), c = floor(t).
  * Valid atoms have t >= 0 and c <= floor(L/h) on every axis.
  * key = (cz * ny + cy) * nx + cx with n = floor(L/h) + 1 cells per axis.
  * perm = atoms ordered by (key, original index): a textbook stable counting
@@ -175,12 +176,13 @@ int orc_bin(int64_t n, const double *pos, const double *box, double h,
     int64_t nc[3];
     for (int d = 0; d < 3; d++) nc[d] = (int64_t)floor(box[3 + d] / h) + 1;
     int64_t ncells = nc[0] * nc[1] * nc[2];
+    double inv_h = 1.0 / h;
     for (int64_t i = 0; i < n; i++) {
         int64_t c[3];
         for (int d = 0; d < 3; d++) {
             double x = pos[3 * i + d];
             if (!isfinite(x)) return ORC_EINVAL;
-            double t = (x - box[d]) / h;
+            double t = (x - box[d]) * inv_h;
             if (!(t >= 0.0)) return ORC_ERANGE;
             double f = floor(t);
             if (f > (double)(nc[d] - 1)) return ORC_ERANGE;

@@ -1,0 +1,411 @@
+"""Thin ctypes binding of libmsm_gb300.so (C ABI in include/msm.h).
+
+Argument marshalling only: every step of the multilevel summation method,
+of velocity Verlet and of parareal runs in the library's CUDA kernels.  Torch
+tensors (CUDA, float64, contiguous) are passed as device pointers with the
+current torch stream; numpy arrays are passed as host pointers and the
+library stages them itself.  There is no CPU fallback: if the library is
+missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from pathlib import Path
+
+import numpy as np
+
+PKG = Path(__file__).resolve().parent
+LIB_PATH = PKG / "libmsm_gb300.so"
+
+KE = 138.935458
+FP64, FP32 = 0, 1
+MODEL_CHARGES, MODEL_WATER = 0, 1
+CODES = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOCONV"}
+
+
+class MSMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODES.get(code, code)}: {msg}")
+        self.code = code
+        self.name = CODES.get(code, str(code))
+
+
+class Params(C.Structure):
+    _fields_ = [("a", C.c_double), ("h", C.c_double), ("n_levels", C.c_int32), ("precision", C.c_int32),
+                ("coulomb_k", C.c_double), ("gamma_kind", C.c_int32), ("basis_kind", C.c_int32),
+                ("model", C.c_int32), ("reserved0", C.c_int32), ("lj_sigma", C.c_double),
+                ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double)]
+
+
+class SystemC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_mol", C.c_int64), ("x", C.c_void_p), ("v", C.c_void_p),
+                ("q", C.c_void_p), ("m", C.c_void_p), ("lj", C.c_void_p), ("box", C.c_double * 6),
+                ("f", C.c_void_p), ("f_valid", C.c_int32), ("reserved0", C.c_int32), ("energy", C.c_double)]
+
+
+_lib = None
+EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces", "msm_energy_forces_batched",
+           "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
+           "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
+           "msm_stage_name", "msm_count_pairs")
+
+
+def lib():
+    """Load libmsm_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH.name} is not built: run __graft_entry__.build() "
+                               "(or python -m paper_1309_1889_gb300.build)")
+        L = C.CDLL(str(LIB_PATH))
+        P, p, i32, i64, d = C.POINTER, C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.msm_default_params.argtypes = [P(Params)]; L.msm_default_params.restype = None
+        L.msm_create.argtypes = [P(Params), P(p)]; L.msm_create.restype = C.c_int
+        L.msm_destroy.argtypes = [p]; L.msm_destroy.restype = None
+        L.msm_energy_forces.argtypes = [p, i64, p, p, P(d), p, p, p, p, p]; L.msm_energy_forces.restype = C.c_int
+        L.msm_energy_forces_batched.argtypes = [p, i32, p, p, p, p, p, p, p, p]
+        L.msm_energy_forces_batched.restype = C.c_int
+        L.msm_system_forces.argtypes = [p, P(SystemC), p, p, p, p]; L.msm_system_forces.restype = C.c_int
+        L.md_run.argtypes = [p, P(SystemC), d, i32, p, p]; L.md_run.restype = C.c_int
+        L.parareal_run.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, d, p, p,
+                                   P(i32), P(d), p]
+        L.parareal_run.restype = C.c_int
+        L.msm_grid_shape.argtypes = [p, i32, p, p]; L.msm_grid_shape.restype = C.c_int
+        L.msm_stage_grid.argtypes = [p, i32, i32, p, i64]; L.msm_stage_grid.restype = C.c_int
+        L.msm_cell_list.argtypes = [p, p, p, p]; L.msm_cell_list.restype = C.c_int
+        L.msm_stage_atoms.argtypes = [p, i32, p, i64]; L.msm_stage_atoms.restype = C.c_int
+        L.msm_kernel_launches.argtypes = []; L.msm_kernel_launches.restype = C.c_int64
+        L.msm_profile_enable.argtypes = [p, i32]; L.msm_profile_enable.restype = C.c_int
+        L.msm_profile_read.argtypes = [p, p, p, i32, i32]; L.msm_profile_read.restype = C.c_int
+        L.msm_stage_name.argtypes = [i32]; L.msm_stage_name.restype = C.c_char_p
+        L.msm_count_pairs.argtypes = [p, P(i64)]; L.msm_count_pairs.restype = C.c_int
+        L.msm_last_error.argtypes = []; L.msm_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MSMError(rc, lib().msm_last_error().decode())
+
+
+def kernel_launches() -> int:
+    return int(lib().msm_kernel_launches())
+
+
+# --------------------------------------------------------------- marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(x) -> bool:
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _ptr(x):
+    """Device pointer of a CUDA tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if x.is_cuda:
+            if not x.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+            return C.c_void_p(x.data_ptr())
+        x = x.numpy()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def _box(box):
+    b = np.asarray(box, dtype=np.float64).reshape(6)
+    return (C.c_double * 6)(*b.tolist())
+
+
+def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
+                lj_epsilon=0.6364, d_oh=0.09572, d_hh=None) -> Params:
+    p = Params()
+    p.a, p.h, p.n_levels = float(a), float(h), int(levels)
+    p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
+    p.coulomb_k = float(ke)
+    p.gamma_kind = p.basis_kind = 0
+    p.model = {"charges": MODEL_CHARGES, "water": MODEL_WATER, 0: 0, 1: 1}[model]
+    p.lj_sigma, p.lj_epsilon = float(lj_sigma), float(lj_epsilon)
+    p.d_oh = float(d_oh)
+    p.d_hh = float(d_hh) if d_hh is not None else 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
+    return p
+
+
+class MSM:
+    """A handle: method parameters plus the device scratch of one evaluation stream."""
+
+    def __init__(self, a=1.2, h=0.25, levels=3, precision="fp32", model="charges", **kw):
+        self.params = make_params(a, h, levels, precision, model, **kw)
+        self._h = C.c_void_p()
+        _check(lib().msm_create(C.byref(self.params), C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().msm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- evaluation -----------------------------------------------------------
+    def energy_forces(self, pos, q, box, *, forces=True, potentials=True, virial=False, stream=None):
+        """U, F (n, 3), phi (n,), [virial] for point charges.
+
+        CUDA tensors in -> CUDA tensors out (no host synchronisation beyond the
+        library's status check); numpy in -> numpy out.
+        """
+        n = int(pos.shape[0])
+        dev = _is_tensor(pos) and pos.is_cuda
+        if dev:
+            torch = _torch()
+            out_f = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if forces else None
+            out_p = torch.empty((n,), dtype=torch.float64, device=pos.device) if potentials else None
+            e = torch.empty(2, dtype=torch.float64, device=pos.device)
+            _check(lib().msm_energy_forces(self._h, n, _ptr(pos), _ptr(q), _box(box), _ptr(e), _ptr(out_f),
+                                           _ptr(out_p), C.c_void_p(e.data_ptr() + 8) if virial else None,
+                                           _stream(stream)))
+            res = (e[0], out_f, out_p)
+            return res + (e[1],) if virial else res
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out_f = np.empty((n, 3)) if forces else None
+        out_p = np.empty(n) if potentials else None
+        e = np.zeros(2)
+        _check(lib().msm_energy_forces(self._h, n, _ptr(pos), _ptr(q), _box(box), _ptr(e[0:1]), _ptr(out_f),
+                                       _ptr(out_p), e[1:2].ctypes.data_as(C.c_void_p) if virial else None,
+                                       _stream(stream)))
+        res = (float(e[0]), out_f, out_p)
+        return res + (float(e[1]),) if virial else res
+
+    def energy_forces_batched(self, offsets, pos, q, boxes, stream=None):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        boxes = np.ascontiguousarray(boxes, dtype=np.float64)
+        n_sys = len(offsets) - 1
+        n = int(offsets[-1])
+        dev = _is_tensor(pos) and pos.is_cuda
+        if dev:
+            torch = _torch()
+            e = torch.empty(n_sys, dtype=torch.float64, device=pos.device)
+            f = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+            p = torch.empty(n, dtype=torch.float64, device=pos.device)
+        else:
+            pos = np.ascontiguousarray(pos, dtype=np.float64); q = np.ascontiguousarray(q, dtype=np.float64)
+            e = np.empty(n_sys); f = np.empty((n, 3)); p = np.empty(n)
+        _check(lib().msm_energy_forces_batched(self._h, n_sys, _ptr(offsets), _ptr(pos), _ptr(q), _ptr(boxes),
+                                               _ptr(e), _ptr(f), _ptr(p), _stream(stream)))
+        return e, f, p
+
+    def system_forces(self, sys, stream=None):
+        """U, F, phi of a System-like object (water model if the handle has it)."""
+        s, keep = _system_struct(sys)
+        n = int(s.n)
+        dev = _is_tensor(sys.pos) and sys.pos.is_cuda
+        if dev:
+            torch = _torch()
+            e = torch.empty(1, dtype=torch.float64, device=sys.pos.device)
+            f = torch.empty((n, 3), dtype=torch.float64, device=sys.pos.device)
+            p = torch.empty(n, dtype=torch.float64, device=sys.pos.device)
+            _check(lib().msm_system_forces(self._h, C.byref(s), _ptr(e), _ptr(f), _ptr(p), _stream(stream)))
+            return e[0], f, p
+        e = np.zeros(1); f = np.empty((n, 3)); p = np.empty(n)
+        _check(lib().msm_system_forces(self._h, C.byref(s), _ptr(e), _ptr(f), _ptr(p), _stream(stream)))
+        return float(e[0]), f, p
+
+    def md_run(self, sys, dt, n_steps, record=True, stream=None):
+        """Advance sys.pos / sys.vel in place; returns (U, K) per step (n_steps+1, 2) or None."""
+        s, keep = _system_struct(sys, need_v=True)
+        dev = _is_tensor(sys.pos) and sys.pos.is_cuda
+        uk = None
+        if record:
+            if dev:
+                uk = _torch().empty((n_steps + 1, 2), dtype=_torch().float64, device=sys.pos.device)
+            else:
+                uk = np.zeros((n_steps + 1, 2))
+        _check(lib().md_run(self._h, C.byref(s), float(dt), int(n_steps), _ptr(uk), _stream(stream)))
+        if s.f:
+            sys.force_valid = int(s.f_valid)
+            sys.energy = float(s.energy)
+        return uk
+
+    # -- profiling ------------------------------------------------------------
+    def profile(self, on=True):
+        _check(lib().msm_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{stage name: (total ms, launches)} accumulated while profiling was on."""
+        ms = np.zeros(32); cnt = np.zeros(32, dtype=np.int64)
+        k = lib().msm_profile_read(self._h, _ptr(ms), _ptr(cnt), 32, 1 if reset else 0)
+        return {lib().msm_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
+
+    def count_pairs(self) -> int:
+        """Ordered pairs (i, j != i) with r_ij < a in the last evaluation."""
+        out = C.c_int64(0)
+        _check(lib().msm_count_pairs(self._h, C.byref(out)))
+        return int(out.value)
+
+    # -- inspection -----------------------------------------------------------
+    def grid_shape(self, level):
+        shp = np.zeros(3, dtype=np.int64); lo = np.zeros(3, dtype=np.int64)
+        _check(lib().msm_grid_shape(self._h, int(level), _ptr(shp), _ptr(lo)))
+        return tuple(int(v) for v in shp), tuple(int(v) for v in lo)
+
+    def stage_grid(self, level, which):
+        """which: 'q' (charges), 'ucut' (lattice-cutoff potential), 'u' (potential); array (nz, ny, nx)."""
+        w = {"q": 0, "ucut": 1, "u": 2}[which]
+        shp, _ = self.grid_shape(level)
+        out = np.empty(shp[::-1])
+        _check(lib().msm_stage_grid(self._h, int(level), w, _ptr(out), out.size))
+        return out
+
+    def cell_list(self, n):
+        nc = C.c_int64(0)
+        _check(lib().msm_cell_list(self._h, None, None, C.byref(nc)))
+        perm = np.empty(n, dtype=np.int64); start = np.empty(nc.value + 1, dtype=np.int64)
+        _check(lib().msm_cell_list(self._h, _ptr(perm), _ptr(start), C.byref(nc)))
+        return perm, start
+
+    def stage_atoms(self, n):
+        """Short-range potential sum_j q_j g*(r_ij) and force sum (before k_e), caller's atom order."""
+        phi = np.empty(n); f = np.empty((n, 3))
+        _check(lib().msm_stage_atoms(self._h, 0, _ptr(phi), n))
+        _check(lib().msm_stage_atoms(self._h, 1, _ptr(f), 3 * n))
+        return phi, f
+
+
+def _system_struct(sys, need_v=False):
+    """Build an msm_system from an object with pos, vel, q, mass, lj, n_mol, box."""
+    s = SystemC()
+    s.n = int(sys.pos.shape[0])
+    s.n_mol = int(getattr(sys, "n_mol", 0))
+    keep = []
+
+    def arr(x, dtype):
+        if x is None:
+            return None
+        if _is_tensor(x):
+            return x
+        a = np.ascontiguousarray(x, dtype=dtype)
+        keep.append(a)
+        return a
+
+    pos = sys.pos
+    if not (_is_tensor(pos) or (isinstance(pos, np.ndarray) and pos.dtype == np.float64 and pos.flags["C_CONTIGUOUS"])):
+        raise ValueError("sys.pos must be a float64 C-contiguous array or a CUDA tensor (updated in place)")
+    s.x = _ptr(pos)
+    vel = getattr(sys, "vel", None)
+    if need_v and vel is None:
+        raise ValueError("velocities required")
+    s.v = _ptr(vel) if vel is not None else None
+    s.q = _ptr(arr(sys.q, np.float64))
+    m = getattr(sys, "mass", None)
+    s.m = _ptr(arr(m, np.float64)) if m is not None else None
+    lj = getattr(sys, "lj", None)
+    s.lj = _ptr(arr(lj, np.uint8)) if lj is not None else None
+    b = np.asarray(sys.box, dtype=np.float64).reshape(6)
+    for d in range(6):
+        s.box[d] = float(b[d])
+    f = getattr(sys, "force", None)          # optional (n, 3) float64: forces carried between md_run calls
+    if f is not None:
+        if not (_is_tensor(f) or (isinstance(f, np.ndarray) and f.dtype == np.float64 and f.flags["C_CONTIGUOUS"])):
+            raise ValueError("sys.force must be a float64 C-contiguous array or a CUDA tensor")
+        s.f = _ptr(f)
+        s.f_valid = int(getattr(sys, "force_valid", 0))
+        s.energy = float(getattr(sys, "energy", 0.0))
+    s._keep = keep
+    return s, keep
+
+
+def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float, model="water",
+                 precision="fp32", stream=None):
+    """Parareal over md_run: G and F are dict(a, h, levels, dt, steps).
+
+    Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
+    pg = make_params(G["a"], G["h"], G["levels"], G.get("precision", precision), model)
+    pf = make_params(F["a"], F["h"], F["levels"], F.get("precision", precision), model)
+    s, keep = _system_struct(sys, need_v=True)
+    n = int(s.n)
+    xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))
+    it = C.c_int32(0); dx = C.c_double(0)
+    rc = lib().parareal_run(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
+                            int(F["steps"]), C.byref(s), int(n_slices), int(max_iter), float(tol), _ptr(xs),
+                            _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
+    if rc not in (0, -6):
+        _check(rc)
+    return xs, vs, it.value, dx.value, rc == 0
+
+
+# ----------------------------------------------------------------- autograd
+
+def msm_energy(pos, q, box, msm: MSM):
+    """U(pos, q) as a differentiable torch scalar; backward gives dU/dpos = -F and dU/dq = phi."""
+    return _MSMEnergy.apply(pos, q, box, msm)
+
+
+def _make_function():
+    torch = _torch()
+
+    class MSMEnergyFn(torch.autograd.Function):
+        """Forward: one MSM evaluation (energy, with forces and potentials from the same pass).
+
+        Backward: the analytic gradient of the quadratic form U = 1/2 q^T K(r) q.
+        dU/dq_i = phi_i (K symmetric: every interpolation operator I^k is
+        symmetric in its two arguments, Sec. 3), dU/dr_i = -F_i, where F_i
+        was formed by the transposed chain interpolation^T (= anterpolation
+        weights' gradients) applied to the prolonged grid potential.
+        """
+
+        @staticmethod
+        def forward(ctx, pos, q, box, msm):
+            e, f, p = msm.energy_forces(pos.detach().contiguous(), q.detach().contiguous(), box)
+            ctx.save_for_backward(f, p)
+            return e.reshape(())
+
+        @staticmethod
+        def backward(ctx, g):
+            f, p = ctx.saved_tensors
+            return -g * f, g * p, None, None
+
+    return MSMEnergyFn
+
+
+class _Lazy:
+    _fn = None
+
+    def apply(self, *args):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_function()
+        return _Lazy._fn.apply(*args)
+
+
+_MSMEnergy = _Lazy()

@@ -1,0 +1,88 @@
+// common.cuh -- types and small device helpers shared by the kernels of
+// libmsm_gb300.so.  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/msm.h"
+
+// Packed 4-vector of the compute type: (x, y, z, w) with natural alignment so
+// that one 128-bit (float) or 256-bit (double) access moves a whole atom.
+template <typename T> struct alignas(4 * sizeof(T)) vec4 { T x, y, z, w; };
+
+// Smoothing constants of the C^2 Taylor gamma (Sec. 3):
+//   gamma(rho) = 15/8 - 5/4 rho^2 + 3/8 rho^4 (rho < 1), 1/rho (rho >= 1).
+#define GAMMA_C0 (15.0 / 8.0)
+#define GAMMA_C1 (-5.0 / 4.0)
+#define GAMMA_C2 (3.0 / 8.0)
+
+// Device status word: the first error wins; every later kernel of the same
+// evaluation checks it and returns at once, so no kernel indexes a grid with
+// an out-of-box atom.
+__device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+__device__ __forceinline__ bool failed(const int *status) { return *(volatile const int *)status != 0; }
+
+// Geometry of one system's finest-grid cells and grid levels.
+struct CellGeom {
+    double origin[3];   // box origin x0
+    double h;           // finest spacing
+    int    nc[3];       // cells per axis: floor(L/h) + 1
+    int    ncells;
+};
+
+#define MSM_MAX_LEVELS 12
+
+struct LevelGeom {
+    int lo[3];          // index of the first point per axis
+    int n[3];           // points per axis
+    int off;            // offset of this level in the concatenated grid buffer
+};
+
+struct GridGeom {
+    int       levels;
+    LevelGeom L[MSM_MAX_LEVELS];
+    int       total;    // points over all levels
+};
+
+// 1-D cubic C1 numerical-Hermite weights of an atom whose fractional
+// coordinate within its finest cell is f in [0, 1): weights of grid points
+// c-1, c, c+1, c+2 (c = the atom's cell), i.e. Phi(f+1), Phi(f), Phi(f-1),
+// Phi(f-2), and their derivatives d/df.  Phi(t) = (1-|t|)(1+|t|-3/2 t^2) on
+// |t| <= 1 and -1/2 (|t|-1)(2-|t|)^2 on 1 <= |t| <= 2 (Sec. 3, p = 3).
+template <typename T>
+__device__ __forceinline__ void phi_weights(T f, T w[4])
+{
+    const T g = T(1) - f;
+    w[0] = T(-0.5) * f * g * g;                         // Phi(1 + f)
+    w[1] = g * (T(1) + f - T(1.5) * f * f);             // Phi(f)
+    w[2] = f * (T(1) + g - T(1.5) * g * g);             // Phi(1 - f)
+    w[3] = T(-0.5) * g * f * f;                         // Phi(2 - f)
+}
+
+template <typename T>
+__device__ __forceinline__ void phi_weights_d(T f, T w[4], T dw[4])
+{
+    const T g = T(1) - f;
+    w[0] = T(-0.5) * f * g * g;
+    w[1] = g * (T(1) + f - T(1.5) * f * f);
+    w[2] = f * (T(1) + g - T(1.5) * g * g);
+    w[3] = T(-0.5) * g * f * f;
+    // d/df of each: Phi'(1+f), Phi'(f), -Phi'(1-f), -Phi'(2-f)
+    dw[0] = T(-0.5) * g * (T(1) - T(3) * f);            // -1/2 (1-f)(1-3f)
+    dw[1] = f * (T(-5) + T(4.5) * f);                   // -5f + 9/2 f^2
+    dw[2] = g * (T(5) - T(4.5) * g);                    // 5g - 9/2 g^2, g = 1-f
+    dw[3] = T(0.5) * f * (T(3) * f - T(2));             // d/df of -1/2 (1-f) f^2
+}
+
+// Kernel launch accounting (reported through msm_kernel_launches()).
+void count_launch(int k = 1);
+
+#define CUDA_TRY(expr)                                                    \
+    do {                                                                  \
+        cudaError_t e__ = (expr);                                         \
+        if (e__ != cudaSuccess) return fail_cuda(e__, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+int fail_msg(int code, const char *fmt, ...);

@@ -1,0 +1,191 @@
+// k_bin.cu -- bit-exact cell binning and the stable counting sort of atoms
+// by finest-grid cell: the cell lists behind the short-range sum and the
+// gather-form anterpolation and interpolation of Sec. 3.
+//
+//   k_bin_keys     cell of every atom: t = (x - x0) * (1/h) with one IEEE FP64
+//                  subtract and one IEEE FP64 multiply (no contraction), c =
+//                  floor(t); key = (cz*ny + cy)*nx + cx; histogram by integer
+//                  atomics (exact).  Also writes the compute-type copies of
+//                  the box-relative position and of the in-cell fraction
+//                  t - c (exact in FP64 by Sterbenz) in original order, so no
+//                  later kernel repeats FP64 work.
+//   k_scan_*       exclusive prefix sum of the histogram -> cell_start
+//   k_scatter      atom -> a slot of its cell (order inside a cell arbitrary)
+//   k_sort_cells   each cell's slots reordered by atom index: the result is the
+//                  unique stable order (key, index), whatever the atomics did
+//   k_gather       sorted copies of position, fraction, key and (molecule, LJ) flag
+#include "kernels.cuh"
+
+namespace msm {
+
+template <typename T>
+__global__ void k_bin_keys(int n, const double *__restrict__ pos, const double *__restrict__ q, CellGeom g,
+                           double inv_h, int *__restrict__ key, int *__restrict__ count, vec4<T> *__restrict__ rel,
+                           vec4<T> *__restrict__ frac, int *__restrict__ status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c[3];
+    double r[3], f[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        double x = pos[3 * i + d];
+        if (!isfinite(x)) { set_status(status, MSM_EINVAL); key[i] = -1; return; }
+        double rl = __dsub_rn(x, g.origin[d]);
+        double t = __dmul_rn(rl, inv_h);
+        double fl = floor(t);
+        if (!(t >= 0.0) || fl > (double)(g.nc[d] - 1)) { set_status(status, MSM_ERANGE); key[i] = -1; return; }
+        c[d] = (int)fl;
+        r[d] = rl;
+        f[d] = __dsub_rn(t, fl);
+    }
+    int k = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+    T qi = (T)q[i];
+    rel[i] = vec4<T>{(T)r[0], (T)r[1], (T)r[2], qi};
+    frac[i] = vec4<T>{(T)f[0], (T)f[1], (T)f[2], qi};
+}
+
+// Exclusive scan in three passes: per-block sums, scan of block sums, add.
+constexpr int SCAN_T = 512, SCAN_E = 8, SCAN_B = SCAN_T * SCAN_E;
+
+__device__ __forceinline__ int block_excl_scan(int v, int *tot)
+{
+    __shared__ int ws[SCAN_T / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < SCAN_T / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, s, o); if (lane >= o) s += y; }
+        if (lane < SCAN_T / 32) ws[lane] = s;
+    }
+    __syncthreads();
+    int base = w ? ws[w - 1] : 0;
+    *tot = ws[SCAN_T / 32 - 1];
+    int r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(int m, const int *__restrict__ in, int *__restrict__ out,
+                                                        int *__restrict__ bsum, const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int b0 = blockIdx.x * SCAN_B + threadIdx.x * SCAN_E;
+    int v[SCAN_E], s = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; e++) { v[e] = (b0 + e < m) ? in[b0 + e] : 0; s += v[e]; }
+    int tot;
+    int ex = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int e = 0; e < SCAN_E; e++) { if (b0 + e < m) out[b0 + e] = ex; ex += v[e]; }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(int nb, int *__restrict__ bsum, int *__restrict__ total,
+                                                      const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int b0 = threadIdx.x * SCAN_E;          // one block; nb <= SCAN_B
+    int v[SCAN_E], s = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; e++) { v[e] = (b0 + e < nb) ? bsum[b0 + e] : 0; s += v[e]; }
+    int tot;
+    int ex = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int e = 0; e < SCAN_E; e++) { if (b0 + e < nb) bsum[b0 + e] = ex; ex += v[e]; }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void k_scan_add(int m, int *__restrict__ out, const int *__restrict__ bsum, const int *__restrict__ total,
+                           const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] += bsum[i / SCAN_B];
+    if (i == 0) out[m] = *total;
+}
+
+__global__ void k_scatter(int n, const int *__restrict__ key, const int *__restrict__ start, int *__restrict__ count,
+                          int *__restrict__ perm, const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = key[i];
+    int slot = start[k] + atomicSub(&count[k], 1) - 1;
+    perm[slot] = i;
+}
+
+__global__ void k_sort_cells(int ncells, const int *__restrict__ start, int *__restrict__ perm,
+                             const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int s0 = start[c], s1 = start[c + 1];
+    for (int s = s0 + 1; s < s1; s++) {           // insertion sort: a cell holds a few atoms
+        int v = perm[s], t = s - 1;
+        while (t >= s0 && perm[t] > v) { perm[t + 1] = perm[t]; t--; }
+        perm[t + 1] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int n, const int *__restrict__ perm, const int *__restrict__ key,
+                         const vec4<T> *__restrict__ rel, const vec4<T> *__restrict__ frac,
+                         const uint8_t *__restrict__ lj, int n_mol, vec4<T> *__restrict__ apos,
+                         vec4<T> *__restrict__ afrac, int *__restrict__ akey, int *__restrict__ aflag,
+                         const int *__restrict__ status)
+{
+    if (failed(status)) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int i = perm[s];
+    apos[s] = rel[i];
+    afrac[s] = frac[i];
+    akey[s] = key[i];
+    const int mol = i < 3 * n_mol ? i / 3 : n_mol + (i - 3 * n_mol);   // single sites: own molecule
+    aflag[s] = (mol << 1) | ((lj && lj[i]) ? 1 : 0);
+}
+
+int scan_scratch_ints() { return SCAN_B + 1; }
+
+template <typename T>
+int launch_bin(const BinArgs<T> &a, cudaStream_t st)
+{
+    const int n = a.n;
+    const int m = a.g.ncells;
+    const int nb = (m + SCAN_B - 1) / SCAN_B;
+    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
+    CUDA_TRY(cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)(m + 1), st));
+    if (n > 0) {
+        k_bin_keys<T><<<(n + 255) / 256, 256, 0, st>>>(n, a.pos, a.q, a.g, a.inv_h, a.key, a.count, a.rel, a.frac,
+                                                       a.status);
+        count_launch();
+    }
+    k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, a.count, a.start, a.bsum, a.status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, a.bsum, a.bsum + SCAN_B, a.status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.bsum, a.bsum + SCAN_B, a.status);
+    count_launch(3);
+    if (n > 0) {
+        k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, a.key, a.start, a.count, a.perm, a.status);
+        k_sort_cells<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.perm, a.status);
+        k_gather<T><<<(n + 255) / 256, 256, 0, st>>>(n, a.perm, a.key, a.rel, a.frac, a.lj, a.n_mol, a.apos,
+                                                     a.afrac, a.akey, a.aflag, a.status);
+        count_launch(3);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+template int launch_bin<float>(const BinArgs<float> &, cudaStream_t);
+template int launch_bin<double>(const BinArgs<double> &, cudaStream_t);
+
+}  // namespace msm

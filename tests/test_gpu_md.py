@@ -1,0 +1,174 @@
+"""GPU velocity Verlet (+ SHAKE/RATTLE water completion) and parareal against the
+FP64 oracle and against their own invariants (Secs. 2 and 4), through the C ABI.
+
+Bars: the FP64 path follows the oracle's trajectory to 1e-9 nm over 10 steps
+(both solve the same constraint equations to 1e-12 relative, so they differ
+only by rounding amplified over a few steps); the FP32 path to 1e-5 nm (FP32
+forces carry ~1e-6 relative error; 10 steps of 2 fs move an atom ~1e-2 nm).
+Parareal invariants are bitwise: the library's F and G are deterministic.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_1889_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A, H = 1.2, 0.25
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def api(torch):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_1889_gb300 import api as a
+    return a
+
+
+def _dev_sys(torch, s):
+    t = lambda x: torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+    return inputs.System(pos=t(s.pos), q=t(s.q), mass=t(s.mass), box=s.box, vel=t(s.vel), n_mol=s.n_mol,
+                         lj=torch.tensor(s.lj, device="cuda"))
+
+
+@pytest.fixture(scope="module")
+def small_water():
+    return inputs.water_box(90, 1.0, margin=0.5, seed=3, vel_seed=4)
+
+
+@pytest.mark.parametrize("prec,tol_x,tol_e", [("fp64", 1e-9, 1e-9), ("fp32", 1e-5, 1e-5)])
+def test_md_matches_oracle(api, torch, small_water, prec, tol_x, tol_e):
+    s = small_water
+    ox, ov, ouk = oracle.md_run(s, a=A, h=H, levels=3, dt=0.002, n_steps=10)
+    m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water")
+    d = _dev_sys(torch, s)
+    uk = m.md_run(d, dt=0.002, n_steps=10).cpu().numpy()
+    assert np.abs(d.pos.cpu().numpy() - ox).max() <= tol_x
+    assert np.abs(d.vel.cpu().numpy() - ov).max() <= 1e3 * tol_x
+    scale = np.abs(ouk).max()
+    assert np.abs(uk - ouk).max() <= tol_e * scale
+
+
+def test_md_keeps_rigid_geometry(api, torch, small_water):
+    s = small_water
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-6)):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water")
+        d = _dev_sys(torch, s)
+        m.md_run(d, dt=0.002, n_steps=20, record=False)
+        x = d.pos.cpu().numpy()[: 3 * s.n_mol].reshape(-1, 3, 3)
+        oh = np.linalg.norm(x[:, 0] - x[:, 1], axis=1)
+        hh = np.linalg.norm(x[:, 1] - x[:, 2], axis=1)
+        assert np.abs(oh / inputs.D_OH - 1).max() <= tol
+        assert np.abs(hh / inputs.d_hh() - 1).max() <= tol
+
+
+def test_md_is_time_reversible_on_gpu(api, torch, small_water):
+    s = small_water
+    m = api.MSM(a=A, h=H, levels=3, precision="fp64", model="water")
+    d = _dev_sys(torch, s)
+    m.md_run(d, dt=0.002, n_steps=15, record=False)
+    d.vel.neg_()
+    m.md_run(d, dt=0.002, n_steps=15, record=False)
+    assert np.abs(d.pos.cpu().numpy() - s.pos).max() < 1e-9
+
+
+def test_md_split_runs_with_carried_forces_equal_one_run(api, torch, small_water):
+    s = small_water
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32", model="water")
+    d1 = _dev_sys(torch, s)
+    m.md_run(d1, dt=0.002, n_steps=6, record=False)
+    d2 = _dev_sys(torch, s)
+    d2.force = torch.zeros_like(d2.pos)
+    for _ in range(6):
+        m.md_run(d2, dt=0.002, n_steps=1, record=False)
+    assert torch.equal(d1.pos, d2.pos) and torch.equal(d1.vel, d2.vel)
+
+
+def test_md_host_buffers_equal_device_buffers(api, torch, small_water):
+    s = small_water
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32", model="water")
+    d = _dev_sys(torch, s)
+    m.md_run(d, dt=0.002, n_steps=5, record=False)
+    hs = inputs.System(pos=s.pos.copy(), q=s.q, mass=s.mass, box=s.box, vel=s.vel.copy(), n_mol=s.n_mol, lj=s.lj)
+    m.md_run(hs, dt=0.002, n_steps=5, record=False)
+    assert np.array_equal(hs.pos, d.pos.cpu().numpy()) and np.array_equal(hs.vel, d.vel.cpu().numpy())
+
+
+def test_nve_energy_is_conserved(api, torch):
+    s = inputs.water_box(3000, 3.1, margin=1.0)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water")
+        d = _dev_sys(torch, s)
+        uk = m.md_run(d, dt=0.002, n_steps=100).cpu().numpy()
+        e = uk.sum(1)
+        out[prec] = (np.abs(e - e[0]).max(), uk[:, 1].mean())
+        assert np.all(np.isfinite(uk))
+    # velocity Verlet at 2 fs: energy fluctuations stay a small fraction of the kinetic energy,
+    # and FP32 arithmetic does not add visible drift on top of the FP64 run
+    for prec in out:
+        assert out[prec][0] < 0.05 * out[prec][1]
+    assert out["fp32"][0] < 2.0 * out["fp64"][0] + 1e-3 * out["fp64"][1]
+
+
+# ------------------------------------------------------------------ parareal
+
+FINE = dict(a=1.2, h=0.25, levels=2, dt=0.002, steps=4)
+COARSE = dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=2)
+
+
+@pytest.fixture(scope="module")
+def pr_sys():
+    return inputs.water_box(45, 0.8, margin=0.5, seed=5, vel_seed=6)
+
+
+def _serial(api, torch, s, p, prec, n_slices):
+    m = api.MSM(a=p["a"], h=p["h"], levels=p["levels"], precision=prec, model="water")
+    d = _dev_sys(torch, s)
+    xs = [d.pos.cpu().numpy().copy()]; vs = [d.vel.cpu().numpy().copy()]
+    for _ in range(n_slices):
+        m.md_run(d, dt=p["dt"], n_steps=p["steps"], record=False)
+        xs.append(d.pos.cpu().numpy().copy()); vs.append(d.vel.cpu().numpy().copy())
+    return np.array(xs), np.array(vs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parareal_invariants_are_bitwise(api, torch, pr_sys, prec):
+    s = pr_sys
+    n_slices = 4
+    gx, gv = _serial(api, torch, s, COARSE, prec, n_slices)
+    fx, fv = _serial(api, torch, s, FINE, prec, n_slices)
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, n_slices, 0, 0.0, precision=prec)
+    assert it == 0 and np.array_equal(xs, gx) and np.array_equal(vs, gv)
+    for k in (1, 2):
+        xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, n_slices, k, 0.0, precision=prec)
+        assert it == k
+        assert np.array_equal(xs[: k + 1], fx[: k + 1]) and np.array_equal(vs[: k + 1], fv[: k + 1])
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, n_slices, n_slices, 0.0, precision=prec)
+    assert np.array_equal(xs, fx) and np.array_equal(vs, fv)
+
+
+def test_parareal_matches_oracle(api, torch, pr_sys):
+    s = pr_sys
+    oxs, ovs, oit, odx, orc = oracle.parareal(s, COARSE, FINE, n_slices=3, max_iter=2, tol=0.0)
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, 3, 2, 0.0, precision="fp64")
+    assert it == oit == 2
+    assert np.abs(xs - oxs).max() < 1e-9
+    assert np.abs(vs - ovs).max() < 1e-6
+
+
+def test_parareal_converges_to_tolerance(api, torch, pr_sys):
+    s = pr_sys
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, 6, 6, 1e-6, precision="fp32")
+    assert conv and dx <= 1e-6 and it <= 6
+    fx, _ = _serial(api, torch, s, FINE, "fp32", 6)
+    assert np.abs(xs - fx).max() <= 1e-5

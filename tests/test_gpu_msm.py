@@ -1,0 +1,230 @@
+"""GPU parity of the MSM evaluation against the FP64 CPU oracle (Sec. 3).
+
+Every call goes through the C ABI (libmsm_gb300.so via the ctypes binding).
+Bars:
+  * cell lists (binning, sort order, cell starts): bit-exact;
+  * FP64 path: relative RMS <= 1e-12 for forces, potentials and every stage,
+    relative energy <= 1e-12;
+  * FP32 path: relative force RMS <= 1e-4 and relative potential RMS <= 1e-4,
+    relative energy <= 1e-6.
+The FP32 energy bar follows from the arithmetic: U = 1/2 sum q_i phi_i is
+accumulated in FP64 from per-atom FP32 potentials whose relative error is
+~1e-6; the errors are independent across atoms, so the sum's relative error
+is far below 1e-6 unless U cancels strongly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_1889_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A, H = 1.2, 0.25
+TOL = {"fp64": dict(f=1e-12, p=1e-12, e=1e-12), "fp32": dict(f=1e-4, p=1e-4, e=1e-6)}
+
+
+def rel_rms(x, ref):
+    x = np.asarray(x, dtype=np.float64); ref = np.asarray(ref, dtype=np.float64)
+    den = np.sqrt((ref ** 2).sum())
+    return float(np.sqrt(((x - ref) ** 2).sum()) / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def api(torch):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_1889_gb300 import api as a
+    return a
+
+
+@pytest.fixture(scope="module")
+def water3k():
+    return inputs.water_box(3000, 3.1, margin=0.5, with_velocities=False)
+
+
+@pytest.fixture(scope="module")
+def water3k_ref(water3k):
+    s = water3k
+    return oracle.msm(s.pos, s.q, s.box, A, H, 3, stages=True)
+
+
+def _dev(torch, x):
+    return torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+def test_cell_list_is_bit_exact(api, torch, water3k):
+    for s in (water3k, inputs.random_cloud(5003, (2.7, 3.3, 1.9), seed=8, margin=0.0)):
+        m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+        m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+        perm, start = m.cell_list(s.n)
+        _, _, operm, ostart = oracle.bin_atoms(s.pos, s.box, H)
+        assert np.array_equal(perm, operm)
+        assert np.array_equal(start, ostart)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_short_range_matches_oracle(api, torch, water3k, water3k_ref, prec):
+    s = water3k
+    m = api.MSM(a=A, h=H, levels=3, precision=prec)
+    m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+    phi, f = m.stage_atoms(s.n)
+    t = TOL[prec]
+    assert rel_rms(phi, water3k_ref["phi_short"]) <= t["p"]
+    assert rel_rms(f, water3k_ref["f_short"]) <= t["f"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_grid_stage_matches_oracle(api, torch, water3k, water3k_ref, prec):
+    s = water3k
+    m = api.MSM(a=A, h=H, levels=3, precision=prec)
+    m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+    ref = water3k_ref
+    tol = TOL[prec]["p"]
+    for k in range(3):
+        assert m.grid_shape(k)[0] == ref["grid_shapes"][k]
+        assert rel_rms(m.stage_grid(k, "q"), ref["qgrids"][k]) <= tol, ("q", k)
+        assert rel_rms(m.stage_grid(k, "u"), ref["ugrids"][k]) <= tol, ("u", k)
+    for k in range(2):
+        assert rel_rms(m.stage_grid(k, "ucut"), ref["ucuts"][k]) <= tol, ("ucut", k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_msm_matches_oracle_on_water(api, torch, water3k, water3k_ref, prec):
+    s = water3k
+    m = api.MSM(a=A, h=H, levels=3, precision=prec)
+    e, f, p, vir = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box, virial=True)
+    ref = water3k_ref
+    t = TOL[prec]
+    assert abs(float(e) - ref["energy"]) <= t["e"] * abs(ref["energy"])
+    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
+    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+    vir_ref = (s.pos * ref["forces"]).sum()
+    assert abs(float(vir) - vir_ref) <= 1e-3 * np.abs(s.pos * ref["forces"]).sum()
+
+
+# ragged sizes, non-cubic boxes, every level count, empty-ish systems
+CASES = [
+    (1, (1.0, 1.0, 1.0), 1), (2, (1.3, 0.9, 1.1), 2), (33, (1.7, 1.7, 1.7), 2), (257, (2.3, 1.1, 3.4), 3),
+    (1000, (2.0, 2.0, 2.0), 1), (1531, (3.3, 2.2, 2.7), 4), (4099, (3.1, 3.1, 3.1), 5),
+]
+
+
+@pytest.mark.parametrize("n,L,levels", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_msm_matches_oracle_on_clouds(api, torch, n, L, levels, prec):
+    s = inputs.random_cloud(n, L, seed=n, margin=0.2)
+    ref = oracle.msm(s.pos, s.q, s.box, A, H, levels)
+    m = api.MSM(a=A, h=H, levels=levels, precision=prec)
+    e, f, p = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+    t = TOL[prec]
+    # U = 1/2 sum q_i phi_i minus the self energy 1/2 k_e sum q_i^2 gamma(0)/a: rounding scales
+    # with those terms, so the bar is relative to their magnitude (|U| alone is ill-conditioned
+    # for one or two atoms, where U is almost entirely cancelled self energy)
+    scale = abs(ref["energy"]) + 0.5 * oracle.KE * (s.q ** 2).sum() * 15.0 / (8.0 * A)
+    assert abs(float(e) - ref["energy"]) <= t["e"] * scale
+    if n > 1:
+        assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
+    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+
+
+def test_host_and_device_inputs_give_identical_bits(api, torch, water3k):
+    s = water3k
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    e1, f1, p1 = m.energy_forces(s.pos, s.q, s.box)                       # numpy -> host pointers
+    e2, f2, p2 = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+    assert e1 == float(e2)
+    assert np.array_equal(f1, f2.cpu().numpy()) and np.array_equal(p1, p2.cpu().numpy())
+
+
+def test_repeated_runs_are_bitwise_identical(api, torch, water3k):
+    s = water3k
+    for prec in ("fp32", "fp64"):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec)
+        r1 = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+        r2 = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+        assert float(r1[0]) == float(r2[0])
+        assert torch.equal(r1[1], r2[1]) and torch.equal(r1[2], r2[2])
+
+
+def test_empty_system(api, torch):
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    e, f, p = m.energy_forces(np.zeros((0, 3)), np.zeros(0), [0, 0, 0, 2.0, 2.0, 2.0])
+    assert e == 0.0 and f.shape == (0, 3)
+
+
+def test_out_of_box_and_non_finite_atoms_are_rejected(api, torch, water3k):
+    s = water3k
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    # valid atoms have 0 <= (x - x0)/h < floor(L/h) + 1: the box rounded up to whole cells of h
+    pos = s.pos.copy(); pos[17, 2] = s.box[2] + (np.floor(s.box[5] / H) + 1) * H + 1e-9
+    with pytest.raises(api.MSMError) as ei:
+        m.energy_forces(pos, s.q, s.box)
+    assert ei.value.name == "ERANGE"
+    pos = s.pos.copy(); pos[3, 1] = s.box[1] - 1e-12
+    with pytest.raises(api.MSMError) as ei:
+        m.energy_forces(pos, s.q, s.box)
+    assert ei.value.name == "ERANGE"
+    pos = s.pos.copy(); pos[5, 0] = np.nan
+    with pytest.raises(api.MSMError) as ei:
+        m.energy_forces(pos, s.q, s.box)
+    assert ei.value.name == "EINVAL"
+    # the handle stays usable after an error
+    e, f, p = m.energy_forces(s.pos, s.q, s.box)
+    assert np.isfinite(e)
+
+
+def test_batched_uneven_systems_equal_single_evaluations(api, torch):
+    systems = [inputs.random_cloud(n, L, seed=n, margin=0.2) for n, L in ((100, 1.5), (731, 2.4), (2050, 2.9))]
+    offs = np.cumsum([0] + [s.n for s in systems])
+    pos = np.concatenate([s.pos for s in systems]); q = np.concatenate([s.q for s in systems])
+    boxes = np.stack([s.box for s in systems])
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    e, f, p = m.energy_forces_batched(offs, _dev(torch, pos), _dev(torch, q), boxes)
+    for k, s in enumerate(systems):
+        e1, f1, p1 = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+        assert float(e[k]) == float(e1)
+        assert torch.equal(f[offs[k]:offs[k + 1]], f1) and torch.equal(p[offs[k]:offs[k + 1]], p1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_water_model_matches_oracle(api, torch, prec):
+    s = inputs.water_box(900, 2.1, margin=0.5, with_velocities=False)
+    ref = oracle.model_forces(s, A, H, 3)
+    m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water")
+    sd = inputs.System(pos=_dev(torch, s.pos), q=_dev(torch, s.q), mass=_dev(torch, s.mass), box=s.box,
+                       n_mol=s.n_mol, lj=torch.tensor(s.lj, device="cuda"))
+    e, f, p = m.system_forces(sd)
+    t = TOL[prec]
+    assert abs(float(e) - ref["energy"]) <= t["e"] * abs(ref["energy"])
+    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
+    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+
+
+def test_fp32_and_fp64_paths_agree_at_full_size(api, torch):
+    """1,000,000 atoms in a 21.5 nm water box, 5 levels (the throughput workload):
+    sampled short-range rows against the oracle, the FP32 path against the FP64 path."""
+    cfg = inputs.WORKLOADS["water1M"]
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=0.5, with_velocities=False)
+    pos, q = _dev(torch, s.pos), _dev(torch, s.q)
+    m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32")
+    m64 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp64")
+    e32, f32, p32 = m32.energy_forces(pos, q, s.box)
+    e64, f64, p64 = m64.energy_forces(pos, q, s.box)
+    assert abs(float(e32) - float(e64)) <= 1e-6 * abs(float(e64))
+    assert rel_rms(f32.cpu().numpy(), f64.cpu().numpy()) <= 1e-4
+    rng = np.random.default_rng(0)
+    tg = rng.choice(s.n, 512, replace=False)
+    ophi, of = oracle.short_range(s.pos, s.q, A, s.box, targets=tg)
+    phi64, fs64 = m64.stage_atoms(s.n)
+    assert rel_rms(phi64[tg], ophi) <= 1e-12 and rel_rms(fs64[tg], of) <= 1e-12
+    phi32, fs32 = m32.stage_atoms(s.n)
+    assert rel_rms(phi32[tg], ophi) <= 1e-4 and rel_rms(fs32[tg], of) <= 1e-4

@@ -1,0 +1,63 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function include/msm.h declares; argument validation that
+happens before any CUDA call works without a GPU.  No kernel is launched."""
+import ctypes as C
+import re
+import shutil
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not Path("/usr/local/cuda/bin/nvcc").exists(),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1309_1889_gb300 import api, build
+    build.build()
+    return api.lib()
+
+
+def declared():
+    text = (ROOT / "include" / "msm.h").read_text()
+    return [n for n in re.findall(r"^MSM_API\s+[\w\s\*]*?\**\s*(\w+)\s*\(", text, re.M)]
+
+
+def test_header_declares_the_boundary():
+    names = set(declared())
+    for want in ("msm_create", "msm_destroy", "msm_energy_forces", "md_run", "parareal_run",
+                 "msm_energy_forces_batched", "msm_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_1309_1889_gb300 import api
+    names = declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(api.EXPORTS)
+
+
+def test_default_params_and_validation_without_gpu(L):
+    from paper_1309_1889_gb300 import api
+    p = api.Params()
+    L.msm_default_params(C.byref(p))
+    assert p.a == 1.2 and p.h == 0.25 and p.n_levels == 3 and p.precision == api.FP32
+    assert abs(p.coulomb_k - 138.935458) < 1e-12
+    h = C.c_void_p()
+    bad = api.make_params(a=-1.0)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1
+    assert b"positive" in L.msm_last_error()
+    bad = api.make_params(levels=0)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1
+    bad = api.make_params(a=5.0, h=0.25)          # 2a/h = 40: lattice-cutoff radius too large
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_1309_1889_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH

@@ -25,7 +25,7 @@ def _cloud(n=400, L=2.3, seed=3):
 def test_binning_matches_stable_argsort():
     s = _cloud(2000, 2.7, seed=5)
     cell, key, perm, start = oracle.bin_atoms(s.pos, s.box, H)
-    t = (s.pos - s.box[:3]) / H
+    t = (s.pos - s.box[:3]) * (1.0 / H)
     c = np.floor(t).astype(np.int64)
     assert np.array_equal(cell, c)
     nc = np.floor(s.box[3:] / H).astype(np.int64) + 1
