@@ -8,8 +8,8 @@ level, FP64 top level, prolongation, interpolation, exclusions, FP64 energy
 reductions, half kicks and SHAKE/RATTLE.
 
 Workload: 1,000,000 atoms (333,333 rigid 3-site water-like molecules + 1
-filler site) in a 21.5 nm cube (+1 nm margin), a = 1.2 nm, h = 0.25 nm, 5
-levels, dt = 2 fs, NVE.  Inputs are resident in HBM when the timed region
+filler site) in a 21.5 nm cube (+1 nm margin with a flat-bottom wall), a =
+1.2 nm, h = 0.25 nm, 5 levels, dt = 2 fs, 1000 NVE steps by default.  Inputs are resident in HBM when the timed region
 starts; the working set (~0.3 GB) is larger than L2, so no flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -39,6 +39,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MSM atom-steps/s @1M atoms, FP32 batched vs plain FP64 GPU at force err ≤1e-4"
 UNIT = "atom-steps/s"
 A, H, DT = 1.2, 0.25, 0.002
+WALL = dict(wall_k=1.0e4, wall_width=0.8)     # flat-bottom wall of the water completion (1 nm margin)
 FLOPS_PER_PAIR = 29          # algorithmic FP32 flops per ordered in-cutoff pair (FMA = 2)
 FP32_LANES_PER_SM = 128
 
@@ -46,7 +47,7 @@ FP32_LANES_PER_SM = 128
 def args_parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="water1M")
@@ -181,7 +182,7 @@ def run_ours(a):
             dist.barrier()
 
     # ---- FP32 path: the timed run
-    m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water")
+    m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", **WALL)
     d = dev_system(torch, s, dev)
     m32.md_run(d, DT, a.warmup, record=False)
     torch.cuda.synchronize()
@@ -223,7 +224,7 @@ def run_ours(a):
     value = n * a.steps * world / (t_ms / 1e3)
 
     # ---- FP64 path on the same start state
-    m64 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp64", model="water")
+    m64 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp64", model="water", **WALL)
     d64 = dev_system(torch, s, dev)
     m64.md_run(d64, DT, 1, record=False)
     torch.cuda.synchronize()
@@ -246,7 +247,7 @@ def run_ours(a):
         import oracle
         oracle.build()
         t = time.perf_counter()
-        ref = oracle.model_forces(s, A, H, cfg["levels"])
+        ref = oracle.model_forces(s, A, H, cfg["levels"], **WALL)
         t_cpu = time.perf_counter() - t
         fo = ref["forces"]
         den = np.sqrt((fo ** 2).sum())
@@ -344,17 +345,17 @@ def run_reference(a):
 
     s = make(n_s)
     t = time.perf_counter()
-    oracle.model_forces(s, A, H, cfg["levels"])
+    oracle.model_forces(s, A, H, cfg["levels"], **WALL)
     t1 = time.perf_counter() - t
     steps = a.steps + a.warmup
     if t1 * steps > budget_s:
         n_s = max(3000, int(n_s * budget_s / (t1 * steps)))
         s = make(n_s)
     for _ in range(a.warmup):
-        oracle.model_forces(s, A, H, cfg["levels"])
+        oracle.model_forces(s, A, H, cfg["levels"], **WALL)
     t = time.perf_counter()
     for _ in range(a.steps):
-        oracle.model_forces(s, A, H, cfg["levels"])
+        oracle.model_forces(s, A, H, cfg["levels"], **WALL)
     dt = time.perf_counter() - t
     value = s.n * a.steps / dt
     sample = (f"one oracle force evaluation per step (MSM + water completion, FP64, plain C) of a "

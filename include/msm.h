@@ -68,7 +68,11 @@ extern "C" {
  *   basis_kind 0 = cubic C1 numerical Hermite Phi (the paper's p = 3 choice)
  *   model      MSM_MODEL_CHARGES or MSM_MODEL_WATER
  *   lj_sigma, lj_epsilon   O-O Lennard-Jones of the water completion
- *   d_oh, d_hh rigid O-H and H-H distances of the water completion (nm)  */
+ *   d_oh, d_hh rigid O-H and H-H distances of the water completion (nm)
+ *   wall_k, wall_width     water completion: harmonic flat-bottom wall that
+ *              keeps atoms inside the open domain; an atom closer than
+ *              wall_width to a box face feels 1/2 wall_k (wall_width - d)^2
+ *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)                     */
 typedef struct msm_params {
     double  a;
     double  h;
@@ -83,6 +87,8 @@ typedef struct msm_params {
     double  lj_epsilon;
     double  d_oh;
     double  d_hh;
+    double  wall_k;
+    double  wall_width;
 } msm_params;
 
 /* An MD system in the library's layout.  Rigid water occupies the first

@@ -272,11 +272,11 @@ LJ_SIGMA = 0.315061    # nm, O-O
 LJ_EPSILON = 0.6364    # kJ/mol
 
 
-def model_params(a, h, ke=KE, sigma=LJ_SIGMA, eps=LJ_EPSILON, d_oh=0.09572, d_hh=None):
+def model_params(a, h, ke=KE, sigma=LJ_SIGMA, eps=LJ_EPSILON, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0):
     if d_hh is None:
         import math
         d_hh = 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
-    return _f64([a, h, ke, sigma, eps, d_oh, d_hh])
+    return _f64([a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_width])
 
 
 def model_forces(sys, a, h, levels, ke=KE, pos=None, **kw):
@@ -308,7 +308,7 @@ def parareal(sys, G: dict, F: dict, n_slices, max_iter, tol, ke=KE):
     n = sys.n
 
     def pack(p):
-        mdp = model_params(p["a"], p["h"], ke)
+        mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0))
         return _f64(list(mdp) + [p["dt"], p["steps"], p["levels"]])
 
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))

@@ -593,10 +593,13 @@ void orc_direct(int64_t n, const double *pos, const double *q, double ke,
  *     the grid's interpolation error of the smooth part;
  *   - a Lennard-Jones 12-6 interaction between flagged sites within the
  *     cutoff a, shifted so it is zero at a;
- *   - rigid O-H and H-H distances, imposed by SHAKE/RATTLE.
- * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh}. */
+ *   - rigid O-H and H-H distances, imposed by SHAKE/RATTLE;
+ *   - a harmonic flat-bottom wall keeping atoms inside the open domain (the
+ *     paper states no boundary conditions): an atom closer than wall_w to a
+ *     face of the box gets 1/2 wall_k (wall_w - distance)^2 (wall_k = 0: off).
+ * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh, wall_k, wall_w}. */
 typedef struct {
-    double a, h, ke, sigma, eps, d_oh, d_hh;
+    double a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_w;
     int l;
     int64_t n, n_mol;
     const double *q, *m;
@@ -608,7 +611,8 @@ static void model_from(orc_model *md, const double *mdp, int l, int64_t n, int64
                        const double *q, const double *m, const unsigned char *lj, const double *box)
 {
     md->a = mdp[0]; md->h = mdp[1]; md->ke = mdp[2]; md->sigma = mdp[3]; md->eps = mdp[4];
-    md->d_oh = mdp[5]; md->d_hh = mdp[6]; md->l = l; md->n = n; md->n_mol = n_mol;
+    md->d_oh = mdp[5]; md->d_hh = mdp[6]; md->wall_k = mdp[7]; md->wall_w = mdp[8];
+    md->l = l; md->n = n; md->n_mol = n_mol;
     md->q = q; md->m = m; md->lj = lj; md->box = box;
 }
 
@@ -671,6 +675,24 @@ static int model_forces(const orc_model *md, const double *x, double *U, double 
             F[3 * i] += fl[3 * i]; F[3 * i + 1] += fl[3 * i + 1]; F[3 * i + 2] += fl[3 * i + 2];
         }
         free(idx); free(fl); free(el);
+    }
+    /* flat-bottom wall on each face of the box */
+    if (md->wall_k > 0.0) {
+        for (int64_t i = 0; i < n; i++)
+            for (int d = 0; d < 3; d++) {
+                double dist_lo = x[3 * i + d] - md->box[d];
+                double dist_hi = (md->box[d] + md->box[3 + d]) - x[3 * i + d];
+                if (dist_lo < md->wall_w) {
+                    double pen = md->wall_w - dist_lo;
+                    dU += 0.5 * md->wall_k * pen * pen;
+                    F[3 * i + d] += md->wall_k * pen;
+                }
+                if (dist_hi < md->wall_w) {
+                    double pen = md->wall_w - dist_hi;
+                    dU += 0.5 * md->wall_k * pen * pen;
+                    F[3 * i + d] -= md->wall_k * pen;
+                }
+            }
     }
     *U += dU;
     if (!pot) free(phi);
@@ -813,17 +835,17 @@ int orc_md_run(const double *mdp, int l, int64_t n, int64_t n_mol, double *x, do
  *              bitwise the bracket is exactly 0 and slice n+1 equals F);
  *   stop when max_{n,i,d} |x^{k+1} - x^k| <= tol, or after max_iter iterations.
  * slices_x/v: (n_slices+1) * n * 3, slot 0 holds state0 on entry.
- * gp/fp: {mdp (7 values), dt, steps, levels}. */
+ * gp/fp: {mdp (9 values), dt, steps, levels}. */
 int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
                  const double *q, const double *m, const unsigned char *lj, const double *box,
                  int n_slices, int max_iter, double tol, double *slices_x, double *slices_v,
                  int *iters_done, double *last_dx)
 {
     orc_model G, F;
-    model_from(&G, gp, (int)gp[9], n, n_mol, q, m, lj, box);
-    model_from(&F, fp, (int)fp[9], n, n_mol, q, m, lj, box);
-    double dtG = gp[7], dtF = fp[7];
-    int sG = (int)gp[8], sF = (int)fp[8];
+    model_from(&G, gp, (int)gp[11], n, n_mol, q, m, lj, box);
+    model_from(&F, fp, (int)fp[11], n, n_mol, q, m, lj, box);
+    double dtG = gp[9], dtF = fp[9];
+    int sG = (int)gp[10], sF = (int)fp[10];
     size_t sz = 3 * (size_t)n;
     int rc = ORC_OK;
     double *gold_x = malloc(sizeof(double) * sz * (size_t)n_slices), *gold_v = malloc(sizeof(double) * sz * (size_t)n_slices);

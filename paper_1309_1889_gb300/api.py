@@ -35,7 +35,8 @@ class Params(C.Structure):
     _fields_ = [("a", C.c_double), ("h", C.c_double), ("n_levels", C.c_int32), ("precision", C.c_int32),
                 ("coulomb_k", C.c_double), ("gamma_kind", C.c_int32), ("basis_kind", C.c_int32),
                 ("model", C.c_int32), ("reserved0", C.c_int32), ("lj_sigma", C.c_double),
-                ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double)]
+                ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double),
+                ("wall_k", C.c_double), ("wall_width", C.c_double)]
 
 
 class SystemC(C.Structure):
@@ -142,7 +143,7 @@ def _box(box):
 
 
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
-                lj_epsilon=0.6364, d_oh=0.09572, d_hh=None) -> Params:
+                lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0) -> Params:
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -152,6 +153,7 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
     p.lj_sigma, p.lj_epsilon = float(lj_sigma), float(lj_epsilon)
     p.d_oh = float(d_oh)
     p.d_hh = float(d_hh) if d_hh is not None else 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
+    p.wall_k, p.wall_width = float(wall_k), float(wall_width)
     return p
 
 
@@ -351,8 +353,10 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
     """Parareal over md_run: G and F are dict(a, h, levels, dt, steps).
 
     Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
-    pg = make_params(G["a"], G["h"], G["levels"], G.get("precision", precision), model)
-    pf = make_params(F["a"], F["h"], F["levels"], F.get("precision", precision), model)
+    pg = make_params(G["a"], G["h"], G["levels"], G.get("precision", precision), model,
+                     wall_k=G.get("wall_k", 0.0), wall_width=G.get("wall_width", 0.0))
+    pf = make_params(F["a"], F["h"], F["levels"], F.get("precision", precision), model,
+                     wall_k=F.get("wall_k", 0.0), wall_width=F.get("wall_width", 0.0))
     s, keep = _system_struct(sys, need_v=True)
     n = int(s.n)
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))

@@ -453,6 +453,15 @@ __global__ void k_interp(const InterpArgs<T> A)
         F[0] += (double)lj.x; F[1] += (double)lj.y; F[2] += (double)lj.z;
         e += 0.5 * (double)lj.w;
     }
+    if (A.wall_k > 0.0) {                          // flat-bottom wall of the water completion
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double x = A.pos[3 * i + d];
+            const double lo = A.wall_w - (x - A.box_lo[d]), hi = A.wall_w - (A.box_hi[d] - x);
+            if (lo > 0.0) { F[d] += A.wall_k * lo; e += 0.5 * A.wall_k * lo * lo; }
+            if (hi > 0.0) { F[d] -= A.wall_k * hi; e += 0.5 * A.wall_k * hi * hi; }
+        }
+    }
     if (A.forces) { A.forces[3 * i] = F[0]; A.forces[3 * i + 1] = F[1]; A.forces[3 * i + 2] = F[2]; }
     if (A.pot) A.pot[i] = phi;
     A.eatom[i] = e;

@@ -113,6 +113,8 @@ template <typename T> struct InterpArgs {
     const double *q;       // n, original order
     double ke, self;       // k_e, gamma(0)/a
     double inv_h;
+    double box_lo[3], box_hi[3];   // domain faces (wall of the water completion)
+    double wall_k, wall_w;         // wall_k = 0: no wall
     double *forces;        // n*3, original order (nullable)
     double *pot;           // n (nullable)
     double *eatom;         // n: 1/2 q_i phi_i + 1/2 E_lj,i

@@ -214,6 +214,7 @@ static int check_params(const msm_params *p)
     if (p->precision != MSM_FP32 && p->precision != MSM_FP64) return fail_msg(MSM_EINVAL, "unknown precision");
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
+    if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     int rad = 0;
     while ((double)(rad + 1) * p->h < 2.0 * p->a) rad++;
     if (rad > 12) return fail_msg(MSM_EINVAL, "2a/h = %.3g is too large (lattice-cutoff radius %d > 12)", 2 * p->a / p->h, rad);
@@ -482,6 +483,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     ia.n = n; ia.cg = h->cg; ia.L0 = h->gg.L[0]; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
     ia.afrac = h->afrac.as<vec4<T>>(); ia.sr = h->sr.as<vec4<T>>(); ia.lj = model ? h->lj.as<vec4<T>>() : nullptr;
     ia.u0 = ug; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k; ia.self = GAMMA_C0 / a; ia.inv_h = h->inv_h;
+    for (int d = 0; d < 3; d++) { ia.box_lo[d] = h->box[d]; ia.box_hi[d] = h->box[d] + h->box[3 + d]; }
+    ia.wall_k = model ? h->p.wall_k : 0.0; ia.wall_w = h->p.wall_width;
     ia.forces = io.forces; ia.pot = io.pot; ia.eatom = h->eatom.as<double>(); ia.vatom = h->vatom.as<double>();
     ia.status = status;
     TRY(launch_interp<T>(ia, st));

@@ -104,3 +104,33 @@ def test_parareal_with_fine_as_coarse_converges_in_one_iteration(pr_setup):
     xs, vs, it, dx, rc = oracle.parareal(s, F, F, n_slices=3, max_iter=2, tol=1e-12)
     assert np.abs(xs - fx).max() < 1e-12
     assert it <= 2 and rc == 0
+
+
+def test_wall_bounce_is_elastic():
+    """A lone rigid molecule thrown at a face of the flat-bottom wall comes back
+    (part of its translation turns into rotation: the wall pushes atoms, not the
+    centre of mass) with its kinetic energy kept -- the wall is conservative --
+    and the wall force is minus the gradient of its energy."""
+    s = inputs.water_box(3, 0.6, margin=0.6, seed=1, vel_seed=2)
+    s.vel[:] = 0.0
+    s.vel[:, 0] = -1.5                                      # nm/ps towards the x0 face
+    kw = dict(a=1.2, h=0.25, levels=2, wall_k=5000.0, wall_width=0.5)
+    m = s.mass[:3]
+    v0 = (m[:, None] * s.vel[:3]).sum(0) / m.sum()
+    x, v, uk = oracle.md_run(s, dt=0.001, n_steps=800, **kw)
+    v1 = (m[:, None] * v[:3]).sum(0) / m.sum()
+    assert x[:3, 0].min() > s.box[0]                        # never reached the face
+    assert v1[0] > 0.9 * abs(v0[0])                           # reflected
+    assert uk[-1, 1] == pytest.approx(uk[0, 1], rel=2e-3)      # no energy left in the wall
+    e = uk.sum(1)
+    assert np.abs(e - e[0]).max() < 1e-3 * uk[:, 1].max()
+    # F = -dU/dx inside the wall zone
+    pos = s.pos.copy(); pos[:, 0] -= pos[:, 0].min() - (s.box[0] + 0.2)
+    sw = inputs.System(pos=pos, q=s.q, mass=s.mass, box=s.box, n_mol=1, lj=s.lj)
+    f = oracle.model_forces(sw, 1.2, 0.25, 2, wall_k=5000.0, wall_width=0.5)["forces"]
+    d = 1e-6
+    pp = pos.copy(); pp[0, 0] += d
+    pm = pos.copy(); pm[0, 0] -= d
+    ep = oracle.model_forces(sw, 1.2, 0.25, 2, pos=pp, wall_k=5000.0, wall_width=0.5)["energy"]
+    em = oracle.model_forces(sw, 1.2, 0.25, 2, pos=pm, wall_k=5000.0, wall_width=0.5)["energy"]
+    assert f[0, 0] == pytest.approx(-(ep - em) / (2 * d), rel=1e-6)
