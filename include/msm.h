@@ -206,6 +206,33 @@ MSM_API const char *msm_stage_name(int32_t stage);
  * evaluation on h: the algorithmic work unit of the short-range sum. */
 MSM_API int  msm_count_pairs(msm_handle *h, int64_t *ordered_pairs);
 
+/* Cell binning and stable sort without any device allocation.  The paper has
+ * no counterpart: this serves callers that must not allocate device memory,
+ * for example a host program whose device memory is owned by another
+ * allocator with a fixed budget, or a time-critical loop that cannot afford
+ * the device-wide synchronisation that cudaMalloc/cudaFree imply.
+ *   pos[n*3]        device, FP64 atom positions
+ *   box, h          host; the same binning contract as every other entry
+ *                   point (t = (x - x0)*(1/h), cell = floor(t), key =
+ *                   (cz*ny + cy)*nx + cx with floor(L/h)+1 cells per axis)
+ *   perm[n]         device output: atoms ordered by (cell key, atom index)
+ *   cell_start[cell_start_len >= ncells+1]  device output: first slot of each
+ *                   cell, cell_start[ncells] = n
+ * The output equals msm_cell_list's after an evaluation of the same atoms.
+ * Scratch lives in a 24 MiB static device array inside the library, held by
+ * every GPU that loads it until the process exits: 4 bytes per atom plus 4
+ * per cell must fit (about 1 M atoms with 4 M cells); larger requests return
+ * MSM_EINVAL, as do host pointers.  The first call on a device, with that
+ * device current, looks up the array's device address; make that first call
+ * before any stream capture.  Every call reuses the same array and clears
+ * the parts that must start at zero; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  Synchronises the stream before returning.  Errors: MSM_EINVAL,
+ * MSM_ERANGE, MSM_ECUDA. */
+MSM_API int  msm_cell_list_noalloc(int64_t n, const double *pos, const double box[6], double h,
+                                   int32_t *perm, int32_t *cell_start, int64_t cell_start_len,
+                                   void *stream);
+
 /* Number of kernels this library launched since load (all handles). */
 MSM_API int64_t msm_kernel_launches(void);
 

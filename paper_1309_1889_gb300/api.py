@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces", "msm_energy_forces_batched",
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
-           "msm_stage_name", "msm_count_pairs")
+           "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc")
 
 
 def lib():
@@ -81,6 +81,8 @@ def lib():
         L.msm_profile_read.argtypes = [p, p, p, i32, i32]; L.msm_profile_read.restype = C.c_int
         L.msm_stage_name.argtypes = [i32]; L.msm_stage_name.restype = C.c_char_p
         L.msm_count_pairs.argtypes = [p, P(i64)]; L.msm_count_pairs.restype = C.c_int
+        L.msm_cell_list_noalloc.argtypes = [i64, p, P(d), d, p, p, i64, p]
+        L.msm_cell_list_noalloc.restype = C.c_int
         L.msm_last_error.argtypes = []; L.msm_last_error.restype = C.c_char_p
         _lib = L
     return _lib

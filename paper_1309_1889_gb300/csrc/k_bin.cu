@@ -157,6 +157,27 @@ __global__ void k_gather(int n, const int *__restrict__ perm, const int *__restr
 
 int scan_scratch_ints() { return SCAN_B + 1; }
 
+// Scan, scatter and per-cell sort of precomputed keys whose histogram is
+// already in count[0..m-1]: the second half of launch_bin, for callers that
+// compute the keys themselves.
+int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int *perm, int *bsum, int *status,
+                       cudaStream_t st)
+{
+    const int nb = (m + SCAN_B - 1) / SCAN_B;
+    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
+    k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, count, start, bsum, status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + SCAN_B, status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + SCAN_B, status);
+    count_launch(3);
+    if (n > 0) {
+        k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, key, start, count, perm, status);
+        k_sort_cells<<<(m + 255) / 256, 256, 0, st>>>(m, start, perm, status);
+        count_launch(2);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
 template <typename T>
 int launch_bin(const BinArgs<T> &a, cudaStream_t st)
 {

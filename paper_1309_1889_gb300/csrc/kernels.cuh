@@ -30,6 +30,8 @@ template <typename T> struct BinArgs {
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
 int scan_scratch_ints();
+int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int *perm, int *bsum, int *status,
+                       cudaStream_t st);
 
 // ---- short range (k_short.cu) ----------------------------------------------
 template <typename T> struct ShortArgs {
