@@ -220,6 +220,7 @@ def run_ours(a):
     uk = uk.cpu().numpy()
     etot = uk.sum(1)
     pairs = m32.count_pairs()
+    lstats = m32.list_stats()
 
     value = n * a.steps * world / (t_ms / 1e3)
 
@@ -313,6 +314,7 @@ def run_ours(a):
         "force_error": err,
         "nve": {"steps": a.steps, "energy_drift_kj_mol": drift,
                 "max_abs_dev_kj_mol": float(np.abs(etot - etot[0]).max()), "kinetic_kj_mol": float(uk[-1, 1])},
+        "verlet_list": lstats,
         "stage_ms_per_launch": stage_ms,
         "stage_share_of_step": step_share,
     }

@@ -72,7 +72,11 @@ extern "C" {
  *   wall_k, wall_width     water completion: harmonic flat-bottom wall that
  *              keeps atoms inside the open domain; an atom closer than
  *              wall_width to a box face feels 1/2 wall_k (wall_width - d)^2
- *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)                     */
+ *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)
+ *   list_skin  md_run only: Verlet-list skin (nm) of the short-range sum;
+ *              lists hold pairs within a + list_skin and are rebuilt when an
+ *              atom has moved more than list_skin/2 (0 = cell search every
+ *              step; the default).  Exact either way: pairs are still tested against a.  */
 typedef struct msm_params {
     double  a;
     double  h;
@@ -89,6 +93,7 @@ typedef struct msm_params {
     double  d_hh;
     double  wall_k;
     double  wall_width;
+    double  list_skin;
 } msm_params;
 
 /* An MD system in the library's layout.  Rigid water occupies the first
@@ -117,7 +122,8 @@ typedef struct msm_system {
 typedef struct msm_handle msm_handle;
 
 /* Fill *p with the defaults: a = 1.2, h = 0.25, 3 levels, FP32, k_e, C^2
- * gamma, cubic Phi, point charges, TIP3P-like O-O LJ and geometry. */
+ * gamma, cubic Phi, point charges, TIP3P-like O-O LJ and geometry, no wall,
+ * Verlet-list skin 0.1 nm. */
 MSM_API void msm_default_params(msm_params *p);
 
 /* Create a handle (validates *p; allocates nothing on the device until the
@@ -232,6 +238,13 @@ MSM_API int  msm_count_pairs(msm_handle *h, int64_t *ordered_pairs);
 MSM_API int  msm_cell_list_noalloc(int64_t n, const double *pos, const double box[6], double h,
                                    int32_t *perm, int32_t *cell_start, int64_t cell_start_len,
                                    void *stream);
+
+/* Verlet-list statistics of h since its creation (up to max values):
+ * builds, overflows (a capacity was exceeded: that step used the cell search
+ * and the capacity grew), entries-per-atom capacity, neighbourhood capacity,
+ * row slots per group, and the largest entries per atom, neighbourhood and
+ * row count seen at a build. */
+MSM_API int  msm_list_stats(msm_handle *h, int64_t *out, int32_t max);
 
 /* Number of kernels this library launched since load (all handles). */
 MSM_API int64_t msm_kernel_launches(void);

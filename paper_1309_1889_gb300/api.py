@@ -36,7 +36,7 @@ class Params(C.Structure):
                 ("coulomb_k", C.c_double), ("gamma_kind", C.c_int32), ("basis_kind", C.c_int32),
                 ("model", C.c_int32), ("reserved0", C.c_int32), ("lj_sigma", C.c_double),
                 ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double),
-                ("wall_k", C.c_double), ("wall_width", C.c_double)]
+                ("wall_k", C.c_double), ("wall_width", C.c_double), ("list_skin", C.c_double)]
 
 
 class SystemC(C.Structure):
@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces", "msm_energy_forces_batched",
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
-           "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc")
+           "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats")
 
 
 def lib():
@@ -81,6 +81,7 @@ def lib():
         L.msm_profile_read.argtypes = [p, p, p, i32, i32]; L.msm_profile_read.restype = C.c_int
         L.msm_stage_name.argtypes = [i32]; L.msm_stage_name.restype = C.c_char_p
         L.msm_count_pairs.argtypes = [p, P(i64)]; L.msm_count_pairs.restype = C.c_int
+        L.msm_list_stats.argtypes = [p, p, i32]; L.msm_list_stats.restype = C.c_int
         L.msm_cell_list_noalloc.argtypes = [i64, p, P(d), d, p, p, i64, p]
         L.msm_cell_list_noalloc.restype = C.c_int
         L.msm_last_error.argtypes = []; L.msm_last_error.restype = C.c_char_p
@@ -145,7 +146,8 @@ def _box(box):
 
 
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
-                lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0) -> Params:
+                lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
+                list_skin=0.0) -> Params:
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -156,6 +158,7 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
     p.d_oh = float(d_oh)
     p.d_hh = float(d_hh) if d_hh is not None else 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
     p.wall_k, p.wall_width = float(wall_k), float(wall_width)
+    p.list_skin = float(list_skin)
     return p
 
 
@@ -272,6 +275,13 @@ class MSM:
         k = lib().msm_profile_read(self._h, _ptr(ms), _ptr(cnt), 32, 1 if reset else 0)
         return {lib().msm_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(k)}
 
+    def list_stats(self) -> dict:
+        v = np.zeros(8, dtype=np.int64)
+        _check(lib().msm_list_stats(self._h, _ptr(v), 8))
+        keys = ("builds", "overflows", "cap_entries", "cap_neighbourhood", "row_slots", "max_entries_seen",
+                "max_neighbourhood_seen", "max_rows_seen")
+        return {k: int(x) for k, x in zip(keys, v)}
+
     def count_pairs(self) -> int:
         """Ordered pairs (i, j != i) with r_ij < a in the last evaluation."""
         out = C.c_int64(0)
@@ -356,9 +366,11 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
 
     Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
     pg = make_params(G["a"], G["h"], G["levels"], G.get("precision", precision), model,
-                     wall_k=G.get("wall_k", 0.0), wall_width=G.get("wall_width", 0.0))
+                     wall_k=G.get("wall_k", 0.0), wall_width=G.get("wall_width", 0.0),
+                     list_skin=G.get("list_skin", 0.0))
     pf = make_params(F["a"], F["h"], F["levels"], F.get("precision", precision), model,
-                     wall_k=F.get("wall_k", 0.0), wall_width=F.get("wall_width", 0.0))
+                     wall_k=F.get("wall_k", 0.0), wall_width=F.get("wall_width", 0.0),
+                     list_skin=F.get("list_skin", 0.0))
     s, keep = _system_struct(sys, need_v=True)
     n = int(s.n)
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))

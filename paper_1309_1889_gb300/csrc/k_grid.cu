@@ -15,44 +15,101 @@
 //   k_interp       phi_i = k_e (u_i^short + sum_mu phi^0_mu(r_i) u^0_mu - q_i gamma(0)/a),
 //                  F_i = k_e (F_i^short - q_i sum_mu grad phi^0_mu(r_i) u^0_mu) [+ LJ],
 //                  scattered back to the caller's atom order
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace msm {
 
 // ---------------------------------------------------------------- anterpolation
 
-template <int O, typename T> __device__ __forceinline__ T wsel(T f)
-{
-    // weight of grid point c - 1 + O for an atom at fraction f in cell c
-    const T g = T(1) - f;
-    if (O == 0) return T(-0.5) * f * g * g;
-    if (O == 1) return g * (T(1) + f - T(1.5) * f * f);
-    if (O == 2) return f * (T(1) + g - T(1.5) * g * g);
-    return T(-0.5) * g * f * f;
-}
 
-template <int OZ, int OY, int OX, typename T>
-__device__ __forceinline__ void anterp_cell(const int *__restrict__ start, const vec4<T> *__restrict__ afrac,
-                                            int cell, T &acc)
+// A CTA owns a tile of AT_X x AT_Y x AT_Z level-0 points.  The cells whose atoms
+// touch the tile (tile - 2 .. tile + 1 per axis) are staged in shared memory:
+// per atom the 4 weights along each axis (x weights pre-multiplied by q), one
+// float per weight, structure-of-arrays.  Each thread then gathers its point's
+// 4^3 cells in a fixed order (cells by oz, oy, ox, atoms by slot).  A block with
+// more atoms than the staging capacity (very dense input) takes the same loop
+// over global memory with the same arithmetic, so results do not depend on
+// which path ran.
+constexpr int AT_X = 8, AT_Y = 8, AT_Z = 4, AT_THREADS = AT_X * AT_Y * AT_Z;
+constexpr int AC_X = AT_X + 3, AC_Y = AT_Y + 3, AC_Z = AT_Z + 3, AC_N = AC_X * AC_Y * AC_Z;
+constexpr int AT_CAP = 1792;
+
+template <typename T> struct AnterpSmem {
+    int cell_off[AC_N + 1];
+    T w[12][AT_CAP];        // [0..3] x weights * q, [4..7] y weights, [8..11] z weights
+};
+template <typename T> size_t anterp_smem_bytes() { return sizeof(AnterpSmem<T>); }
+
+template <typename T>
+__device__ __forceinline__ void anterp_weights(const vec4<T> f, T wx[4], T wy[4], T wz[4])
 {
-    const int s0 = start[cell], s1 = start[cell + 1];
-    for (int s = s0; s < s1; s++) {
-        const vec4<T> f = afrac[s];
-        acc = fma(wsel<OZ>(f.z) * wsel<OY>(f.y), wsel<OX>(f.x) * f.w, acc);
-    }
+    phi_weights(f.x, wx);
+    phi_weights(f.y, wy);
+    phi_weights(f.z, wz);
+#pragma unroll
+    for (int o = 0; o < 4; o++) wx[o] *= f.w;
 }
 
 template <typename T>
-__global__ void k_anterp(const AnterpArgs<T> A)
+__global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AnterpSmem<T> &S = *reinterpret_cast<AnterpSmem<T> *>(smem_raw);
+    __shared__ int s_total;
+    if (failed(A.status)) return;
     const LevelGeom &L = A.L0;
-    if (idx >= L.n[0] * L.n[1] * L.n[2] || failed(A.status)) return;
-    const int ix = idx % L.n[0], iy = (idx / L.n[0]) % L.n[1], iz = idx / (L.n[0] * L.n[1]);
-    const int mx = L.lo[0] + ix, my = L.lo[1] + iy, mz = L.lo[2] + iz;
+    const int ntx = (L.n[0] + AT_X - 1) / AT_X, nty = (L.n[1] + AT_Y - 1) / AT_Y;
+    const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
     const int nx = A.cg.nc[0], ny = A.cg.nc[1], nz = A.cg.nc[2];
+    // absolute index of the tile's first point; cell block origin = that - 2
+    const int m0x = L.lo[0] + bx * AT_X, m0y = L.lo[1] + by * AT_Y, m0z = L.lo[2] + bz * AT_Z;
+    const int c0x = m0x - 2, c0y = m0y - 2, c0z = m0z - 2;
+    const int t = threadIdx.x;
+
+    // cell counts of the block (cells outside the grid count 0), exclusive scan
+    for (int e = t; e < AC_N; e += AT_THREADS) {
+        const int lx = e % AC_X, ly = (e / AC_X) % AC_Y, lz = e / (AC_X * AC_Y);
+        const int cx = c0x + lx, cy = c0y + ly, cz = c0z + lz;
+        int c = 0;
+        if (cx >= 0 && cx < nx && cy >= 0 && cy < ny && cz >= 0 && cz < nz) {
+            const int cell = (cz * ny + cy) * nx + cx;
+            c = A.start[cell + 1] - A.start[cell];
+        }
+        S.cell_off[e + 1] = c;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int acc = 0;
+        S.cell_off[0] = 0;
+        for (int e = 1; e <= AC_N; e++) { acc += S.cell_off[e]; S.cell_off[e] = acc; }
+        s_total = acc;
+    }
+    __syncthreads();
+    const bool staged = s_total <= AT_CAP;
+    if (staged) {
+        for (int e = t; e < AC_N; e += AT_THREADS) {
+            const int lx = e % AC_X, ly = (e / AC_X) % AC_Y, lz = e / (AC_X * AC_Y);
+            const int cx = c0x + lx, cy = c0y + ly, cz = c0z + lz;
+            if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
+            const int cell = (cz * ny + cy) * nx + cx;
+            const int g0 = A.start[cell], g1 = A.start[cell + 1];
+            for (int g = g0, k = S.cell_off[e]; g < g1; g++, k++) {
+                T wx[4], wy[4], wz[4];
+                anterp_weights(A.afrac[g], wx, wy, wz);
+#pragma unroll
+                for (int o = 0; o < 4; o++) { S.w[o][k] = wx[o]; S.w[4 + o][k] = wy[o]; S.w[8 + o][k] = wz[o]; }
+            }
+        }
+    }
+    __syncthreads();
+
+    const int ix = bx * AT_X + t % AT_X, iy = by * AT_Y + (t / AT_X) % AT_Y, iz = bz * AT_Z + t / (AT_X * AT_Y);
+    if (ix >= L.n[0] || iy >= L.n[1] || iz >= L.n[2]) return;
+    const int mx = L.lo[0] + ix, my = L.lo[1] + iy, mz = L.lo[2] + iz;
     T acc = 0;
-    // grid point mu receives weight index O = mu - c + 1 from an atom in cell c
+    // point mu receives weight index O = mu - c + 1 from an atom in cell c
 #pragma unroll
     for (int oz = 0; oz < 4; oz++) {
         const int cz = mz + 1 - oz;
@@ -61,30 +118,36 @@ __global__ void k_anterp(const AnterpArgs<T> A)
         for (int oy = 0; oy < 4; oy++) {
             const int cy = my + 1 - oy;
             if (cy < 0 || cy >= ny) continue;
-            const int rb = (cz * ny + cy) * nx;
 #pragma unroll
             for (int ox = 0; ox < 4; ox++) {
                 const int cx = mx + 1 - ox;
                 if (cx < 0 || cx >= nx) continue;
-                const int cell = rb + cx;
-#define AC(a, b, c) if (oz == a && oy == b && ox == c) anterp_cell<a, b, c, T>(A.start, A.afrac, cell, acc);
-#define AC4(a, b) AC(a, b, 0) AC(a, b, 1) AC(a, b, 2) AC(a, b, 3)
-#define AC16(a) AC4(a, 0) AC4(a, 1) AC4(a, 2) AC4(a, 3)
-                AC16(0) AC16(1) AC16(2) AC16(3)
-#undef AC16
-#undef AC4
-#undef AC
+                if (staged) {
+                    const int e = ((cz - c0z) * AC_Y + (cy - c0y)) * AC_X + (cx - c0x);
+                    for (int k = S.cell_off[e]; k < S.cell_off[e + 1]; k++)
+                        acc += (S.w[ox][k] * S.w[4 + oy][k]) * S.w[8 + oz][k];
+                } else {
+                    const int cell = (cz * ny + cy) * nx + cx;
+                    for (int g = A.start[cell]; g < A.start[cell + 1]; g++) {
+                        T wx[4], wy[4], wz[4];
+                        anterp_weights(A.afrac[g], wx, wy, wz);
+                        acc += (wx[ox] * wy[oy]) * wz[oz];
+                    }
+                }
             }
         }
     }
-    A.q0[L.off + idx] = acc;
+    A.q0[L.off + (iz * L.n[1] + iy) * L.n[0] + ix] = acc;
 }
 
 template <typename T>
 int launch_anterp(const AnterpArgs<T> &a, cudaStream_t st)
 {
-    const int m = a.L0.n[0] * a.L0.n[1] * a.L0.n[2];
-    k_anterp<T><<<(m + 255) / 256, 256, 0, st>>>(a);
+    const int ntx = (a.L0.n[0] + AT_X - 1) / AT_X, nty = (a.L0.n[1] + AT_Y - 1) / AT_Y,
+              ntz = (a.L0.n[2] + AT_Z - 1) / AT_Z;
+    const size_t smem = anterp_smem_bytes<T>();
+    CUDA_TRY(cudaFuncSetAttribute(k_anterp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_anterp<T><<<ntx * nty * ntz, AT_THREADS, smem, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -178,116 +241,177 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
     return MSM_OK;
 }
 
-constexpr int ST_TXT = 8;     // threads along x
-constexpr int ST_R = 4;       // outputs per thread along x
-constexpr int ST_TY = 4;
-constexpr int ST_TZ = 4;
-constexpr int ST_TX = ST_TXT * ST_R;
-constexpr int ST_THREADS = ST_TXT * ST_TY * ST_TZ;
+// Lattice cutoff, all levels 0..l-2 in one persistent launch.  A tile is
+// ST_TX x ST_TY x ST_TZ outputs of one level; each thread owns ST_RX outputs
+// along x times ST_RZ along z in registers.  The tile's input planes z' =
+// z0-rad .. z0+ST_TZ-1+rad are streamed through shared memory one at a time
+// (the plane plus an x/y halo of rad points); every plane row (y + dy) is read
+// into registers once and applied to the ST_RZ output planes it reaches
+// (dz = z' - z), walking the tap row (dy, dz) of the sphere with compile-time
+// offsets.  The weight table W[n] = g^0(|n| h) sits in shared memory; the level
+// factor 2^{-k} is applied at the end.  CTAs take tiles from a counter.
+constexpr int ST_RX = 4, ST_RZ = 4;
+constexpr int ST_TXT = 8, ST_TYT = 8;                 // threads along x and y
+constexpr int ST_TX = ST_TXT * ST_RX, ST_TY = ST_TYT, ST_TZ = ST_RZ;
+constexpr int ST_THREADS = ST_TXT * ST_TYT;
 constexpr int ST_MAXRAD = 12;
 
-__host__ __device__ constexpr int st_sx(int rad) { return ((ST_TX + 2 * rad) | 3) ; }   // odd stride: conflict-free rows
-__host__ __device__ constexpr int st_sy(int rad) { return ST_TY + 2 * rad; }
-__host__ __device__ constexpr int st_sz(int rad) { return ST_TZ + 2 * rad; }
+__host__ __device__ constexpr int st_px(int rad) { return ST_TX + 2 * rad; }
+__host__ __device__ constexpr int st_py(int rad) { return ST_TY + 2 * rad; }
 
 template <typename T> size_t stencil_smem_bytes(int rad)
 {
-    return sizeof(T) * (size_t)st_sx(rad) * st_sy(rad) * st_sz(rad);
+    const int wd = 2 * rad + 1;
+    return sizeof(T) * ((size_t)wd * wd * wd + (size_t)st_px(rad) * st_py(rad)) + sizeof(int) * (size_t)(wd * wd + 4);
 }
 template size_t stencil_smem_bytes<float>(int);
 template size_t stencil_smem_bytes<double>(int);
 
-template <int W, typename T>
-__device__ __forceinline__ void stencil_row(const T *__restrict__ s, const T *__restrict__ wr, T (&acc)[ST_R])
+template <int W, int RAD, typename T>
+__device__ __forceinline__ void stencil_row(const T (&v)[ST_RX + 2 * RAD], const T *__restrict__ wr, T (&acc)[ST_RX])
 {
-    T v[ST_R + 2 * W];
-#pragma unroll
-    for (int i = 0; i < ST_R + 2 * W; i++) v[i] = s[i - W];
 #pragma unroll
     for (int d = -W; d <= W; d++) {
-        const T w = __ldg(wr + d);
+        const T w = wr[d];
 #pragma unroll
-        for (int r = 0; r < ST_R; r++) acc[r] = fma(w, v[r + d + W], acc[r]);
+        for (int r = 0; r < ST_RX; r++) acc[r] = fma(w, v[r + d + RAD], acc[r]);
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A)
+template <int RAD, typename T>
+__device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[ST_RX + 2 * RAD], const T *wr, T (&acc)[ST_RX])
 {
+    switch (w) {
+#define ST_CASE(k) case k: if (k <= RAD) stencil_row<(k <= RAD ? k : 0), RAD>(v, wr, acc); break;
+    ST_CASE(0) ST_CASE(1) ST_CASE(2) ST_CASE(3) ST_CASE(4) ST_CASE(5) ST_CASE(6)
+    ST_CASE(7) ST_CASE(8) ST_CASE(9) ST_CASE(10) ST_CASE(11) ST_CASE(12)
+#undef ST_CASE
+    default: break;
+    }
+}
+
+template <typename T, int RAD>
+__global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, int *__restrict__ counter)
+{
+    constexpr int WD = 2 * RAD + 1, PX = st_px(RAD), PY = st_py(RAD);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);
+    T *wt = reinterpret_cast<T *>(smem_raw);                 // WD^3 weights
+    T *plane = wt + WD * WD * WD;                            // PY x PX input plane
+    int *hw = reinterpret_cast<int *>(plane + PX * PY);      // WD^2 half widths (-1: empty row)
+    __shared__ int s_tile;
     if (failed(A.status)) return;
-    int lev = 0;
-    while (lev + 1 < A.nlev && (int)blockIdx.x >= A.blk_off[lev + 1]) lev++;
-    const int b = blockIdx.x - A.blk_off[lev];
-    const LevelGeom &L = A.gg.L[lev];
-    const int tx = b % A.tiles[lev][0], ty = (b / A.tiles[lev][0]) % A.tiles[lev][1],
-              tz = b / (A.tiles[lev][0] * A.tiles[lev][1]);
-    const int x0 = tx * ST_TX, y0 = ty * ST_TY, z0 = tz * ST_TZ;     // tile origin (array indices)
-    const int rad = A.sg.rad;
-    const int SX = st_sx(rad), SY = st_sy(rad), SZ = st_sz(rad);
-    const T *__restrict__ q = A.q + L.off;
-
-    // stage q over the tile plus a halo of rad points (zero outside the grid)
-    const int tot = SX * SY * SZ;
-    for (int e = threadIdx.x; e < tot; e += ST_THREADS) {
-        const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
-        const int gx = x0 + sx - rad, gy = y0 + sy - rad, gz = z0 + sz - rad;
-        T v = 0;
-        if (sx < ST_TX + 2 * rad && gx >= 0 && gx < L.n[0] && gy >= 0 && gy < L.n[1] && gz >= 0 && gz < L.n[2])
-            v = q[(size_t)(gz * L.n[1] + gy) * L.n[0] + gx];
-        tile[e] = v;
-    }
+    const int t = threadIdx.x;
+    for (int e = t; e < WD * WD * WD; e += ST_THREADS) wt[e] = A.w[e];
+    for (int e = t; e < WD * WD; e += ST_THREADS) hw[e] = -1;
     __syncthreads();
-
-    const int lx = threadIdx.x % ST_TXT, ly = (threadIdx.x / ST_TXT) % ST_TY, lz = threadIdx.x / (ST_TXT * ST_TY);
-    T acc[ST_R];
-#pragma unroll
-    for (int r = 0; r < ST_R; r++) acc[r] = 0;
-    const int wd = A.sg.wdim;
-    for (int ri = 0; ri < A.sg.nrows; ri++) {
-        const int4 row = A.rows[ri];
-        const T *s = tile + ((lz + rad + row.y) * SY + (ly + rad + row.x)) * SX + lx * ST_R + rad;
-        const T *wr = A.w + ((row.y + rad) * wd + (row.x + rad)) * wd + rad;
-        switch (row.z) {
-        case 0: stencil_row<0>(s, wr, acc); break;
-        case 1: stencil_row<1>(s, wr, acc); break;
-        case 2: stencil_row<2>(s, wr, acc); break;
-        case 3: stencil_row<3>(s, wr, acc); break;
-        case 4: stencil_row<4>(s, wr, acc); break;
-        case 5: stencil_row<5>(s, wr, acc); break;
-        case 6: stencil_row<6>(s, wr, acc); break;
-        case 7: stencil_row<7>(s, wr, acc); break;
-        case 8: stencil_row<8>(s, wr, acc); break;
-        case 9: stencil_row<9>(s, wr, acc); break;
-        case 10: stencil_row<10>(s, wr, acc); break;
-        case 11: stencil_row<11>(s, wr, acc); break;
-        default: stencil_row<12>(s, wr, acc); break;
-        }
+    for (int e = t; e < A.sg.nrows; e += ST_THREADS) {
+        const int4 r = A.rows[e];
+        hw[(r.y + RAD) * WD + (r.x + RAD)] = r.z;
     }
-    const T scale = (T)ldexp(1.0, -lev);            // g^k = 2^{-k} g^0 at level-k spacing
-    const int gy = y0 + ly, gz = z0 + lz;
-    if (gy < L.n[1] && gz < L.n[2]) {
-        T *out = A.ucut + L.off + (size_t)(gz * L.n[1] + gy) * L.n[0];
+    const int lx = t % ST_TXT, ly = t / ST_TXT;
+    const int total = A.blk_off[A.nlev];
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= total) break;
+        int lev = 0;
+        while (lev + 1 < A.nlev && tile >= A.blk_off[lev + 1]) lev++;
+        const int b = tile - A.blk_off[lev];
+        const LevelGeom &L = A.gg.L[lev];
+        const int tx = b % A.tiles[lev][0], ty = (b / A.tiles[lev][0]) % A.tiles[lev][1],
+                  tz = b / (A.tiles[lev][0] * A.tiles[lev][1]);
+        const int x0 = tx * ST_TX, y0 = ty * ST_TY, z0 = tz * ST_TZ;
+        const T *__restrict__ q = A.q + L.off;
+        T acc[ST_RZ][ST_RX];
 #pragma unroll
-        for (int r = 0; r < ST_R; r++) {
-            const int gx = x0 + lx * ST_R + r;
-            if (gx < L.n[0]) out[gx] = scale * acc[r];
+        for (int s = 0; s < ST_RZ; s++)
+#pragma unroll
+            for (int r = 0; r < ST_RX; r++) acc[s][r] = 0;
+        for (int zp = z0 - RAD; zp < z0 + ST_TZ + RAD; zp++) {
+            const bool zin = zp >= 0 && zp < L.n[2];
+            __syncthreads();
+            for (int e = t; e < PX * PY; e += ST_THREADS) {
+                const int px = e % PX, py = e / PX;
+                const int gx = x0 + px - RAD, gy = y0 + py - RAD;
+                T v = 0;
+                if (zin && gx >= 0 && gx < L.n[0] && gy >= 0 && gy < L.n[1]) v = q[(size_t)(zp * L.n[1] + gy) * L.n[0] + gx];
+                plane[e] = v;
+            }
+            __syncthreads();
+            if (!zin) continue;
+#pragma unroll 1
+            for (int dy = -RAD; dy <= RAD; dy++) {
+                T v[ST_RX + 2 * RAD];
+                const T *row = plane + (ly + RAD + dy) * PX + lx * ST_RX;
+#pragma unroll
+                for (int i = 0; i < ST_RX + 2 * RAD; i++) v[i] = row[i];
+#pragma unroll
+                for (int s = 0; s < ST_RZ; s++) {
+                    const int dz = zp - (z0 + s);
+                    if (dz < -RAD || dz > RAD) continue;
+                    const int w = hw[(dz + RAD) * WD + (dy + RAD)];
+                    if (w < 0) continue;
+                    stencil_row_dispatch<RAD>(w, v, wt + ((dz + RAD) * WD + (dy + RAD)) * WD + RAD, acc[s]);
+                }
+            }
+        }
+        const T scale = (T)ldexp(1.0, -lev);        // g^k = 2^{-k} g^0 at level-k spacing
+        const int gy = y0 + ly;
+#pragma unroll
+        for (int s = 0; s < ST_RZ; s++) {
+            const int gz = z0 + s;
+            if (gy < L.n[1] && gz < L.n[2]) {
+                T *out = A.ucut + L.off + (size_t)(gz * L.n[1] + gy) * L.n[0];
+#pragma unroll
+                for (int r = 0; r < ST_RX; r++) {
+                    const int gx = x0 + lx * ST_RX + r;
+                    if (gx < L.n[0]) out[gx] = scale * acc[s][r];
+                }
+            }
         }
     }
 }
 
-template <typename T>
-int launch_stencil(const StencilArgs<T> &a, cudaStream_t st)
+template <typename T, int RAD>
+static int launch_stencil_rad(const StencilArgs<T> &a, int *counter, int sms, cudaStream_t st)
 {
-    if (a.nlev <= 0) return MSM_OK;
-    if (a.sg.rad > ST_MAXRAD) return fail_msg(MSM_EINVAL, "stencil radius %d exceeds %d (2a/h too large)", a.sg.rad, ST_MAXRAD);
-    const size_t smem = stencil_smem_bytes<T>(a.sg.rad);
-    CUDA_TRY(cudaFuncSetAttribute(k_stencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_stencil<T><<<a.blk_off[a.nlev], ST_THREADS, smem, st>>>(a);
+    const size_t smem = stencil_smem_bytes<T>(RAD);
+    CUDA_TRY(cudaFuncSetAttribute(k_stencil<T, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_THREADS, smem));
+    if (per_sm < 1) return fail_msg(MSM_EINVAL, "lattice-cutoff tile does not fit (radius %d)", RAD);
+    const int grid = std::min(a.blk_off[a.nlev], sms * per_sm);
+    k_stencil<T, RAD><<<grid, ST_THREADS, smem, st>>>(a, counter);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
+}
+
+template <typename T>
+int launch_stencil(const StencilArgs<T> &a, int *counter, cudaStream_t st)
+{
+    if (a.nlev <= 0) return MSM_OK;
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    switch (a.sg.rad) {
+    case 1: return launch_stencil_rad<T, 1>(a, counter, sms, st);
+    case 2: return launch_stencil_rad<T, 2>(a, counter, sms, st);
+    case 3: return launch_stencil_rad<T, 3>(a, counter, sms, st);
+    case 4: return launch_stencil_rad<T, 4>(a, counter, sms, st);
+    case 5: return launch_stencil_rad<T, 5>(a, counter, sms, st);
+    case 6: return launch_stencil_rad<T, 6>(a, counter, sms, st);
+    case 7: return launch_stencil_rad<T, 7>(a, counter, sms, st);
+    case 8: return launch_stencil_rad<T, 8>(a, counter, sms, st);
+    case 9: return launch_stencil_rad<T, 9>(a, counter, sms, st);
+    case 10: return launch_stencil_rad<T, 10>(a, counter, sms, st);
+    case 11: return launch_stencil_rad<T, 11>(a, counter, sms, st);
+    case 12: return launch_stencil_rad<T, 12>(a, counter, sms, st);
+    default: return fail_msg(MSM_EINVAL, "lattice-cutoff radius %d outside 1..%d", a.sg.rad, ST_MAXRAD);
+    }
 }
 
 void stencil_tiles(const LevelGeom &L, int t[3])
@@ -360,32 +484,36 @@ __global__ void k_prolong(LevelGeom F, LevelGeom C, const T *__restrict__ ucut, 
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= F.n[0] * F.n[1] * F.n[2] || failed(status)) return;
     const int m[3] = {F.lo[0] + idx % F.n[0], F.lo[1] + (idx / F.n[0]) % F.n[1], F.lo[2] + idx / (F.n[0] * F.n[1])};
-    int nu0[3], cnt[3];
+    // Four coarse points per axis nu0 .. nu0+3 with weights Phi(mu/2 - nu):
+    // even mu: nu0 = mu/2 - 1, weights (0, 1, 0, 0); odd mu: nu0 = (mu-3)/2, weights (-1, 9, 9, -1)/16.
+    int c0[3];
     T w[3][4];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        if ((m[d] & 1) == 0) {                     // even: only nu = mu/2 (Phi(0) = 1; Phi(+-1) = 0)
-            nu0[d] = m[d] >> 1; cnt[d] = 1; w[d][0] = T(1);
-        } else {                                   // odd: nu = (mu-3)/2 .. (mu+3)/2
-            nu0[d] = (m[d] - 3) >> 1; cnt[d] = 4;
-            w[d][0] = T(-1.0 / 16.0); w[d][1] = T(9.0 / 16.0); w[d][2] = T(9.0 / 16.0); w[d][3] = T(-1.0 / 16.0);
-        }
+        const bool odd = m[d] & 1;
+        c0[d] = (odd ? (m[d] - 3) >> 1 : (m[d] >> 1) - 1) - C.lo[d];
+        w[d][0] = odd ? T(-1.0 / 16.0) : T(0);
+        w[d][1] = odd ? T(9.0 / 16.0) : T(1);
+        w[d][2] = odd ? T(9.0 / 16.0) : T(0);
+        w[d][3] = odd ? T(-1.0 / 16.0) : T(0);
     }
     T acc = 0;
-    for (int a = 0; a < cnt[2]; a++) {
-        const int cz = nu0[2] + a - C.lo[2];
-        if (cz < 0 || cz >= C.n[2]) continue;
-        for (int b = 0; b < cnt[1]; b++) {
-            const int cy = nu0[1] + b - C.lo[1];
-            if (cy < 0 || cy >= C.n[1]) continue;
-            const T wzy = w[2][a] * w[1][b];
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        const int cz = c0[2] + a;
+        if (w[2][a] == T(0) || cz < 0 || cz >= C.n[2]) continue;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int cy = c0[1] + b;
+            if (w[1][b] == T(0) || cy < 0 || cy >= C.n[1]) continue;
+            const S *row = uc + (size_t)(cz * C.n[1] + cy) * C.n[0];
             T racc = 0;
-            for (int c = 0; c < cnt[0]; c++) {
-                const int cx = nu0[0] + c - C.lo[0];
-                if (cx < 0 || cx >= C.n[0]) continue;
-                racc = fma(w[0][c], (T)uc[(cz * C.n[1] + cy) * C.n[0] + cx], racc);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int cx = c0[0] + c;
+                if (w[0][c] != T(0) && cx >= 0 && cx < C.n[0]) racc = fma(w[0][c], (T)row[cx], racc);
             }
-            acc = fma(wzy, racc, acc);
+            acc = fma(w[2][a] * w[1][b], racc, acc);
         }
     }
     uf[F.off + idx] = ucut[F.off + idx] + acc;
@@ -440,8 +568,8 @@ __global__ void k_interp(const InterpArgs<T> A)
             gz = fma(dz[oz] * wy[oy], rp, gz);
         }
     }
-    const vec4<T> sr = A.sr[s];
     const int i = A.perm[s];
+    const vec4<T> sr = A.sr[i];
     const double q = A.q[i];
     const double ke = A.ke, ih = A.inv_h;
     const double phi = ke * ((double)sr.w + (double)p - q * A.self);
@@ -449,7 +577,7 @@ __global__ void k_interp(const InterpArgs<T> A)
                    ke * ((double)sr.z - q * (double)gz * ih)};
     double e = 0.5 * q * phi;
     if (A.lj) {
-        const vec4<T> lj = A.lj[s];
+        const vec4<T> lj = A.lj[i];
         F[0] += (double)lj.x; F[1] += (double)lj.y; F[2] += (double)lj.z;
         e += 0.5 * (double)lj.w;
     }
@@ -484,8 +612,8 @@ template int launch_anterp<float>(const AnterpArgs<float> &, cudaStream_t);
 template int launch_anterp<double>(const AnterpArgs<double> &, cudaStream_t);
 template int launch_restrict<float>(const LevelGeom &, const LevelGeom &, const float *, float *, const int *, cudaStream_t);
 template int launch_restrict<double>(const LevelGeom &, const LevelGeom &, const double *, double *, const int *, cudaStream_t);
-template int launch_stencil<float>(const StencilArgs<float> &, cudaStream_t);
-template int launch_stencil<double>(const StencilArgs<double> &, cudaStream_t);
+template int launch_stencil<float>(const StencilArgs<float> &, int *, cudaStream_t);
+template int launch_stencil<double>(const StencilArgs<double> &, int *, cudaStream_t);
 template int launch_top<float>(const LevelGeom &, const double *, const float *, double *, const int *, cudaStream_t);
 template int launch_top<double>(const LevelGeom &, const double *, const double *, double *, const int *, cudaStream_t);
 template int launch_prolong<float, float>(const LevelGeom &, const LevelGeom &, const float *, const float *, float *, const int *, cudaStream_t);

@@ -17,42 +17,45 @@ namespace msm {
 
 // ---------------------------------------------------------------- exclusions
 
+template <typename T>
 __global__ void k_exclusions(const ExclArgs A)
 {
     const int mo = blockIdx.x * blockDim.x + threadIdx.x;
     if (mo >= A.n_mol || failed(A.status)) return;
     const int i0 = 3 * mo;
-    double x[3][3], q[3], F[3][3] = {{0}}, dphi[3] = {0, 0, 0}, de[3] = {0, 0, 0};
+    double x[3][3];
+    T q[3], F[3][3], dphi[3], de[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        q[a] = A.q[i0 + a];
+        q[a] = (T)A.q[i0 + a];
+        dphi[a] = de[a] = 0;
 #pragma unroll
-        for (int d = 0; d < 3; d++) x[a][d] = A.x[3 * (i0 + a) + d];
+        for (int d = 0; d < 3; d++) { x[a][d] = A.x[3 * (i0 + a) + d]; F[a][d] = 0; }
     }
-    const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+    const T ke = (T)A.ke, ia = T(1) / (T)A.a;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const int a = pi[c], b = pj[c];
-        const double dx = x[a][0] - x[b][0], dy = x[a][1] - x[b][1], dz = x[a][2] - x[b][2];
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        const double rho = r / A.a;
-        double gam, dgam;                              // gamma(rho), gamma'(rho)
-        if (rho < 1.0) {
-            const double r2 = rho * rho;
-            gam = GAMMA_C0 + GAMMA_C1 * r2 + GAMMA_C2 * r2 * r2;
-            dgam = 2.0 * GAMMA_C1 * rho + 4.0 * GAMMA_C2 * r2 * rho;
+        const int a = c == 2 ? 1 : 0, b = c == 0 ? 1 : 2;
+        const T dx = (T)(x[a][0] - x[b][0]), dy = (T)(x[a][1] - x[b][1]), dz = (T)(x[a][2] - x[b][2]);
+        const T r = sqrt(dx * dx + dy * dy + dz * dz);
+        const T rho = r * ia;
+        T gam, dgam;                                   // gamma(rho), gamma'(rho)
+        if (rho < T(1)) {
+            const T r2 = rho * rho;
+            gam = T(GAMMA_C0) + T(GAMMA_C1) * r2 + T(GAMMA_C2) * r2 * r2;
+            dgam = T(2 * GAMMA_C1) * rho + T(4 * GAMMA_C2) * r2 * rho;
         } else {
-            gam = 1.0 / rho;
-            dgam = -1.0 / (rho * rho);
+            gam = T(1) / rho;
+            dgam = -gam * gam;
         }
-        const double sm = gam / A.a;                   // smooth part of 1/r
-        const double e = A.ke * q[a] * q[b] * sm;
-        dphi[a] -= A.ke * q[b] * sm;
-        dphi[b] -= A.ke * q[a] * sm;
-        de[a] -= 0.5 * e;
-        de[b] -= 0.5 * e;
+        const T sm = gam * ia;                         // smooth part of 1/r
+        const T e = ke * q[a] * q[b] * sm;
+        dphi[a] -= ke * q[b] * sm;
+        dphi[b] -= ke * q[a] * sm;
+        de[a] -= T(0.5) * e;
+        de[b] -= T(0.5) * e;
         // U_corr = -k_e q_a q_b gamma(r/a)/a  =>  F_a = k_e q_a q_b gamma'(r/a)/a^2 (r_a - r_b)/r
-        const double s = A.ke * q[a] * q[b] * dgam / (A.a * A.a * r);
+        const T s = ke * q[a] * q[b] * dgam * ia * ia / r;
         F[a][0] += s * dx; F[a][1] += s * dy; F[a][2] += s * dz;
         F[b][0] -= s * dx; F[b][1] -= s * dy; F[b][2] -= s * dz;
     }
@@ -62,23 +65,26 @@ __global__ void k_exclusions(const ExclArgs A)
         double v = 0;
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            if (A.forces) A.forces[3 * i + d] += F[a][d];
-            v += x[a][d] * F[a][d];
+            if (A.forces) A.forces[3 * i + d] += (double)F[a][d];
+            v += x[a][d] * (double)F[a][d];
         }
-        if (A.pot) A.pot[i] += dphi[a];
-        A.eatom[i] += de[a];
+        if (A.pot) A.pot[i] += (double)dphi[a];
+        A.eatom[i] += (double)de[a];
         A.vatom[i] += v;
     }
 }
 
+template <typename T>
 int launch_exclusions(const ExclArgs &a, cudaStream_t st)
 {
     if (a.n_mol <= 0) return MSM_OK;
-    k_exclusions<<<(a.n_mol + 127) / 128, 128, 0, st>>>(a);
+    k_exclusions<T><<<(a.n_mol + 127) / 128, 128, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
 }
+template int launch_exclusions<float>(const ExclArgs &, cudaStream_t);
+template int launch_exclusions<double>(const ExclArgs &, cudaStream_t);
 
 // ---------------------------------------------------------------- FP64 sums
 
@@ -145,12 +151,9 @@ int launch_sum(int m, int ncols, const double *const *cols, double *partials, do
 
 // --------------------------------------------------------- velocity Verlet
 
-// Units: a molecule (3 atoms, first n_mol units) or a single site.
-__device__ __forceinline__ void unit_atoms(int u, int n_mol, int &i0, int &na)
-{
-    if (u < n_mol) { i0 = 3 * u; na = 3; }
-    else { i0 = 3 * n_mol + (u - n_mol); na = 1; }
-}
+// Bond c of a triple joins atoms (0,1), (0,2), (1,2): compile-time tables.
+__device__ __forceinline__ constexpr int bond_i(int c) { return c == 2 ? 1 : 0; }
+__device__ __forceinline__ constexpr int bond_j(int c) { return c == 0 ? 1 : 2; }
 
 template <typename T>
 __global__ void k_vv_first(const VVArgs A)
@@ -158,63 +161,79 @@ __global__ void k_vv_first(const VVArgs A)
     const int units = A.n_mol + (A.n - 3 * A.n_mol);
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= units || failed(A.status)) return;
-    int i0, na;
-    unit_atoms(u, A.n_mol, i0, na);
     const double dt = A.dt;
+    if (u >= A.n_mol) {                                 // single site: half kick, drift
+        const int i = 3 * A.n_mol + (u - A.n_mol);
+        const double im = A.im[i];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double x = A.x[3 * i + d];
+            const double v = A.v[3 * i + d] + 0.5 * dt * A.f[3 * i + d] * im;
+            A.xo[3 * i + d] = x;
+            A.x[3 * i + d] = x + dt * v;
+            A.v[3 * i + d] = v;
+        }
+        return;
+    }
+    const int i0 = 3 * u;
     double xo[3][3], xn[3][3], v[3][3], im[3];
-    for (int a = 0; a < na; a++) {
-        const int i = i0 + a;
-        im[a] = 1.0 / A.m[i];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        im[a] = A.im[i0 + a];
+#pragma unroll
         for (int d = 0; d < 3; d++) {
-            xo[a][d] = A.x[3 * i + d];
-            v[a][d] = A.v[3 * i + d] + 0.5 * dt * A.f[3 * i + d] * im[a];     // half kick
-            xn[a][d] = xo[a][d] + dt * v[a][d];                               // drift
+            xo[a][d] = A.x[3 * (i0 + a) + d];
+            v[a][d] = A.v[3 * (i0 + a) + d] + 0.5 * dt * A.f[3 * (i0 + a) + d] * im[a];   // half kick
+            xn[a][d] = xo[a][d] + dt * v[a][d];                                         // drift
         }
     }
-    if (na == 3) {
-        // SHAKE in local coordinates (relative to the old O position), compute type T
-        T p[3][3], ro[3][3];
-        const int bi[3] = {0, 0, 1}, bj[3] = {1, 2, 2};
-        const T d2[3] = {(T)A.d_oh2, (T)A.d_oh2, (T)A.d_hh2};
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) p[a][d] = (T)(xn[a][d] - xo[0][d]);
-        for (int c = 0; c < 3; c++)
-            for (int d = 0; d < 3; d++) ro[c][d] = (T)(xo[bi[c]][d] - xo[bj[c]][d]);
-        T p0[3][3];
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) p0[a][d] = p[a][d];
-        bool ok = false;
-        for (int it = 0; it < A.max_iter && !ok; it++) {
-            ok = true;
-            for (int c = 0; c < 3; c++) {
-                const int a = bi[c], b = bj[c];
-                T rn[3], rn2 = 0, dot = 0;
-                for (int d = 0; d < 3; d++) { rn[d] = p[a][d] - p[b][d]; rn2 += rn[d] * rn[d]; }
-                const T diff = d2[c] - rn2;
-                if (fabs((double)diff) <= A.tol * (double)d2[c]) continue;
+    // SHAKE in local coordinates (relative to the old O position), compute type T
+    T p[3][3], p0[3][3], ro[3][3], w[3], d2[3];
+    d2[0] = d2[1] = (T)A.d_oh2;
+    d2[2] = (T)A.d_hh2;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        w[a] = (T)im[a];
+#pragma unroll
+        for (int d = 0; d < 3; d++) p0[a][d] = p[a][d] = (T)(xn[a][d] - xo[0][d]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) ro[c][d] = (T)(xo[bond_i(c)][d] - xo[bond_j(c)][d]);
+    const T tol = (T)A.tol;
+    bool ok = false;
+    for (int it = 0; it < A.max_iter && !ok; it++) {
+        ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int a = bond_i(c), b = bond_j(c);
+            T rn[3], rn2 = 0, dot = 0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) { rn[d] = p[a][d] - p[b][d]; rn2 += rn[d] * rn[d]; }
+            const T diff = d2[c] - rn2;
+            if (fabs(diff) > tol * d2[c]) {
                 ok = false;
+#pragma unroll
                 for (int d = 0; d < 3; d++) dot += ro[c][d] * rn[d];
-                const T wa = (T)im[a], wb = (T)im[b];
-                const T g = diff / (T(2) * dot * (wa + wb));
-                for (int d = 0; d < 3; d++) { p[a][d] += g * wa * ro[c][d]; p[b][d] -= g * wb * ro[c][d]; }
+                const T g = diff / (T(2) * dot * (w[a] + w[b]));
+#pragma unroll
+                for (int d = 0; d < 3; d++) { p[a][d] += g * w[a] * ro[c][d]; p[b][d] -= g * w[b] * ro[c][d]; }
             }
         }
-        if (!ok) set_status(A.status, MSM_ENOCONV);
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) {
-                const double dp = (double)(p[a][d] - p0[a][d]);
-                xn[a][d] = xn[a][d] + dp;
-                v[a][d] += dp / dt;
-            }
     }
-    for (int a = 0; a < na; a++) {
-        const int i = i0 + a;
+    if (!ok) set_status(A.status, MSM_ENOCONV);
+    const double inv_dt = 1.0 / dt;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
         for (int d = 0; d < 3; d++) {
+            const double dp = (double)(p[a][d] - p0[a][d]);
+            const int i = i0 + a;
             A.xo[3 * i + d] = xo[a][d];
-            A.x[3 * i + d] = xn[a][d];
-            A.v[3 * i + d] = v[a][d];
+            A.x[3 * i + d] = xn[a][d] + dp;
+            A.v[3 * i + d] = v[a][d] + dp * inv_dt;
         }
-    }
 }
 
 template <typename T>
@@ -223,53 +242,75 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
     const int units = A.n_mol + (A.n - 3 * A.n_mol);
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= units || failed(A.status)) return;
-    int i0, na;
-    unit_atoms(u, A.n_mol, i0, na);
-    const double dt = A.dt;
+    const double hdt = 0.5 * A.dt;
+    if (u >= A.n_mol) {
+        const int i = 3 * A.n_mol + (u - A.n_mol);
+        const double m = A.m[i], im = A.im[i];
+        double k2 = 0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double v = A.v[3 * i + d] + hdt * A.f[3 * i + d] * im;
+            A.v[3 * i + d] = v;
+            k2 += v * v;
+        }
+        if (kin) kin[i] = 0.5 * m * k2;
+        return;
+    }
+    const int i0 = 3 * u;
     double v[3][3], m[3];
-    for (int a = 0; a < na; a++) {
-        const int i = i0 + a;
-        m[a] = A.m[i];
-        for (int d = 0; d < 3; d++) v[a][d] = A.v[3 * i + d] + 0.5 * dt * A.f[3 * i + d] / m[a];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        m[a] = A.m[i0 + a];
+        const double im = A.im[i0 + a];
+#pragma unroll
+        for (int d = 0; d < 3; d++) v[a][d] = A.v[3 * (i0 + a) + d] + hdt * A.f[3 * (i0 + a) + d] * im;
     }
-    if (na == 3) {
-        // RATTLE velocity stage: zero the bond-parallel relative velocities
-        const int bi[3] = {0, 0, 1}, bj[3] = {1, 2, 2};
-        T r[3][3], w[3][3], r2[3];
+    // RATTLE velocity stage: zero the bond-parallel relative velocities
+    T r[3][3], r2[3], wv[3][3], w0[3][3], wm[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        r2[c] = 0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            r[c][d] = (T)(A.x[3 * (i0 + bond_i(c)) + d] - A.x[3 * (i0 + bond_j(c)) + d]);
+            r2[c] += r[c][d] * r[c][d];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        wm[a] = (T)A.im[i0 + a];
+#pragma unroll
+        for (int d = 0; d < 3; d++) w0[a][d] = wv[a][d] = (T)v[a][d];
+    }
+    const T tol = (T)A.tol_v;
+    bool ok = false;
+    for (int it = 0; it < A.max_iter && !ok; it++) {
+        ok = true;
+#pragma unroll
         for (int c = 0; c < 3; c++) {
-            r2[c] = 0;
-            for (int d = 0; d < 3; d++) {
-                r[c][d] = (T)(A.x[3 * (i0 + bi[c]) + d] - A.x[3 * (i0 + bj[c]) + d]);
-                r2[c] += r[c][d] * r[c][d];
-            }
-        }
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) w[a][d] = (T)v[a][d];
-        T w0[3][3];
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) w0[a][d] = w[a][d];
-        bool ok = false;
-        for (int it = 0; it < A.max_iter && !ok; it++) {
-            ok = true;
-            for (int c = 0; c < 3; c++) {
-                const int a = bi[c], b = bj[c];
-                T rv = 0;
-                for (int d = 0; d < 3; d++) rv += r[c][d] * (w[a][d] - w[b][d]);
-                if (fabs((double)rv) <= A.tol_v) continue;
+            const int a = bond_i(c), b = bond_j(c);
+            T rv = 0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) rv += r[c][d] * (wv[a][d] - wv[b][d]);
+            if (fabs(rv) > tol) {
                 ok = false;
-                const T wa = T(1) / (T)m[a], wb = T(1) / (T)m[b];
-                const T k = rv / (r2[c] * (wa + wb));
-                for (int d = 0; d < 3; d++) { w[a][d] -= k * wa * r[c][d]; w[b][d] += k * wb * r[c][d]; }
+                const T k = rv / (r2[c] * (wm[a] + wm[b]));
+#pragma unroll
+                for (int d = 0; d < 3; d++) { wv[a][d] -= k * wm[a] * r[c][d]; wv[b][d] += k * wm[b] * r[c][d]; }
             }
         }
-        if (!ok) set_status(A.status, MSM_ENOCONV);
-        for (int a = 0; a < 3; a++)
-            for (int d = 0; d < 3; d++) v[a][d] += (double)(w[a][d] - w0[a][d]);
     }
-    for (int a = 0; a < na; a++) {
+    if (!ok) set_status(A.status, MSM_ENOCONV);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
         const int i = i0 + a;
         double k2 = 0;
-        for (int d = 0; d < 3; d++) { A.v[3 * i + d] = v[a][d]; k2 += v[a][d] * v[a][d]; }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double vv = v[a][d] + (double)(wv[a][d] - w0[a][d]);
+            A.v[3 * i + d] = vv;
+            k2 += vv * vv;
+        }
         if (kin) kin[i] = 0.5 * m[a] * k2;
     }
 }
@@ -302,6 +343,21 @@ __global__ void k_kinetic(int n, const double *__restrict__ v, const double *__r
     if (i >= n) return;
     const double a = v[3 * i], b = v[3 * i + 1], c = v[3 * i + 2];
     kin[i] = 0.5 * m[i] * (a * a + b * b + c * c);
+}
+
+__global__ void k_inverse(int n, const double *__restrict__ m, double *__restrict__ im)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) im[i] = 1.0 / m[i];
+}
+
+int launch_inverse(int n, const double *m, double *im, cudaStream_t st)
+{
+    if (n <= 0) return MSM_OK;
+    k_inverse<<<(n + 255) / 256, 256, 0, st>>>(n, m, im);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
 }
 
 int launch_kinetic(const VVArgs &a, double *kin_atom, cudaStream_t st)

@@ -46,15 +46,46 @@ template <typename T> struct ShortArgs {
     T c0, c1, c2;          // gamma(r/a)/a = c0 + c1 r^2 + c2 r^4
     T d0, d1;              // -g*'(r)/r - 1/r^3 = d0 + d1 r^2
     T lj_s2, lj_4eps, lj_24eps, lj_shift;
-    vec4<T> *sr;           // sorted: (F_x, F_y, F_z, phi) of the g* sum, before k_e
-    vec4<T> *lj;           // sorted: (F_x, F_y, F_z, E) of the LJ sum (nullable)
+    const int *perm;       // sorted slot -> atom
+    vec4<T> *sr;           // by atom: (F_x, F_y, F_z, phi) of the g* sum, before k_e
+    vec4<T> *lj;           // by atom: (F_x, F_y, F_z, E) of the LJ sum (nullable)
     double *cnt;           // counting mode: per sorted atom, number of j with r_ij < a
+    const int *vl_ctl;     // Verlet-list flags (nullable): skip when the list path ran
     const int *status;
 };
 // model = true: skip pairs of the same molecule (their smooth part is removed by
 // the exclusion kernel) and add the LJ term between flagged sites.
 template <typename T> int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st);
 template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st);
+
+// ---- Verlet lists (k_list.cu) --------------------------------------------
+template <typename T> struct ListArgs {
+    CellGeom g;
+    int bd[3], nb[3];      // bricks of the short-range kernel
+    int ng[3], ngroups;    // groups of 1 x 2 x 2 bricks
+    int max_rows, jcap, cap;   // row slots per group, staged atoms per group, list entries per atom
+    T a2, rl2, rl_sel, skin_half2;
+    T c0, c1, c2, d0, d1;
+    T lj_s2, lj_4eps, lj_24eps, lj_shift;
+    bool model;
+    int n;
+    const double *x, *q;   // this step, original order
+    const int *perm, *start;
+    const vec4<T> *apos;
+    const int *aflag;
+    int *vl_perm, *vl_start;   // reference order of the last build
+    double *vl_xref;
+    vec4<T> *vl_pos;
+    int2 *grp_rows;
+    int *grp_nrows, *grp_j;
+    int *cnt, *cntlj;
+    uint16_t *nbr;         // n x cap
+    int *ctl;
+    vec4<T> *sr, *lj;      // outputs by atom
+    const int *status;
+};
+template <typename T> int launch_list_maintain(const ListArgs<T> &a, cudaStream_t st);
+template <typename T> int launch_list_force(const ListArgs<T> &a, cudaStream_t st);
 
 // ---- grids (k_grid.cu) -----------------------------------------------------
 template <typename T> struct AnterpArgs {
@@ -87,7 +118,7 @@ template <typename T> struct StencilArgs {
     T *ucut;               // concatenated, levels < nlev
     const int *status;
 };
-template <typename T> int launch_stencil(const StencilArgs<T> &a, cudaStream_t st);
+template <typename T> int launch_stencil(const StencilArgs<T> &a, int *tile_counter, cudaStream_t st);
 template <typename T> size_t stencil_smem_bytes(int rad);
 
 int launch_top_table(const LevelGeom &top, double a_top, double h_top, double *table, cudaStream_t st);
@@ -134,7 +165,7 @@ struct ExclArgs {
     double *forces, *pot, *eatom, *vatom;
     const int *status;
 };
-int launch_exclusions(const ExclArgs &a, cudaStream_t st);
+template <typename T> int launch_exclusions(const ExclArgs &a, cudaStream_t st);
 
 // Deterministic FP64 sum of m values per column (ncols arrays) into out[ncols].
 int launch_sum(int m, int ncols, const double *const *cols, double *partials, double *out, const int *status,
@@ -146,6 +177,7 @@ struct VVArgs {
     double *x, *v;
     double *xo;            // scratch: positions before the drift
     const double *f, *m;
+    const double *im;      // 1/m, computed once per md_run call
     double dt;
     double d_oh2, d_hh2;
     double tol;            // relative tolerance on squared bond lengths (SHAKE)
@@ -156,6 +188,7 @@ struct VVArgs {
 template <typename T> int launch_vv_first(const VVArgs &a, cudaStream_t st);
 template <typename T> int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st);
 int launch_kinetic(const VVArgs &a, double *kin_atom, cudaStream_t st);
+int launch_inverse(int n, const double *m, double *im, cudaStream_t st);
 
 int launch_parareal_update(int count, const double *f, const double *gnew, const double *gold, double *out,
                            const double *prev, double *dx_partials, cudaStream_t st);

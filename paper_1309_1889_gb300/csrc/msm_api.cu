@@ -2,6 +2,7 @@
 // handle and scratch management, geometry and table set-up, and the
 // orchestration of one MSM evaluation (Sec. 3, worked example steps 1-9),
 // of velocity Verlet (Sec. 2) and of parareal (Sec. 4).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -97,11 +98,11 @@ static bool on_device(const void *p)
 
 // Stages timed by the profiler (CUDA events around each stage's launches).
 enum Stage { ST_BIN, ST_SHORT, ST_ANTERP, ST_RESTRICT, ST_STENCIL, ST_TOP, ST_PROLONG, ST_INTERP, ST_SUMS,
-             ST_VV1, ST_VV2, N_STAGES };
+             ST_VV1, ST_VV2, ST_LIST, N_STAGES };
 static const char *kStageNames[N_STAGES] = {"bin_sort",      "short_range", "anterpolation",
                                             "restriction",   "lattice_cutoff", "top_level",
                                             "prolongation",  "interpolation", "exclusions_sums",
-                                            "vv_first_shake", "vv_second_rattle"};
+                                            "vv_first_shake", "vv_second_rattle", "verlet_list_maintenance"};
 
 struct Profiler {
     bool on = false;
@@ -134,9 +135,18 @@ struct msm_handle {
     DevBuf qgrid, ucut, ugrid, utop, ttop, wst_d, wst_t, rows;
     DevBuf eatom, vatom, kin, partials, sums, status;
     DevBuf in_pos, in_q, in_lj, out_f, out_p;          // staging of host arrays
-    DevBuf md_f, md_xo, md_x, md_v, md_q, md_m, md_lj, md_uk;
+    DevBuf md_f, md_xo, md_x, md_v, md_q, md_m, md_lj, md_uk, md_im;
     int *h_status = nullptr;
     double *h_scal = nullptr;
+    // Verlet lists (md_run with list_skin > 0)
+    bool list_on = false;
+    DevBuf vl_perm, vl_start, vl_xref, vl_pos, grp_rows, grp_nrows, grp_j, vl_cnt, vl_cntlj, vl_nbr, vl_ctl;
+    int vl_cap = 0, vl_jcap = 0, vl_rows = 0, vl_ngroups = 0;
+    int64_t vl_key_n = -1, vl_key_nmol = -1;
+    double vl_key_box[6] = {0, 0, 0, 0, 0, 0};
+    const void *vl_key_lj = nullptr;
+    int *h_ctl = nullptr;
+    int64_t vl_builds = 0, vl_overflows = 0, vl_seen[3] = {0, 0, 0};
 };
 
 static int prof_event(msm_handle *h, cudaStream_t st, int *idx)
@@ -202,6 +212,9 @@ extern "C" void msm_default_params(msm_params *p)
     p->lj_epsilon = 0.6364;
     p->d_oh = 0.09572;
     p->d_hh = 2.0 * 0.09572 * sin(104.52 * M_PI / 360.0);
+    p->wall_k = 0.0;
+    p->wall_width = 0.0;
+    p->list_skin = 0.0;
 }
 
 static int check_params(const msm_params *p)
@@ -215,6 +228,7 @@ static int check_params(const msm_params *p)
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
+    if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
     int rad = 0;
     while ((double)(rad + 1) * p->h < 2.0 * p->a) rad++;
     if (rad > 12) return fail_msg(MSM_EINVAL, "2a/h = %.3g is too large (lattice-cutoff radius %d > 12)", 2 * p->a / p->h, rad);
@@ -232,6 +246,7 @@ extern "C" int msm_create(const msm_params *p, msm_handle **out)
     h->precision = p->precision;
     cudaError_t e = cudaMallocHost(&h->h_status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_scal, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(int) * 8);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -249,11 +264,14 @@ extern "C" void msm_destroy(msm_handle *h)
                      &h->akey, &h->aflag, &h->sr, &h->lj, &h->qgrid, &h->ucut, &h->ugrid, &h->utop, &h->ttop,
                      &h->wst_d, &h->wst_t, &h->rows, &h->eatom, &h->vatom, &h->kin, &h->partials, &h->sums,
                      &h->status, &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
-                     &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk};
+                     &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk, &h->md_im,
+                     &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->grp_rows, &h->grp_nrows,
+                     &h->grp_j, &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_ctl};
     for (DevBuf *b : all) release(*b);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
     delete h;
 }
 
@@ -435,8 +453,37 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     const double sa6 = pow(sg2 / (a * a), 3.0);
     s.lj_s2 = (T)sg2; s.lj_4eps = (T)(4.0 * h->p.lj_epsilon); s.lj_24eps = (T)(24.0 * h->p.lj_epsilon);
     s.lj_shift = (T)(4.0 * h->p.lj_epsilon * (sa6 * sa6 - sa6));
+    s.perm = h->perm.as<int>();
     s.sr = h->sr.as<vec4<T>>(); s.lj = model ? h->lj.as<vec4<T>>() : nullptr; s.cnt = nullptr; s.status = status;
-    { PROF(ST_SHORT); TRY(launch_short<T>(s, model, st)); }
+    s.vl_ctl = h->list_on ? h->vl_ctl.as<int>() : nullptr;
+    {
+        ListArgs<T> la;
+        if (h->list_on) {
+            la.g = h->cg;
+            for (int d = 0; d < 3; d++) { la.bd[d] = h->bd[d]; la.nb[d] = h->nb[d]; }
+            la.ng[0] = h->nb[0]; la.ng[1] = (h->nb[1] + 1) / 2; la.ng[2] = (h->nb[2] + 1) / 2;
+            la.ngroups = h->vl_ngroups;
+            la.max_rows = h->vl_rows; la.jcap = h->vl_jcap; la.cap = h->vl_cap;
+            const double rl = a + h->p.list_skin;
+            la.a2 = s.a2; la.rl2 = (T)(rl * rl); la.rl_sel = (T)(rl + 1e-3 * h->p.h);
+            la.skin_half2 = (T)(0.25 * h->p.list_skin * h->p.list_skin);
+            la.c0 = s.c0; la.c1 = s.c1; la.c2 = s.c2; la.d0 = s.d0; la.d1 = s.d1;
+            la.lj_s2 = s.lj_s2; la.lj_4eps = s.lj_4eps; la.lj_24eps = s.lj_24eps; la.lj_shift = s.lj_shift;
+            la.model = model; la.n = n; la.x = io.pos; la.q = io.q;
+            la.perm = h->perm.as<int>(); la.start = h->start.as<int>(); la.apos = h->apos.as<vec4<T>>();
+            la.aflag = h->aflag.as<int>();
+            la.vl_perm = h->vl_perm.as<int>(); la.vl_start = h->vl_start.as<int>(); la.vl_xref = h->vl_xref.as<double>();
+            la.vl_pos = h->vl_pos.as<vec4<T>>(); la.grp_rows = h->grp_rows.as<int2>();
+            la.grp_nrows = h->grp_nrows.as<int>(); la.grp_j = h->grp_j.as<int>();
+            la.cnt = h->vl_cnt.as<int>(); la.cntlj = h->vl_cntlj.as<int>(); la.nbr = h->vl_nbr.as<uint16_t>();
+            la.ctl = h->vl_ctl.as<int>(); la.sr = s.sr; la.lj = s.lj; la.status = status;
+            PROF(ST_LIST);
+            TRY(launch_list_maintain<T>(la, st));
+        }
+        PROF(ST_SHORT);
+        if (h->list_on) TRY(launch_list_force<T>(la, st));
+        TRY(launch_short<T>(s, model, st));
+    }
 
     // step 2: anterpolation
     T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
@@ -461,24 +508,25 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         }
         sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
         PROF(ST_STENCIL);
-        TRY(launch_stencil<T>(sa, st));
+        TRY(launch_stencil<T>(sa, h->status.as<int>() + 2, st));
     }
     // step 5: top level in FP64
     const LevelGeom &top = h->gg.L[l - 1];
     { PROF(ST_TOP); TRY(launch_top<T>(top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
     // steps 6-7: prolongation back to level 0
-    PROF(ST_PROLONG);
-    if (l == 1) {
-        const int m = top.n[0] * top.n[1] * top.n[2];
-        if (sizeof(T) == sizeof(float)) TRY(launch_cast_f64(m, h->utop.as<double>(), reinterpret_cast<float *>(ug), st));
-        else CUDA_TRY(cudaMemcpyAsync(ug, h->utop.p, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-    } else {
-        TRY((launch_prolong<T, double>(h->gg.L[l - 2], top, uc, h->utop.as<double>(), ug, status, st)));
-        for (int k = l - 3; k >= 0; k--)
-            TRY((launch_prolong<T, T>(h->gg.L[k], h->gg.L[k + 1], uc, ug + h->gg.L[k + 1].off, ug, status, st)));
+    {
+        PROF(ST_PROLONG);
+        if (l == 1) {
+            const int m = top.n[0] * top.n[1] * top.n[2];
+            if (sizeof(T) == sizeof(float)) TRY(launch_cast_f64(m, h->utop.as<double>(), reinterpret_cast<float *>(ug), st));
+            else CUDA_TRY(cudaMemcpyAsync(ug, h->utop.p, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+        } else {
+            TRY((launch_prolong<T, double>(h->gg.L[l - 2], top, uc, h->utop.as<double>(), ug, status, st)));
+            for (int k = l - 3; k >= 0; k--)
+                TRY((launch_prolong<T, T>(h->gg.L[k], h->gg.L[k + 1], uc, ug + h->gg.L[k + 1].off, ug, status, st)));
+        }
     }
     // step 8-9: interpolation, totals, scatter to the caller's order
-    ProfScope ps_interp(h, ST_INTERP, st);
     InterpArgs<T> ia;
     ia.n = n; ia.cg = h->cg; ia.L0 = h->gg.L[0]; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
     ia.afrac = h->afrac.as<vec4<T>>(); ia.sr = h->sr.as<vec4<T>>(); ia.lj = model ? h->lj.as<vec4<T>>() : nullptr;
@@ -487,14 +535,14 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     ia.wall_k = model ? h->p.wall_k : 0.0; ia.wall_w = h->p.wall_width;
     ia.forces = io.forces; ia.pot = io.pot; ia.eatom = h->eatom.as<double>(); ia.vatom = h->vatom.as<double>();
     ia.status = status;
-    TRY(launch_interp<T>(ia, st));
-    ProfScope ps_sums(h, ST_SUMS, st);
+    { PROF(ST_INTERP); TRY(launch_interp<T>(ia, st)); }
+    PROF(ST_SUMS);
     if (h->p.model == MSM_MODEL_WATER && io.n_mol > 0) {
         ExclArgs ex;
         ex.n_mol = (int)io.n_mol; ex.x = io.pos; ex.q = io.q; ex.ke = h->p.coulomb_k; ex.a = h->p.a;
         ex.forces = io.forces; ex.pot = io.pot; ex.eatom = h->eatom.as<double>(); ex.vatom = h->vatom.as<double>();
         ex.status = status;
-        TRY(launch_exclusions(ex, st));
+        TRY(launch_exclusions<T>(ex, st));
     }
     const double *cols[2] = {h->eatom.as<double>(), h->vatom.as<double>()};
     TRY(launch_sum(n, 2, cols, h->partials.as<double>(), h->sums.as<double>(), status, st));
@@ -515,12 +563,22 @@ static int evaluate(msm_handle *h, const EvalIO &io, const double box[6], cudaSt
     return evaluate_t<double>(h, io, st);
 }
 
+static int list_grow(msm_handle *h, cudaStream_t st);
+
 // Copy the device status word to the host, synchronise, translate.
 static int finish(msm_handle *h, cudaStream_t st)
 {
     CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (h->vl_ctl.p) CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->vl_ctl.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     prof_resolve(h);
+    if (h->vl_ctl.p) {
+        h->vl_builds += h->h_ctl[7];
+        h->vl_overflows += h->h_ctl[1] ? 1 : 0;
+        for (int k = 4; k <= 6; k++) h->vl_seen[k - 4] = std::max(h->vl_seen[k - 4], (int64_t)h->h_ctl[k]);
+        if (h->h_ctl[7]) CUDA_TRY(cudaMemsetAsync(h->vl_ctl.as<int>() + 7, 0, sizeof(int), st));
+        if (h->h_ctl[1]) TRY(list_grow(h, st));
+    }
     const int s = h->h_status[0];
     if (s != 0) return fail_msg(s, "%s", status_text(s));
     return MSM_OK;
@@ -620,6 +678,79 @@ struct SysDev {
     double energy = 0;
 };
 
+// ------------------------------------------------------------ Verlet lists
+
+static int list_alloc(msm_handle *h, int64_t n, size_t vsz)
+{
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    TRY(ensure(h->vl_perm, sizeof(int) * nn));
+    TRY(ensure(h->vl_start, sizeof(int) * ((size_t)h->cg.ncells + 1)));
+    TRY(ensure(h->vl_xref, sizeof(double) * 3 * nn));
+    TRY(ensure(h->vl_pos, vsz * nn));
+    TRY(ensure(h->grp_rows, sizeof(int2) * (size_t)h->vl_ngroups * h->vl_rows));
+    TRY(ensure(h->grp_nrows, sizeof(int) * (size_t)h->vl_ngroups));
+    TRY(ensure(h->grp_j, sizeof(int) * (size_t)h->vl_ngroups));
+    TRY(ensure(h->vl_cnt, sizeof(int) * nn));
+    TRY(ensure(h->vl_cntlj, sizeof(int) * nn));
+    TRY(ensure(h->vl_nbr, sizeof(uint16_t) * nn * (size_t)h->vl_cap));
+    TRY(ensure(h->vl_ctl, sizeof(int) * 8));
+    return MSM_OK;
+}
+
+// Size the lists for the system and invalidate them when the system changed or
+// the call does not continue a trajectory (fresh): md_run's results then depend
+// only on its inputs, never on what the handle ran before.
+template <typename T>
+static int list_setup(msm_handle *h, const SysDev &s, bool fresh, cudaStream_t st)
+{
+    TRY(set_geometry(h, s.box, st));
+    choose_bricks(h, s.n);
+    const double rl = h->p.a + h->p.list_skin, hh = h->p.h;
+    const int R = (int)ceil((rl + 1e-3 * hh) / hh) + 1;
+    const int rows = (2 * h->bd[1] + 2 * R + 1) * (2 * h->bd[2] + 2 * R + 1);
+    const int ngroups = h->nb[0] * ((h->nb[1] + 1) / 2) * ((h->nb[2] + 1) / 2);
+    const bool changed = s.n != h->vl_key_n || s.n_mol != h->vl_key_nmol || s.lj != h->vl_key_lj ||
+                         memcmp(s.box, h->vl_key_box, sizeof h->vl_key_box) != 0 || rows > h->vl_rows ||
+                         ngroups != h->vl_ngroups;
+    if (!changed && !fresh && h->vl_ctl.p) return MSM_OK;
+    if (h->vl_cap == 0) {
+        // entries per atom: pairs within a + skin at 1.8x the box's mean density, at least 256
+        double vol = s.box[3] * s.box[4] * s.box[5];
+        const double dens = (double)s.n / vol;
+        const double want = 1.8 * dens * 4.18879020478639 * rl * rl * rl + 32.0;
+        h->vl_cap = ((std::max(256, (int)want) + 7) / 8) * 8;
+        h->vl_jcap = sizeof(T) == 4 ? 4608 : 4608;
+    }
+    h->vl_rows = std::max(h->vl_rows, rows);
+    h->vl_ngroups = ngroups;
+    TRY(list_alloc(h, s.n, sizeof(vec4<T>)));
+    CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
+    const int invalid = 1;
+    CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));                    // 'invalid' lives on the host stack
+    h->vl_key_n = s.n; h->vl_key_nmol = s.n_mol; h->vl_key_lj = s.lj;
+    memcpy(h->vl_key_box, s.box, sizeof h->vl_key_box);
+    return MSM_OK;
+}
+
+// After an overflow: grow the exceeded capacity, invalidate, resume with lists next time.
+static int list_grow(msm_handle *h, cudaStream_t st)
+{
+    const int *c = h->h_ctl;
+    const size_t vsz = h->precision == MSM_FP32 ? sizeof(vec4<float>) : sizeof(vec4<double>);
+    const int max_jcap = h->precision == MSM_FP32 ? 10240 : 5120;   // shared memory of one CTA
+    if (c[4] + 16 > h->vl_cap) h->vl_cap = (((int)(1.25 * c[4]) + 32 + 7) / 8) * 8;
+    if (c[5] > h->vl_jcap) h->vl_jcap = std::min(max_jcap, (((int)(1.2 * c[5]) + 64) + 7) / 8 * 8);
+    if (c[6] > h->vl_rows) h->vl_rows = c[6] + 16;
+    if (c[5] > max_jcap) h->p.list_skin = 0.0;              // too dense for staged lists: cell search only
+    TRY(list_alloc(h, h->vl_key_n, vsz));
+    CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
+    const int invalid = 1;
+    CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MSM_OK;
+}
+
 template <typename T> static double shake_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-12; }
 template <typename T> static double rattle_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-14; }
 
@@ -637,9 +768,13 @@ static int run_md_t(msm_handle *h, const SysDev &s, double dt, int n_steps, doub
     io.pot = nullptr;
     VVArgs va;
     va.n = (int)s.n; va.n_mol = (int)s.n_mol; va.x = s.x; va.v = s.v; va.xo = h->md_xo.as<double>();
-    va.f = io.forces; va.m = s.m; va.dt = dt;
+    TRY(ensure(h->md_im, sizeof(double) * nn));
+    TRY(launch_inverse(int(s.n), s.m, h->md_im.as<double>(), st));
+    va.f = io.forces; va.m = s.m; va.im = h->md_im.as<double>(); va.dt = dt;
     va.d_oh2 = h->p.d_oh * h->p.d_oh; va.d_hh2 = h->p.d_hh * h->p.d_hh;
     va.tol = shake_tol<T>(); va.tol_v = rattle_tol<T>(); va.max_iter = sizeof(T) == 4 ? 200 : 1000;
+    h->list_on = false;
+    if (h->p.list_skin > 0 && s.n > 0) TRY(list_setup<T>(h, s, !(s.f && s.f_valid), st));
     if (s.f && s.f_valid) {
         // forces and energy of the start positions come with the system
         TRY(set_geometry(h, s.box, st));
@@ -659,9 +794,11 @@ static int run_md_t(msm_handle *h, const SysDev &s, double dt, int n_steps, doub
         const double *cols[1] = {h->kin.as<double>()};
         TRY(launch_sum((int)s.n, 1, cols, h->partials.as<double>(), uk + 1, va.status, st));
     }
+    h->list_on = h->vl_ctl.p != nullptr && h->p.list_skin > 0 && s.n > 0;
     for (int step = 0; step < n_steps; step++) {
         { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
-        TRY(evaluate_t<T>(h, io, st));
+        int rc = evaluate_t<T>(h, io, st);
+        if (rc) { h->list_on = false; return rc; }
         { PROF(ST_VV2); TRY(launch_vv_second<T>(va, uk ? h->kin.as<double>() : nullptr, st)); }
         if (uk) {
             CUDA_TRY(cudaMemcpyAsync(uk + 2 * (step + 1), h->sums.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -669,6 +806,7 @@ static int run_md_t(msm_handle *h, const SysDev &s, double dt, int n_steps, doub
             TRY(launch_sum((int)s.n, 1, cols, h->partials.as<double>(), uk + 2 * (step + 1) + 1, va.status, st));
         }
     }
+    h->list_on = false;
     return MSM_OK;
 }
 
@@ -771,6 +909,7 @@ static int count_pairs_t(msm_handle *h, int64_t *out)
     s.start = h->start.as<int>(); s.apos = h->apos.as<vec4<T>>(); s.aflag = h->aflag.as<int>();
     const double a = h->p.a;
     s.a = (T)a; s.a2 = (T)(a * a); s.a_sel = (T)(a + 1e-3 * h->p.h);
+    s.perm = h->perm.as<int>(); s.vl_ctl = nullptr;
     s.sr = nullptr; s.lj = nullptr; s.cnt = h->eatom.as<double>(); s.status = h->status.as<int>();
     CUDA_TRY(cudaMemsetAsync(h->eatom.p, 0, sizeof(double) * (size_t)(h->last_n > 0 ? h->last_n : 1), st));
     TRY(launch_count_pairs<T>(s, st));
@@ -977,11 +1116,19 @@ extern "C" int msm_stage_atoms(msm_handle *h, int32_t which, double *out, int64_
         CUDA_TRY(cudaMemcpy(t.data(), h->sr.p, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < t.size(); i++) sr[i] = t[i];
     }
-    for (int64_t s = 0; s < n; s++) {
-        const int i = perm[(size_t)s];
-        if (which == 0) out[i] = sr[4 * s + 3];
-        else for (int d = 0; d < 3; d++) out[3 * i + d] = sr[4 * s + d];
+    for (int64_t i = 0; i < n; i++) {                      // stored by atom index
+        if (which == 0) out[i] = sr[4 * i + 3];
+        else for (int d = 0; d < 3; d++) out[3 * i + d] = sr[4 * i + d];
     }
+    return MSM_OK;
+}
+
+extern "C" int msm_list_stats(msm_handle *h, int64_t *out, int32_t max)
+{
+    if (!h || !out) return fail_msg(MSM_EINVAL, "NULL argument");
+    const int64_t v[8] = {h->vl_builds, h->vl_overflows, h->vl_cap, h->vl_jcap, h->vl_rows,
+                          h->vl_seen[0], h->vl_seen[1], h->vl_seen[2]};
+    for (int k = 0; k < 8 && k < max; k++) out[k] = v[k];
     return MSM_OK;
 }
 

@@ -172,3 +172,19 @@ def test_parareal_converges_to_tolerance(api, torch, pr_sys):
     assert conv and dx <= 1e-6 and it <= 6
     fx, _ = _serial(api, torch, s, FINE, "fp32", 6)
     assert np.abs(xs - fx).max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_verlet_lists_equal_cell_search(api, torch, prec, tol):
+    """md_run with Verlet lists (skin 0.1 nm, rebuilt when an atom moved more than
+    skin/2) follows the every-step cell search to rounding: both sum exactly the
+    pairs within a."""
+    s = inputs.water_box(3000, 3.1, margin=1.0, seed=7, vel_seed=8)
+    out = {}
+    for skin in (0.0, 0.1):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water", list_skin=skin, wall_k=1e4, wall_width=0.8)
+        d = _dev_sys(torch, s)
+        uk = m.md_run(d, dt=0.002, n_steps=30).cpu().numpy()
+        out[skin] = (d.pos.cpu().numpy(), uk)
+    assert np.abs(out[0.0][0] - out[0.1][0]).max() <= tol
+    assert np.abs(out[0.0][1] - out[0.1][1]).max() <= 10 * tol * np.abs(out[0.0][1]).max()
