@@ -57,6 +57,10 @@ extern "C" {
 #define MSM_MODEL_CHARGES 0  /* bare point charges: the paper's Coulomb sum     */
 #define MSM_MODEL_WATER   1  /* + rigid 3-site water completion (see msm_system) */
 
+#define MSM_FLAG_GRAPHS   1  /* md_run: steps after the first replay one captured CUDA graph */
+#define MSM_FLAG_AUTOTUNE 2  /* time the short-range brick shapes on the first evaluation of
+                                each single-system geometry and keep the fastest           */
+
 /* Method parameters (Sec. 3).
  *   a          cutoff of the short-range part g* (nm); the level-k lattice
  *              cutoff is 2^{k+1} a (eq. split and the g^k definitions)
@@ -73,6 +77,11 @@ extern "C" {
  *              keeps atoms inside the open domain; an atom closer than
  *              wall_width to a box face feels 1/2 wall_k (wall_width - d)^2
  *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)
+ *   flags      MSM_FLAG_* bits (default: both).  Neither changes a result bit:
+ *              a graph replays exactly the launches of an eager step, and the
+ *              short-range sum adds each atom's neighbours in ascending sorted
+ *              order whatever the brick shape.  Graphs are not used while the
+ *              profiler is on.
  *   list_skin  md_run only: Verlet-list skin (nm) of the short-range sum;
  *              lists hold pairs within a + list_skin and are rebuilt when an
  *              atom has moved more than list_skin/2 (0 = cell search every
@@ -86,7 +95,7 @@ typedef struct msm_params {
     int32_t gamma_kind;
     int32_t basis_kind;
     int32_t model;
-    int32_t reserved0;
+    int32_t flags;
     double  lj_sigma;
     double  lj_epsilon;
     double  d_oh;
@@ -122,8 +131,8 @@ typedef struct msm_system {
 typedef struct msm_handle msm_handle;
 
 /* Fill *p with the defaults: a = 1.2, h = 0.25, 3 levels, FP32, k_e, C^2
- * gamma, cubic Phi, point charges, TIP3P-like O-O LJ and geometry, no wall,
- * Verlet-list skin 0.1 nm. */
+ * gamma, cubic Phi, point charges, graphs and autotuning on, TIP3P-like O-O
+ * LJ and geometry, no wall, no Verlet lists (skin 0). */
 MSM_API void msm_default_params(msm_params *p);
 
 /* Create a handle (validates *p; allocates nothing on the device until the
@@ -148,10 +157,14 @@ MSM_API int  msm_energy_forces(msm_handle *h, int64_t n, const double *pos, cons
                        double *potentials, double *virial, void *stream);
 
 /* Same evaluation for independent systems of uneven sizes in one call:
- * system s owns atoms offsets[s] .. offsets[s+1]-1 (host array of n_sys+1)
- * and box boxes[6*s .. 6*s+5] (host).  energies[n_sys]; other arrays are
- * concatenated per atom.  Each system is evaluated exactly as by
- * msm_energy_forces. */
+ * system s owns atoms offsets[s] .. offsets[s+1]-1 (host array of n_sys+1,
+ * offsets[0] = 0) and box boxes[6*s .. 6*s+5] (host).  energies[n_sys]
+ * (device or host); other arrays are concatenated per atom.  All systems go
+ * through the same launches (one per stage for the whole batch; the
+ * per-system geometry sits in a device table), and each system's results are
+ * bitwise those of msm_energy_forces on it alone.  The paper runs its
+ * independent fine propagators in parallel (Sec. 4); a batch is the GPU form
+ * of that. */
 MSM_API int  msm_energy_forces_batched(msm_handle *h, int32_t n_sys, const int64_t *offsets,
                                const double *pos, const double *q, const double *boxes,
                                double *energies, double *forces, double *potentials,
@@ -167,10 +180,32 @@ MSM_API int  msm_system_forces(msm_handle *h, const msm_system *sys, double *ene
  * SHAKE/RATTLE for the rigid triples: n_steps steps of length dt (ps) on
  * sys->x, sys->v (device, updated in place).  uk (nullable, device or
  * host) receives (U, K) before the first step and after every step:
- * 2*(n_steps+1) values.  Errors as above plus MSM_ENOCONV (constraints). */
+ * 2*(n_steps+1) values.  With MSM_FLAG_GRAPHS the first step is launched
+ * kernel by kernel and the others replay a CUDA graph of one step (captured
+ * on a private stream, launched on the caller's).  Errors as above plus
+ * MSM_ENOCONV (constraints). */
 MSM_API int  md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps, double *uk, void *stream);
 
+/* Energies and forces of n_sys independent msm_systems (uneven sizes and
+ * boxes) in one batched evaluation under the handle's model: x, q, lj of each
+ * system are gathered (device or host), forces go to systems[s].f (nullable;
+ * f_valid and energy are then set), energies[n_sys] (host, nullable).  Each
+ * system's results equal msm_system_forces on it alone, bit for bit. */
+MSM_API int  msm_system_forces_batched(msm_handle *h, int32_t n_sys, msm_system *systems, double *energies,
+                                       void *stream);
+
+/* md_run for n_sys independent systems stepped together: every stage of
+ * every step is one launch for the whole batch.  x, v (and f when non-NULL)
+ * of each system are updated in place; forces are carried in only if every
+ * system has f with f_valid = 1.  uk (nullable, device or host) receives
+ * n_sys blocks of 2*(n_steps+1) values, system s first.  Each system's
+ * trajectory equals md_run on it alone, bit for bit. */
+MSM_API int  md_run_batched(msm_handle *h, int32_t n_sys, msm_system *systems, double dt, int32_t n_steps,
+                            double *uk, void *stream);
+
 /* Parareal (Sec. 4): lambda^{k+1}_{n+1} = G(lambda^{k+1}_n) + F(lambda^k_n) - G(lambda^k_n),
+ * the fine propagations F of one iteration run as one batch (md_run_batched
+ * over the slices not yet exact), G sequentially;
  * evaluated as F + (G_new - G_old) in FP64; F and G are md_run with their own
  * parameters, time steps and step counts (dtG*stepsG must equal dtF*stepsF).
  * state0 gives the system and lambda_0 = (x, v).  slices_x/slices_v

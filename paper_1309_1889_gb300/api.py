@@ -21,6 +21,7 @@ LIB_PATH = PKG / "libmsm_gb300.so"
 KE = 138.935458
 FP64, FP32 = 0, 1
 MODEL_CHARGES, MODEL_WATER = 0, 1
+FLAG_GRAPHS, FLAG_AUTOTUNE = 1, 2
 CODES = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOCONV"}
 
 
@@ -34,7 +35,7 @@ class MSMError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("a", C.c_double), ("h", C.c_double), ("n_levels", C.c_int32), ("precision", C.c_int32),
                 ("coulomb_k", C.c_double), ("gamma_kind", C.c_int32), ("basis_kind", C.c_int32),
-                ("model", C.c_int32), ("reserved0", C.c_int32), ("lj_sigma", C.c_double),
+                ("model", C.c_int32), ("flags", C.c_int32), ("lj_sigma", C.c_double),
                 ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double),
                 ("wall_k", C.c_double), ("wall_width", C.c_double), ("list_skin", C.c_double)]
 
@@ -49,7 +50,8 @@ _lib = None
 EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces", "msm_energy_forces_batched",
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
-           "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats")
+           "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats",
+           "msm_system_forces_batched", "md_run_batched")
 
 
 def lib():
@@ -69,6 +71,9 @@ def lib():
         L.msm_energy_forces_batched.restype = C.c_int
         L.msm_system_forces.argtypes = [p, P(SystemC), p, p, p, p]; L.msm_system_forces.restype = C.c_int
         L.md_run.argtypes = [p, P(SystemC), d, i32, p, p]; L.md_run.restype = C.c_int
+        L.msm_system_forces_batched.argtypes = [p, i32, P(SystemC), p, p]
+        L.msm_system_forces_batched.restype = C.c_int
+        L.md_run_batched.argtypes = [p, i32, P(SystemC), d, i32, p, p]; L.md_run_batched.restype = C.c_int
         L.parareal_run.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, d, p, p,
                                    P(i32), P(d), p]
         L.parareal_run.restype = C.c_int
@@ -147,7 +152,7 @@ def _box(box):
 
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
                 lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
-                list_skin=0.0) -> Params:
+                list_skin=0.0, graphs=True, autotune=True) -> Params:
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -159,6 +164,7 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
     p.d_hh = float(d_hh) if d_hh is not None else 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
     p.wall_k, p.wall_width = float(wall_k), float(wall_width)
     p.list_skin = float(list_skin)
+    p.flags = (FLAG_GRAPHS if graphs else 0) | (FLAG_AUTOTUNE if autotune else 0)
     return p
 
 
@@ -265,6 +271,49 @@ class MSM:
             sys.energy = float(s.energy)
         return uk
 
+    def system_forces_batched(self, systems, stream=None):
+        """Energies (list) and forces of independent System-like objects in one batched
+        evaluation; each system needs a `force` array/tensor (n, 3) to receive F."""
+        arr = (SystemC * len(systems))()
+        keep = []
+        for b, sy in enumerate(systems):
+            s, k = _system_struct(sy)
+            arr[b] = s
+            keep.append((s, k))
+        e = np.zeros(len(systems))
+        _check(lib().msm_system_forces_batched(self._h, len(systems), arr, _ptr(e), _stream(stream)))
+        for b, sy in enumerate(systems):
+            if arr[b].f:
+                sy.force_valid = int(arr[b].f_valid)
+                sy.energy = float(arr[b].energy)
+        return e
+
+    def md_run_batched(self, systems, dt, n_steps, record=True, stream=None):
+        """md_run for independent systems stepped together (one launch per stage for all).
+
+        Advances every system's pos / vel in place; returns (U, K) per system and
+        step, shape (n_sys, n_steps+1, 2), or None."""
+        arr = (SystemC * len(systems))()
+        keep = []
+        for b, sy in enumerate(systems):
+            s, k = _system_struct(sy, need_v=True)
+            arr[b] = s
+            keep.append((s, k))
+        dev = _is_tensor(systems[0].pos) and systems[0].pos.is_cuda
+        uk = None
+        if record:
+            if dev:
+                uk = _torch().empty((len(systems), n_steps + 1, 2), dtype=_torch().float64,
+                                    device=systems[0].pos.device)
+            else:
+                uk = np.zeros((len(systems), n_steps + 1, 2))
+        _check(lib().md_run_batched(self._h, len(systems), arr, float(dt), int(n_steps), _ptr(uk), _stream(stream)))
+        for b, sy in enumerate(systems):
+            if arr[b].f:
+                sy.force_valid = int(arr[b].f_valid)
+                sy.energy = float(arr[b].energy)
+        return uk
+
     # -- profiling ------------------------------------------------------------
     def profile(self, on=True):
         _check(lib().msm_profile_enable(self._h, 1 if on else 0))
@@ -365,12 +414,12 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
     """Parareal over md_run: G and F are dict(a, h, levels, dt, steps).
 
     Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
-    pg = make_params(G["a"], G["h"], G["levels"], G.get("precision", precision), model,
-                     wall_k=G.get("wall_k", 0.0), wall_width=G.get("wall_width", 0.0),
-                     list_skin=G.get("list_skin", 0.0))
-    pf = make_params(F["a"], F["h"], F["levels"], F.get("precision", precision), model,
-                     wall_k=F.get("wall_k", 0.0), wall_width=F.get("wall_width", 0.0),
-                     list_skin=F.get("list_skin", 0.0))
+    def params(P):
+        return make_params(P["a"], P["h"], P["levels"], P.get("precision", precision), model,
+                           wall_k=P.get("wall_k", 0.0), wall_width=P.get("wall_width", 0.0),
+                           list_skin=P.get("list_skin", 0.0), graphs=P.get("graphs", True),
+                           autotune=P.get("autotune", True))
+    pg, pf = params(G), params(F)
     s, keep = _system_struct(sys, need_v=True)
     n = int(s.n)
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))

@@ -45,6 +45,28 @@ struct GridGeom {
     int       total;    // points over all levels
 };
 
+// One system of a batch.  A batch is B independent systems evaluated by the
+// same launches: their atoms, sorted slots, cells and grid points are
+// concatenated, and every kernel finds its system's geometry here (the
+// system index is blockIdx.y, or the owner of a tile of a persistent
+// launch).  A single system is the batch B = 1.  Nothing in a system's
+// arithmetic depends on the other systems, so each result equals the
+// result of evaluating that system alone, bit for bit.
+struct SysDesc {
+    CellGeom g;         // finest cells of this system
+    GridGeom gg;        // its levels; LevelGeom::off counts from grid_off
+    double inv_h;       // 1/h rounded once (the binning contract)
+    double box_lo[3], box_hi[3];
+    int atom_off, n;    // atoms, and sorted slots, [atom_off, atom_off + n)
+    int n_mol;          // leading rigid (O, H, H) triples of the system
+    int cell_off;       // global id of its first cell (cell_start index)
+    int bd[3], nb[3], nbricks;   // short-range bricks: edge in cells, count per axis
+    int grid_off;       // first point of its grids in the concatenated grid buffers
+    int top_off;        // first point of its top level in the FP64 top buffer
+    int ttab_off;       // first entry of its top-level Toeplitz table
+    int part_off;       // first block of its FP64 sum partials
+};
+
 // 1-D cubic C1 numerical-Hermite weights of an atom whose fractional
 // coordinate within its finest cell is f in [0, 1): weights of grid points
 // c-1, c, c+1, c+2 (c = the atom's cell), i.e. Phi(f+1), Phi(f), Phi(f-1),

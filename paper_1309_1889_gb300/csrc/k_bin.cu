@@ -14,17 +14,25 @@
 //   k_sort_cells   each cell's slots reordered by atom index: the result is the
 //                  unique stable order (key, index), whatever the atomics did
 //   k_gather       sorted copies of position, fraction, key and (molecule, LJ) flag
+//
+// A batch of systems is binned by one pass of each kernel: a system's cell ids
+// are offset by the cells of the systems before it, so the one global stable
+// sort leaves each system's atoms in a contiguous slot range, ordered exactly
+// as a sort of that system alone.
 #include "kernels.cuh"
 
 namespace msm {
 
 template <typename T>
-__global__ void k_bin_keys(int n, const double *__restrict__ pos, const double *__restrict__ q, CellGeom g,
-                           double inv_h, int *__restrict__ key, int *__restrict__ count, vec4<T> *__restrict__ rel,
+__global__ void k_bin_keys(const Batch bt, const double *__restrict__ pos, const double *__restrict__ q,
+                           int *__restrict__ key, int *__restrict__ count, vec4<T> *__restrict__ rel,
                            vec4<T> *__restrict__ frac, int *__restrict__ status)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= D.n) return;
+    const int i = D.atom_off + li;
+    const CellGeom &g = D.g;
     int c[3];
     double r[3], f[3];
 #pragma unroll
@@ -32,14 +40,14 @@ __global__ void k_bin_keys(int n, const double *__restrict__ pos, const double *
         double x = pos[3 * i + d];
         if (!isfinite(x)) { set_status(status, MSM_EINVAL); key[i] = -1; return; }
         double rl = __dsub_rn(x, g.origin[d]);
-        double t = __dmul_rn(rl, inv_h);
+        double t = __dmul_rn(rl, D.inv_h);
         double fl = floor(t);
         if (!(t >= 0.0) || fl > (double)(g.nc[d] - 1)) { set_status(status, MSM_ERANGE); key[i] = -1; return; }
         c[d] = (int)fl;
         r[d] = rl;
         f[d] = __dsub_rn(t, fl);
     }
-    int k = (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
+    int k = D.cell_off + (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
     key[i] = k;
     atomicAdd(&count[k], 1);
     T qi = (T)q[i];
@@ -137,21 +145,26 @@ __global__ void k_sort_cells(int ncells, const int *__restrict__ start, int *__r
     }
 }
 
+// Sorted slots of system s are [atom_off, atom_off + n): its cells come before
+// the next system's and every atom lands in a cell of its own system.
 template <typename T>
-__global__ void k_gather(int n, const int *__restrict__ perm, const int *__restrict__ key,
+__global__ void k_gather(const Batch bt, const int *__restrict__ perm, const int *__restrict__ key,
                          const vec4<T> *__restrict__ rel, const vec4<T> *__restrict__ frac,
-                         const uint8_t *__restrict__ lj, int n_mol, vec4<T> *__restrict__ apos,
+                         const uint8_t *__restrict__ lj, vec4<T> *__restrict__ apos,
                          vec4<T> *__restrict__ afrac, int *__restrict__ akey, int *__restrict__ aflag,
                          const int *__restrict__ status)
 {
     if (failed(status)) return;
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int i = perm[s];
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const int ls = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ls >= D.n) return;
+    const int s = D.atom_off + ls;
+    const int i = perm[s];
     apos[s] = rel[i];
     afrac[s] = frac[i];
     akey[s] = key[i];
-    const int mol = i < 3 * n_mol ? i / 3 : n_mol + (i - 3 * n_mol);   // single sites: own molecule
+    const int li = i - D.atom_off;
+    const int mol = li < 3 * D.n_mol ? i - li % 3 : i;       // first atom of the molecule; single sites: own
     aflag[s] = (mol << 1) | ((lj && lj[i]) ? 1 : 0);
 }
 
@@ -181,14 +194,13 @@ int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int
 template <typename T>
 int launch_bin(const BinArgs<T> &a, cudaStream_t st)
 {
-    const int n = a.n;
-    const int m = a.g.ncells;
+    const int n = a.n_total, m = a.m_total, B = a.bt.B;
     const int nb = (m + SCAN_B - 1) / SCAN_B;
     if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
     CUDA_TRY(cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)(m + 1), st));
+    const dim3 ga((a.max_n + 255) / 256, B);
     if (n > 0) {
-        k_bin_keys<T><<<(n + 255) / 256, 256, 0, st>>>(n, a.pos, a.q, a.g, a.inv_h, a.key, a.count, a.rel, a.frac,
-                                                       a.status);
+        k_bin_keys<T><<<ga, 256, 0, st>>>(a.bt, a.pos, a.q, a.key, a.count, a.rel, a.frac, a.status);
         count_launch();
     }
     k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, a.count, a.start, a.bsum, a.status);
@@ -198,8 +210,8 @@ int launch_bin(const BinArgs<T> &a, cudaStream_t st)
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, a.key, a.start, a.count, a.perm, a.status);
         k_sort_cells<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.perm, a.status);
-        k_gather<T><<<(n + 255) / 256, 256, 0, st>>>(n, a.perm, a.key, a.rel, a.frac, a.lj, a.n_mol, a.apos,
-                                                     a.afrac, a.akey, a.aflag, a.status);
+        k_gather<T><<<ga, 256, 0, st>>>(a.bt, a.perm, a.key, a.rel, a.frac, a.lj, a.apos, a.afrac, a.akey,
+                                        a.aflag, a.status);
         count_launch(3);
     }
     CUDA_TRY(cudaGetLastError());

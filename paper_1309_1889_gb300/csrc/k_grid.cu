@@ -15,6 +15,11 @@
 //   k_interp       phi_i = k_e (u_i^short + sum_mu phi^0_mu(r_i) u^0_mu - q_i gamma(0)/a),
 //                  F_i = k_e (F_i^short - q_i sum_mu grad phi^0_mu(r_i) u^0_mu) [+ LJ],
 //                  scattered back to the caller's atom order
+//
+// Every kernel serves a batch of systems (one launch per stage for all of
+// them): blockIdx.y picks the system for the per-point and per-atom kernels,
+// and the persistent lattice-cutoff kernel takes tiles of every (system,
+// level) pair from one counter.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -59,10 +64,13 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
     AnterpSmem<T> &S = *reinterpret_cast<AnterpSmem<T> *>(smem_raw);
     __shared__ int s_total;
     if (failed(A.status)) return;
-    const LevelGeom &L = A.L0;
-    const int ntx = (L.n[0] + AT_X - 1) / AT_X, nty = (L.n[1] + AT_Y - 1) / AT_Y;
+    const SysDesc &D = A.bt.sd[blockIdx.y];
+    const LevelGeom &L = D.gg.L[0];
+    const int ntx = (L.n[0] + AT_X - 1) / AT_X, nty = (L.n[1] + AT_Y - 1) / AT_Y, ntz = (L.n[2] + AT_Z - 1) / AT_Z;
+    if ((int)blockIdx.x >= ntx * nty * ntz) return;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
-    const int nx = A.cg.nc[0], ny = A.cg.nc[1], nz = A.cg.nc[2];
+    const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
+    const int *__restrict__ start = A.start + D.cell_off;
     // absolute index of the tile's first point; cell block origin = that - 2
     const int m0x = L.lo[0] + bx * AT_X, m0y = L.lo[1] + by * AT_Y, m0z = L.lo[2] + bz * AT_Z;
     const int c0x = m0x - 2, c0y = m0y - 2, c0z = m0z - 2;
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
         int c = 0;
         if (cx >= 0 && cx < nx && cy >= 0 && cy < ny && cz >= 0 && cz < nz) {
             const int cell = (cz * ny + cy) * nx + cx;
-            c = A.start[cell + 1] - A.start[cell];
+            c = start[cell + 1] - start[cell];
         }
         S.cell_off[e + 1] = c;
     }
@@ -94,7 +102,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
             const int cx = c0x + lx, cy = c0y + ly, cz = c0z + lz;
             if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
             const int cell = (cz * ny + cy) * nx + cx;
-            const int g0 = A.start[cell], g1 = A.start[cell + 1];
+            const int g0 = start[cell], g1 = start[cell + 1];
             for (int g = g0, k = S.cell_off[e]; g < g1; g++, k++) {
                 T wx[4], wy[4], wz[4];
                 anterp_weights(A.afrac[g], wx, wy, wz);
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
                         acc += (S.w[ox][k] * S.w[4 + oy][k]) * S.w[8 + oz][k];
                 } else {
                     const int cell = (cz * ny + cy) * nx + cx;
-                    for (int g = A.start[cell]; g < A.start[cell + 1]; g++) {
+                    for (int g = start[cell]; g < start[cell + 1]; g++) {
                         T wx[4], wy[4], wz[4];
                         anterp_weights(A.afrac[g], wx, wy, wz);
                         acc += (wx[ox] * wy[oy]) * wz[oz];
@@ -137,17 +145,21 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
             }
         }
     }
-    A.q0[L.off + (iz * L.n[1] + iy) * L.n[0] + ix] = acc;
+    A.q[D.grid_off + L.off + (iz * L.n[1] + iy) * L.n[0] + ix] = acc;
+}
+
+int anterp_tiles(const LevelGeom &L)
+{
+    return ((L.n[0] + AT_X - 1) / AT_X) * ((L.n[1] + AT_Y - 1) / AT_Y) * ((L.n[2] + AT_Z - 1) / AT_Z);
 }
 
 template <typename T>
 int launch_anterp(const AnterpArgs<T> &a, cudaStream_t st)
 {
-    const int ntx = (a.L0.n[0] + AT_X - 1) / AT_X, nty = (a.L0.n[1] + AT_Y - 1) / AT_Y,
-              ntz = (a.L0.n[2] + AT_Z - 1) / AT_Z;
+    if (a.max_tiles <= 0) return MSM_OK;
     const size_t smem = anterp_smem_bytes<T>();
     CUDA_TRY(cudaFuncSetAttribute(k_anterp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_anterp<T><<<ntx * nty * ntz, AT_THREADS, smem, st>>>(a);
+    k_anterp<T><<<dim3(a.max_tiles, a.bt.B), AT_THREADS, smem, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -167,11 +179,13 @@ __device__ __forceinline__ double rtap(int o)
 }
 
 template <typename T>
-__global__ void k_restrict(LevelGeom F, LevelGeom C, const T *__restrict__ qf, T *__restrict__ qc,
-                           const int *__restrict__ status)
+__global__ void k_restrict(const Batch bt, int k, T *__restrict__ q, const int *__restrict__ status)
 {
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const LevelGeom &F = D.gg.L[k], &C = D.gg.L[k + 1];
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= C.n[0] * C.n[1] * C.n[2] || failed(status)) return;
+    const T *__restrict__ qf = q + D.grid_off + F.off;
     const int mx = C.lo[0] + idx % C.n[0], my = C.lo[1] + (idx / C.n[0]) % C.n[1],
               mz = C.lo[2] + idx / (C.n[0] * C.n[1]);
     const int offs[5] = {-3, -1, 0, 1, 3};
@@ -186,7 +200,7 @@ __global__ void k_restrict(LevelGeom F, LevelGeom C, const T *__restrict__ qf, T
             const int ny = 2 * my + offs[b] - F.lo[1];
             if (ny < 0 || ny >= F.n[1]) continue;
             const T wy = wz * (T)rtap(offs[b]);
-            const T *row = qf + F.off + (size_t)(nz * F.n[1] + ny) * F.n[0];
+            const T *row = qf + (size_t)(nz * F.n[1] + ny) * F.n[0];
             T racc = 0;
 #pragma unroll
             for (int c = 0; c < 5; c++) {
@@ -197,15 +211,14 @@ __global__ void k_restrict(LevelGeom F, LevelGeom C, const T *__restrict__ qf, T
             acc = fma(wy, racc, acc);
         }
     }
-    qc[C.off + idx] = acc;
+    q[D.grid_off + C.off + idx] = acc;
 }
 
 template <typename T>
-int launch_restrict(const LevelGeom &fine, const LevelGeom &coarse, const T *qf, T *qc, const int *status,
-                    cudaStream_t st)
+int launch_restrict(const Batch &bt, int k, int max_coarse, T *q, const int *status, cudaStream_t st)
 {
-    const int m = coarse.n[0] * coarse.n[1] * coarse.n[2];
-    k_restrict<T><<<(m + 255) / 256, 256, 0, st>>>(fine, coarse, qf, qc, status);
+    if (max_coarse <= 0) return MSM_OK;
+    k_restrict<T><<<dim3((max_coarse + 255) / 256, bt.B), 256, 0, st>>>(bt, k, q, status);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -298,7 +311,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
     T *wt = reinterpret_cast<T *>(smem_raw);                 // WD^3 weights
     T *plane = wt + WD * WD * WD;                            // PY x PX input plane
     int *hw = reinterpret_cast<int *>(plane + PX * PY);      // WD^2 half widths (-1: empty row)
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_ent;
     if (failed(A.status)) return;
     const int t = threadIdx.x;
     for (int e = t; e < WD * WD * WD; e += ST_THREADS) wt[e] = A.w[e];
@@ -309,21 +322,31 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
         hw[(r.y + RAD) * WD + (r.x + RAD)] = r.z;
     }
     const int lx = t % ST_TXT, ly = t / ST_TXT;
-    const int total = A.blk_off[A.nlev];
+    const int total = A.total_tiles, nent = A.bt.B * A.nlev;
     for (;;) {
         __syncthreads();
-        if (t == 0) s_tile = atomicAdd(counter, 1);
+        if (t == 0) {
+            const int tile = atomicAdd(counter, 1);
+            // owner (system, level) of the tile: last entry whose first tile is <= tile
+            int lo_e = 0, hi_e = nent - 1;
+            while (lo_e < hi_e) {
+                const int mid = (lo_e + hi_e + 1) >> 1;
+                if (A.blk_off[mid] <= tile) lo_e = mid; else hi_e = mid - 1;
+            }
+            s_tile = tile;
+            s_ent = lo_e;
+        }
         __syncthreads();
         const int tile = s_tile;
         if (tile >= total) break;
-        int lev = 0;
-        while (lev + 1 < A.nlev && tile >= A.blk_off[lev + 1]) lev++;
-        const int b = tile - A.blk_off[lev];
-        const LevelGeom &L = A.gg.L[lev];
-        const int tx = b % A.tiles[lev][0], ty = (b / A.tiles[lev][0]) % A.tiles[lev][1],
-                  tz = b / (A.tiles[lev][0] * A.tiles[lev][1]);
+        const int ent = s_ent, lev = ent % A.nlev;
+        const SysDesc &D = A.bt.sd[ent / A.nlev];
+        const LevelGeom &L = D.gg.L[lev];
+        const int b = tile - A.blk_off[ent];
+        const int ntx = (L.n[0] + ST_TX - 1) / ST_TX, nty = (L.n[1] + ST_TY - 1) / ST_TY;
+        const int tx = b % ntx, ty = (b / ntx) % nty, tz = b / (ntx * nty);
         const int x0 = tx * ST_TX, y0 = ty * ST_TY, z0 = tz * ST_TZ;
-        const T *__restrict__ q = A.q + L.off;
+        const T *__restrict__ q = A.q + D.grid_off + L.off;
         T acc[ST_RZ][ST_RX];
 #pragma unroll
         for (int s = 0; s < ST_RZ; s++)
@@ -363,7 +386,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
         for (int s = 0; s < ST_RZ; s++) {
             const int gz = z0 + s;
             if (gy < L.n[1] && gz < L.n[2]) {
-                T *out = A.ucut + L.off + (size_t)(gz * L.n[1] + gy) * L.n[0];
+                T *out = A.ucut + D.grid_off + L.off + (size_t)(gz * L.n[1] + gy) * L.n[0];
 #pragma unroll
                 for (int r = 0; r < ST_RX; r++) {
                     const int gx = x0 + lx * ST_RX + r;
@@ -382,7 +405,7 @@ static int launch_stencil_rad(const StencilArgs<T> &a, int *counter, int sms, cu
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_THREADS, smem));
     if (per_sm < 1) return fail_msg(MSM_EINVAL, "lattice-cutoff tile does not fit (radius %d)", RAD);
-    const int grid = std::min(a.blk_off[a.nlev], sms * per_sm);
+    const int grid = std::min(a.total_tiles, sms * per_sm);
     k_stencil<T, RAD><<<grid, ST_THREADS, smem, st>>>(a, counter);
     count_launch();
     CUDA_TRY(cudaGetLastError());
@@ -392,7 +415,7 @@ static int launch_stencil_rad(const StencilArgs<T> &a, int *counter, int sms, cu
 template <typename T>
 int launch_stencil(const StencilArgs<T> &a, int *counter, cudaStream_t st)
 {
-    if (a.nlev <= 0) return MSM_OK;
+    if (a.nlev <= 0 || a.total_tiles <= 0) return MSM_OK;
     int dev = 0, sms = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -414,11 +437,9 @@ int launch_stencil(const StencilArgs<T> &a, int *counter, cudaStream_t st)
     }
 }
 
-void stencil_tiles(const LevelGeom &L, int t[3])
+int stencil_tile_count(const LevelGeom &L)
 {
-    t[0] = (L.n[0] + ST_TX - 1) / ST_TX;
-    t[1] = (L.n[1] + ST_TY - 1) / ST_TY;
-    t[2] = (L.n[2] + ST_TZ - 1) / ST_TZ;
+    return ((L.n[0] + ST_TX - 1) / ST_TX) * ((L.n[1] + ST_TY - 1) / ST_TY) * ((L.n[2] + ST_TZ - 1) / ST_TZ);
 }
 
 // ------------------------------------------------------------------ top level
@@ -443,33 +464,57 @@ int launch_top_table(const LevelGeom &top, double a_top, double h_top, double *t
 }
 
 template <typename T>
-__global__ void k_top(LevelGeom L, const double *__restrict__ table, const T *__restrict__ q,
+__global__ void k_top(const Batch bt, const double *__restrict__ table, const T *__restrict__ q,
                       double *__restrict__ u, const int *__restrict__ status)
 {
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const LevelGeom &L = D.gg.L[D.gg.levels - 1];
     const int lane = threadIdx.x & 31;
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int m = L.n[0] * L.n[1] * L.n[2];
     if (p >= m || failed(status)) return;
     const int px = p % L.n[0], py = (p / L.n[0]) % L.n[1], pz = p / (L.n[0] * L.n[1]);
     const int wx = 2 * L.n[0] - 1, wy = 2 * L.n[1] - 1;
-    const T *qt = q + L.off;
+    const T *qt = q + D.grid_off + L.off;
+    const double *tab = table + D.ttab_off;
     double acc = 0.0;
     for (int j = lane; j < m; j += 32) {
         const int jx = j % L.n[0], jy = (j / L.n[0]) % L.n[1], jz = j / (L.n[0] * L.n[1]);
         const int t = ((pz - jz + L.n[2] - 1) * wy + (py - jy + L.n[1] - 1)) * wx + (px - jx + L.n[0] - 1);
-        acc = fma(table[t], (double)qt[j], acc);
+        acc = fma(tab[t], (double)qt[j], acc);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) u[p] = acc;
+    if (lane == 0) u[D.top_off + p] = acc;
 }
 
 template <typename T>
-int launch_top(const LevelGeom &top, const double *table, const T *qtop, double *utop, const int *status,
+int launch_top(const Batch &bt, int max_top, const double *table, const T *q, double *utop, const int *status,
                cudaStream_t st)
 {
-    const int m = top.n[0] * top.n[1] * top.n[2];
-    k_top<T><<<(m * 32 + 255) / 256, 256, 0, st>>>(top, table, qtop, utop, status);
+    if (max_top <= 0) return MSM_OK;
+    k_top<T><<<dim3((max_top * 32 + 255) / 256, bt.B), 256, 0, st>>>(bt, table, q, utop, status);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+template <typename T>
+__global__ void k_top_to_grid(const Batch bt, const double *__restrict__ utop, T *__restrict__ u,
+                              const int *__restrict__ status)
+{
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const LevelGeom &L = D.gg.L[D.gg.levels - 1];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.n[0] * L.n[1] * L.n[2] || failed(status)) return;
+    u[D.grid_off + L.off + p] = (T)utop[D.top_off + p];
+}
+
+template <typename T>
+int launch_top_to_grid(const Batch &bt, int max_top, const double *utop, T *u, const int *status, cudaStream_t st)
+{
+    if (max_top <= 0) return MSM_OK;
+    k_top_to_grid<T><<<dim3((max_top + 255) / 256, bt.B), 256, 0, st>>>(bt, utop, u, status);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -478,11 +523,8 @@ int launch_top(const LevelGeom &top, const double *table, const T *qtop, double 
 // ---------------------------------------------------------------- prolongation
 
 template <typename T, typename S>
-__global__ void k_prolong(LevelGeom F, LevelGeom C, const T *__restrict__ ucut, const S *__restrict__ uc,
-                          T *__restrict__ uf, const int *__restrict__ status)
+__device__ __forceinline__ T prolong_point(const LevelGeom &F, const LevelGeom &C, int idx, const S *__restrict__ uc)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= F.n[0] * F.n[1] * F.n[2] || failed(status)) return;
     const int m[3] = {F.lo[0] + idx % F.n[0], F.lo[1] + (idx / F.n[0]) % F.n[1], F.lo[2] + idx / (F.n[0] * F.n[1])};
     // Four coarse points per axis nu0 .. nu0+3 with weights Phi(mu/2 - nu):
     // even mu: nu0 = mu/2 - 1, weights (0, 1, 0, 0); odd mu: nu0 = (mu-3)/2, weights (-1, 9, 9, -1)/16.
@@ -516,15 +558,31 @@ __global__ void k_prolong(LevelGeom F, LevelGeom C, const T *__restrict__ ucut, 
             acc = fma(w[2][a] * w[1][b], racc, acc);
         }
     }
-    uf[F.off + idx] = ucut[F.off + idx] + acc;
+    return acc;
 }
 
-template <typename T, typename S>
-int launch_prolong(const LevelGeom &fine, const LevelGeom &coarse, const T *ucut, const S *uc, T *uf,
+// u^k_mu = u^{k,cut}_mu + prolongation of u^{k+1}; from_top: level k+1 is the
+// top level, read in FP64 from the top buffer.
+template <typename T>
+__global__ void k_prolong(const Batch bt, int k, const T *__restrict__ ucut, const double *__restrict__ utop,
+                          bool from_top, T *__restrict__ u, const int *__restrict__ status)
+{
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const LevelGeom &F = D.gg.L[k], &C = D.gg.L[k + 1];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= F.n[0] * F.n[1] * F.n[2] || failed(status)) return;
+    const T acc = from_top ? prolong_point<T, double>(F, C, idx, utop + D.top_off)
+                           : prolong_point<T, T>(F, C, idx, u + D.grid_off + C.off);
+    const int o = D.grid_off + F.off + idx;
+    u[o] = ucut[o] + acc;
+}
+
+template <typename T>
+int launch_prolong(const Batch &bt, int k, int max_fine, const T *ucut, const double *utop, bool from_top, T *u,
                    const int *status, cudaStream_t st)
 {
-    const int m = fine.n[0] * fine.n[1] * fine.n[2];
-    k_prolong<T, S><<<(m + 255) / 256, 256, 0, st>>>(fine, coarse, ucut, uc, uf, status);
+    if (max_fine <= 0) return MSM_OK;
+    k_prolong<T><<<dim3((max_fine + 255) / 256, bt.B), 256, 0, st>>>(bt, k, ucut, utop, from_top, u, status);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -535,19 +593,21 @@ int launch_prolong(const LevelGeom &fine, const LevelGeom &coarse, const T *ucut
 template <typename T>
 __global__ void k_interp(const InterpArgs<T> A)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= A.n || failed(A.status)) return;
-    const int key = A.akey[s];
-    const int nx = A.cg.nc[0], ny = A.cg.nc[1];
+    const SysDesc &D = A.bt.sd[blockIdx.y];
+    const int ls = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ls >= D.n || failed(A.status)) return;
+    const int s = D.atom_off + ls;
+    const int key = A.akey[s] - D.cell_off;
+    const int nx = D.g.nc[0], ny = D.g.nc[1];
     const int cx = key % nx, cy = (key / nx) % ny, cz = key / (nx * ny);
     const vec4<T> f = A.afrac[s];
     T wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
     phi_weights_d(f.x, wx, dx);
     phi_weights_d(f.y, wy, dy);
     phi_weights_d(f.z, wz, dz);
-    const LevelGeom &L = A.L0;
+    const LevelGeom &L = D.gg.L[0];
     // grid point mu = c - 1 + o sits at array index c - 1 + o - lo = c + o (lo = -1)
-    const T *u = A.u0 + L.off;
+    const T *u = A.u + D.grid_off + L.off;
     T p = 0, gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int oz = 0; oz < 4; oz++) {
@@ -571,7 +631,7 @@ __global__ void k_interp(const InterpArgs<T> A)
     const int i = A.perm[s];
     const vec4<T> sr = A.sr[i];
     const double q = A.q[i];
-    const double ke = A.ke, ih = A.inv_h;
+    const double ke = A.ke, ih = D.inv_h;
     const double phi = ke * ((double)sr.w + (double)p - q * A.self);
     double F[3] = {ke * ((double)sr.x - q * (double)gx * ih), ke * ((double)sr.y - q * (double)gy * ih),
                    ke * ((double)sr.z - q * (double)gz * ih)};
@@ -585,7 +645,7 @@ __global__ void k_interp(const InterpArgs<T> A)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double x = A.pos[3 * i + d];
-            const double lo = A.wall_w - (x - A.box_lo[d]), hi = A.wall_w - (A.box_hi[d] - x);
+            const double lo = A.wall_w - (x - D.box_lo[d]), hi = A.wall_w - (D.box_hi[d] - x);
             if (lo > 0.0) { F[d] += A.wall_k * lo; e += 0.5 * A.wall_k * lo * lo; }
             if (hi > 0.0) { F[d] -= A.wall_k * hi; e += 0.5 * A.wall_k * hi * hi; }
         }
@@ -599,8 +659,8 @@ __global__ void k_interp(const InterpArgs<T> A)
 template <typename T>
 int launch_interp(const InterpArgs<T> &a, cudaStream_t st)
 {
-    if (a.n <= 0) return MSM_OK;
-    k_interp<T><<<(a.n + 255) / 256, 256, 0, st>>>(a);
+    if (a.max_n <= 0) return MSM_OK;
+    k_interp<T><<<dim3((a.max_n + 255) / 256, a.bt.B), 256, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -610,15 +670,16 @@ int launch_interp(const InterpArgs<T> &a, cudaStream_t st)
 
 template int launch_anterp<float>(const AnterpArgs<float> &, cudaStream_t);
 template int launch_anterp<double>(const AnterpArgs<double> &, cudaStream_t);
-template int launch_restrict<float>(const LevelGeom &, const LevelGeom &, const float *, float *, const int *, cudaStream_t);
-template int launch_restrict<double>(const LevelGeom &, const LevelGeom &, const double *, double *, const int *, cudaStream_t);
+template int launch_restrict<float>(const Batch &, int, int, float *, const int *, cudaStream_t);
+template int launch_restrict<double>(const Batch &, int, int, double *, const int *, cudaStream_t);
 template int launch_stencil<float>(const StencilArgs<float> &, int *, cudaStream_t);
 template int launch_stencil<double>(const StencilArgs<double> &, int *, cudaStream_t);
-template int launch_top<float>(const LevelGeom &, const double *, const float *, double *, const int *, cudaStream_t);
-template int launch_top<double>(const LevelGeom &, const double *, const double *, double *, const int *, cudaStream_t);
-template int launch_prolong<float, float>(const LevelGeom &, const LevelGeom &, const float *, const float *, float *, const int *, cudaStream_t);
-template int launch_prolong<float, double>(const LevelGeom &, const LevelGeom &, const float *, const double *, float *, const int *, cudaStream_t);
-template int launch_prolong<double, double>(const LevelGeom &, const LevelGeom &, const double *, const double *, double *, const int *, cudaStream_t);
+template int launch_top<float>(const Batch &, int, const double *, const float *, double *, const int *, cudaStream_t);
+template int launch_top<double>(const Batch &, int, const double *, const double *, double *, const int *, cudaStream_t);
+template int launch_top_to_grid<float>(const Batch &, int, const double *, float *, const int *, cudaStream_t);
+template int launch_top_to_grid<double>(const Batch &, int, const double *, double *, const int *, cudaStream_t);
+template int launch_prolong<float>(const Batch &, int, int, const float *, const double *, bool, float *, const int *, cudaStream_t);
+template int launch_prolong<double>(const Batch &, int, int, const double *, const double *, bool, double *, const int *, cudaStream_t);
 template int launch_interp<float>(const InterpArgs<float> &, cudaStream_t);
 template int launch_interp<double>(const InterpArgs<double> &, cudaStream_t);
 

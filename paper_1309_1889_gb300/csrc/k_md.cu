@@ -11,6 +11,11 @@
 //   k_vv_second    second half kick, RATTLE velocity stage, kinetic energy
 //   k_pr_update    parareal correction lambda^{k+1}_{n+1} = F + (G_new - G_old)
 //                  in FP64 (Sec. 4) with the max |dx| partials
+//   k_record_uk    (U, K) of every system after a step, at a step index kept
+//                  on the device so that a replayed CUDA graph writes each
+//                  step's entry
+//
+// The per-system kernels take a batch: blockIdx.y is the system.
 #include "kernels.cuh"
 
 namespace msm {
@@ -20,9 +25,10 @@ namespace msm {
 template <typename T>
 __global__ void k_exclusions(const ExclArgs A)
 {
+    const SysDesc &D = A.bt.sd[blockIdx.y];
     const int mo = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mo >= A.n_mol || failed(A.status)) return;
-    const int i0 = 3 * mo;
+    if (mo >= D.n_mol || failed(A.status)) return;
+    const int i0 = D.atom_off + 3 * mo;
     double x[3][3];
     T q[3], F[3][3], dphi[3], de[3];
 #pragma unroll
@@ -77,8 +83,8 @@ __global__ void k_exclusions(const ExclArgs A)
 template <typename T>
 int launch_exclusions(const ExclArgs &a, cudaStream_t st)
 {
-    if (a.n_mol <= 0) return MSM_OK;
-    k_exclusions<T><<<(a.n_mol + 127) / 128, 128, 0, st>>>(a);
+    if (a.max_mol <= 0) return MSM_OK;
+    k_exclusions<T><<<dim3((a.max_mol + 127) / 128, a.bt.B), 128, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -91,7 +97,7 @@ template int launch_exclusions<double>(const ExclArgs &, cudaStream_t);
 constexpr int SUM_T = 256;
 constexpr int SUM_CHUNK = 4096;    // values per block: fixed partition
 
-int sum_partials_needed(int m) { return (m + SUM_CHUNK - 1) / SUM_CHUNK + 1; }
+__host__ __device__ int sum_blocks(int n) { return n > 0 ? (n + SUM_CHUNK - 1) / SUM_CHUNK : 1; }
 
 __device__ __forceinline__ double block_sum(double v)
 {
@@ -110,40 +116,46 @@ __device__ __forceinline__ double block_sum(double v)
 
 struct SumCols { const double *c[4]; };
 
-__global__ void k_sum_partials(int m, int ncols, SumCols cols, double *__restrict__ part, int nblk,
+// block (x, s): chunk x of system s
+__global__ void k_sum_partials(const Batch bt, int ncols, SumCols cols, double *__restrict__ part, int total_blocks,
                                const int *__restrict__ status)
 {
     if (status && failed(status)) return;
-    const int b0 = blockIdx.x * SUM_CHUNK;
+    const SysDesc &D = bt.sd[blockIdx.y];
+    if ((int)blockIdx.x >= sum_blocks(D.n)) return;
+    const int b0 = blockIdx.x * SUM_CHUNK, e0 = min(D.n, b0 + SUM_CHUNK);
     for (int c = 0; c < ncols; c++) {
+        const double *col = cols.c[c] + D.atom_off;
         double v = 0;
-        for (int i = b0 + threadIdx.x; i < min(m, b0 + SUM_CHUNK); i += SUM_T) v += cols.c[c][i];
+        for (int i = b0 + threadIdx.x; i < e0; i += SUM_T) v += col[i];
         v = block_sum(v);
-        if (threadIdx.x == 0) part[c * nblk + blockIdx.x] = v;
+        if (threadIdx.x == 0) part[c * total_blocks + D.part_off + blockIdx.x] = v;
     }
 }
 
-__global__ void k_sum_final(int nblk, int ncols, const double *__restrict__ part, double *__restrict__ out,
-                            const int *__restrict__ status)
+// block s: the partials of system s in order
+__global__ void k_sum_final(const Batch bt, int ncols, const double *__restrict__ part, int total_blocks,
+                            double *__restrict__ out, int out_stride, const int *__restrict__ status)
 {
     if (status && failed(status)) return;
+    const SysDesc &D = bt.sd[blockIdx.x];
+    const int nblk = sum_blocks(D.n);
     for (int c = 0; c < ncols; c++) {
         double v = 0;
-        for (int i = threadIdx.x; i < nblk; i += SUM_T) v += part[c * nblk + i];
+        for (int i = threadIdx.x; i < nblk; i += SUM_T) v += part[c * total_blocks + D.part_off + i];
         v = block_sum(v);
-        if (threadIdx.x == 0) out[c] = v;
+        if (threadIdx.x == 0) out[blockIdx.x * out_stride + c] = v;
     }
 }
 
-int launch_sum(int m, int ncols, const double *const *cols, double *partials, double *out, const int *status,
-               cudaStream_t st)
+int launch_sum(const Batch &bt, int max_n, int total_blocks, int ncols, const double *const *cols, double *part,
+               double *out, int out_stride, const int *status, cudaStream_t st)
 {
     if (ncols > 4) return fail_msg(MSM_EINVAL, "launch_sum: at most 4 columns");
     SumCols sc;
     for (int c = 0; c < 4; c++) sc.c[c] = c < ncols ? cols[c] : nullptr;
-    const int nblk = m > 0 ? (m + SUM_CHUNK - 1) / SUM_CHUNK : 1;
-    k_sum_partials<<<nblk, SUM_T, 0, st>>>(m, ncols, sc, partials, nblk, status);
-    k_sum_final<<<1, SUM_T, 0, st>>>(nblk, ncols, partials, out, status);
+    k_sum_partials<<<dim3(sum_blocks(max_n), bt.B), SUM_T, 0, st>>>(bt, ncols, sc, part, total_blocks, status);
+    k_sum_final<<<bt.B, SUM_T, 0, st>>>(bt, ncols, part, total_blocks, out, out_stride, status);
     count_launch(2);
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -158,12 +170,13 @@ __device__ __forceinline__ constexpr int bond_j(int c) { return c == 0 ? 1 : 2; 
 template <typename T>
 __global__ void k_vv_first(const VVArgs A)
 {
-    const int units = A.n_mol + (A.n - 3 * A.n_mol);
+    const SysDesc &D = A.bt.sd[blockIdx.y];
+    const int units = D.n_mol + (D.n - 3 * D.n_mol);
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= units || failed(A.status)) return;
     const double dt = A.dt;
-    if (u >= A.n_mol) {                                 // single site: half kick, drift
-        const int i = 3 * A.n_mol + (u - A.n_mol);
+    if (u >= D.n_mol) {                                 // single site: half kick, drift
+        const int i = D.atom_off + 3 * D.n_mol + (u - D.n_mol);
         const double im = A.im[i];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
@@ -175,7 +188,7 @@ __global__ void k_vv_first(const VVArgs A)
         }
         return;
     }
-    const int i0 = 3 * u;
+    const int i0 = D.atom_off + 3 * u;
     double xo[3][3], xn[3][3], v[3][3], im[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -239,12 +252,13 @@ __global__ void k_vv_first(const VVArgs A)
 template <typename T>
 __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
 {
-    const int units = A.n_mol + (A.n - 3 * A.n_mol);
+    const SysDesc &D = A.bt.sd[blockIdx.y];
+    const int units = D.n_mol + (D.n - 3 * D.n_mol);
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= units || failed(A.status)) return;
     const double hdt = 0.5 * A.dt;
-    if (u >= A.n_mol) {
-        const int i = 3 * A.n_mol + (u - A.n_mol);
+    if (u >= D.n_mol) {
+        const int i = D.atom_off + 3 * D.n_mol + (u - D.n_mol);
         const double m = A.m[i], im = A.im[i];
         double k2 = 0;
 #pragma unroll
@@ -256,7 +270,7 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
         if (kin) kin[i] = 0.5 * m * k2;
         return;
     }
-    const int i0 = 3 * u;
+    const int i0 = D.atom_off + 3 * u;
     double v[3][3], m[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -318,9 +332,8 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
 template <typename T>
 int launch_vv_first(const VVArgs &a, cudaStream_t st)
 {
-    const int units = a.n_mol + (a.n - 3 * a.n_mol);
-    if (units <= 0) return MSM_OK;
-    k_vv_first<T><<<(units + 127) / 128, 128, 0, st>>>(a);
+    if (a.max_units <= 0) return MSM_OK;
+    k_vv_first<T><<<dim3((a.max_units + 127) / 128, a.bt.B), 128, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -329,9 +342,8 @@ int launch_vv_first(const VVArgs &a, cudaStream_t st)
 template <typename T>
 int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st)
 {
-    const int units = a.n_mol + (a.n - 3 * a.n_mol);
-    if (units <= 0) return MSM_OK;
-    k_vv_second<T><<<(units + 127) / 128, 128, 0, st>>>(a, kin_atom);
+    if (a.max_units <= 0) return MSM_OK;
+    k_vv_second<T><<<dim3((a.max_units + 127) / 128, a.bt.B), 128, 0, st>>>(a, kin_atom);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -360,10 +372,34 @@ int launch_inverse(int n, const double *m, double *im, cudaStream_t st)
     return MSM_OK;
 }
 
-int launch_kinetic(const VVArgs &a, double *kin_atom, cudaStream_t st)
+int launch_kinetic(int n, const double *v, const double *m, double *kin_atom, cudaStream_t st)
 {
-    if (a.n <= 0) return MSM_OK;
-    k_kinetic<<<(a.n + 255) / 256, 256, 0, st>>>(a.n, a.v, a.m, kin_atom);
+    if (n <= 0) return MSM_OK;
+    k_kinetic<<<(n + 255) / 256, 256, 0, st>>>(n, v, m, kin_atom);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// One thread per system: uk[s*uk_stride + 2*step + (0, 1)] = (U_s, K_s), step = *ctr.
+__global__ void k_record_uk(int B, const double *__restrict__ sums, int sums_stride, const double *__restrict__ kin,
+                            double *__restrict__ uk, int uk_stride, int *__restrict__ ctr)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int step = *ctr;
+    if (s < B) {
+        uk[(size_t)s * uk_stride + 2 * step] = sums[s * sums_stride];
+        uk[(size_t)s * uk_stride + 2 * step + 1] = kin[s];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x == 0 && gridDim.x == 1) *ctr = step + 1;
+}
+
+int launch_record_uk(int B, const double *sums, int sums_stride, const double *kin, double *uk, int uk_stride,
+                     int *ctr, cudaStream_t st)
+{
+    if (B > 1024) return fail_msg(MSM_EINVAL, "at most 1024 systems record energies");
+    k_record_uk<<<1, 1024, 0, st>>>(B, sums, sums_stride, kin, uk, uk_stride, ctr);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

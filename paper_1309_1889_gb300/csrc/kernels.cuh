@@ -6,26 +6,36 @@
 
 namespace msm {
 
+// ---- batch launch shape ----------------------------------------------------
+// Every batched kernel runs on a grid (x, B): blockIdx.y is the system and
+// blocks past that system's work return at once.  gx is the x extent needed
+// by the largest system.
+struct Batch {
+    int B;                 // systems
+    const SysDesc *sd;     // device array of B descriptors
+};
+
 // ---- binning (k_bin.cu) --------------------------------------------------
 template <typename T> struct BinArgs {
-    int n;
-    const double *pos;     // n*3 FP64, original order
-    const double *q;       // n
-    const uint8_t *lj;     // n, nullable
-    CellGeom g;
-    double inv_h;          // 1/h rounded once in FP64 (the binning contract)
-    int *key;              // n
-    int *count;            // ncells + 1 (histogram, left zeroed by the scatter)
-    int *start;            // ncells + 1
-    int *perm;             // n: sorted slot -> atom
+    Batch bt;
+    int n_total;           // atoms over all systems
+    int m_total;           // cells over all systems
+    int max_n;             // atoms of the largest system
+    const double *pos;     // n_total*3 FP64, original order (systems concatenated)
+    const double *q;       // n_total
+    const uint8_t *lj;     // n_total, nullable
+    int *key;              // n_total: global cell id (system cell_off + local key)
+    int *count;            // m_total + 1 (histogram, left zeroed by the scatter)
+    int *start;            // m_total + 1
+    int *perm;             // n_total: sorted slot -> atom
     int *bsum;             // scan scratch (scan_scratch_ints())
-    vec4<T> *rel;          // n, original order: (x - x0, y - y0, z - z0, q)
-    vec4<T> *frac;         // n, original order: fractional position in the cell, q
-    vec4<T> *apos;         // n, sorted copy of rel
-    vec4<T> *afrac;        // n, sorted copy of frac
-    int *akey;             // n, sorted key
-    int *aflag;            // n, sorted (molecule id << 1) | LJ flag
-    int n_mol;             // leading rigid triples: atom i < 3 n_mol belongs to molecule i / 3
+    vec4<T> *rel;          // original order: (x - x0, y - y0, z - z0, q) of the atom's system
+    vec4<T> *frac;         // original order: fractional position in the cell, q
+    vec4<T> *apos;         // sorted copy of rel
+    vec4<T> *afrac;        // sorted copy of frac
+    int *akey;             // sorted global cell id
+    int *aflag;            // sorted (molecule id << 1) | LJ flag; molecule id = global
+                           // index of the molecule's first atom (single sites: own index)
     int *status;
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
@@ -35,11 +45,9 @@ int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int
 
 // ---- short range (k_short.cu) ----------------------------------------------
 template <typename T> struct ShortArgs {
-    CellGeom g;
-    int bd[3];             // brick edge in cells
-    int nb[3];             // bricks per axis
-    int nbricks;
-    const int *start;      // cell_start
+    Batch bt;
+    int max_bricks;        // bricks of the largest system
+    const int *start;      // global cell_start
     const vec4<T> *apos;
     const int *aflag;
     T a, a2, a_sel;        // cutoff, its square, row-selection radius (cutoff + rounding pad)
@@ -57,6 +65,9 @@ template <typename T> struct ShortArgs {
 // the exclusion kernel) and add the LJ term between flagged sites.
 template <typename T> int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st);
 template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st);
+// Largest brick (cells per axis) whose candidate rows fit the kernel's row list
+// for cutoff a_sel and cell edge h.
+bool short_rows_fit(const int bd[3], double a_sel, double h);
 
 // ---- Verlet lists (k_list.cu) --------------------------------------------
 template <typename T> struct ListArgs {
@@ -89,17 +100,19 @@ template <typename T> int launch_list_force(const ListArgs<T> &a, cudaStream_t s
 
 // ---- grids (k_grid.cu) -----------------------------------------------------
 template <typename T> struct AnterpArgs {
-    CellGeom cg;
-    LevelGeom L0;
-    const int *start;
+    Batch bt;
+    int max_tiles;         // anterpolation tiles of the largest level-0 grid
+    const int *start;      // global cell_start
     const vec4<T> *afrac;
-    T *q0;
+    T *q;                  // concatenated grids
     const int *status;
 };
 template <typename T> int launch_anterp(const AnterpArgs<T> &a, cudaStream_t st);
+int anterp_tiles(const LevelGeom &L0);
 
-template <typename T> int launch_restrict(const LevelGeom &fine, const LevelGeom &coarse, const T *qf, T *qc,
-                                          const int *status, cudaStream_t st);
+// level k -> k+1 of every system; max_coarse = points of the largest level k+1
+template <typename T> int launch_restrict(const Batch &bt, int k, int max_coarse, T *q, const int *status,
+                                          cudaStream_t st);
 
 struct StencilGeom {
     int rad;               // max |n_x| of a tap: largest r with r h < 2a
@@ -107,58 +120,60 @@ struct StencilGeom {
     int nrows;             // non-empty (dy, dz) rows
 };
 template <typename T> struct StencilArgs {
-    GridGeom gg;
+    Batch bt;
     int nlev;              // levels 0..nlev-1 get a lattice cutoff (nlev = l - 1)
-    int blk_off[MSM_MAX_LEVELS + 1];
-    int tiles[MSM_MAX_LEVELS][3];
+    const int *blk_off;    // B*nlev + 1 tile offsets, entry s*nlev + k = first tile of (system s, level k)
+    int total_tiles;
     StencilGeom sg;
     const T *w;            // wdim^3 weights g^0(|n| h) (0 outside the sphere), x fastest
     const int4 *rows;      // (dy, dz, half-width, 0) of each non-empty row
-    const T *q;            // concatenated grids (GridGeom offsets)
+    const T *q;            // concatenated grids
     T *ucut;               // concatenated, levels < nlev
     const int *status;
 };
 template <typename T> int launch_stencil(const StencilArgs<T> &a, int *tile_counter, cudaStream_t st);
 template <typename T> size_t stencil_smem_bytes(int rad);
+int stencil_tile_count(const LevelGeom &L);
 
 int launch_top_table(const LevelGeom &top, double a_top, double h_top, double *table, cudaStream_t st);
-template <typename T> int launch_top(const LevelGeom &top, const double *table, const T *qtop, double *utop,
+// utop: per system top_off; max_top = points of the largest top level
+template <typename T> int launch_top(const Batch &bt, int max_top, const double *table, const T *q, double *utop,
                                      const int *status, cudaStream_t st);
-// uc points at the first point of the coarse level (its own array or an offset
-// into the concatenated grids); ucut and uf are concatenated (fine.off applies).
-template <typename T, typename S> int launch_prolong(const LevelGeom &fine, const LevelGeom &coarse, const T *ucut,
-                                                      const S *uc, T *uf, const int *status, cudaStream_t st);
-void stencil_tiles(const LevelGeom &L, int t[3]);
+// u^k = u^{k,cut} + prolongation of u^{k+1} for level k of every system; the
+// coarse level is the FP64 top buffer when from_top, else the grid buffer.
+template <typename T> int launch_prolong(const Batch &bt, int k, int max_fine, const T *ucut, const double *utop,
+                                         bool from_top, T *u, const int *status, cudaStream_t st);
+// l = 1: the top level is level 0; copy it (to the compute type) into u.
+template <typename T> int launch_top_to_grid(const Batch &bt, int max_top, const double *utop, T *u,
+                                             const int *status, cudaStream_t st);
 int launch_cast_f64(int m, const double *src, float *dst, cudaStream_t st);
 int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t st);
 
 template <typename T> struct InterpArgs {
-    int n;
-    CellGeom cg;
-    LevelGeom L0;
+    Batch bt;
+    int max_n;
     const int *perm;
-    const int *akey;
+    const int *akey;       // global cell ids
     const vec4<T> *afrac;
     const vec4<T> *sr;
     const vec4<T> *lj;     // nullable
-    const T *u0;
-    const double *pos;     // n*3, original order (virial)
-    const double *q;       // n, original order
+    const T *u;            // concatenated grids
+    const double *pos;     // original order (virial, wall)
+    const double *q;       // original order
     double ke, self;       // k_e, gamma(0)/a
-    double inv_h;
-    double box_lo[3], box_hi[3];   // domain faces (wall of the water completion)
-    double wall_k, wall_w;         // wall_k = 0: no wall
-    double *forces;        // n*3, original order (nullable)
-    double *pot;           // n (nullable)
-    double *eatom;         // n: 1/2 q_i phi_i + 1/2 E_lj,i
-    double *vatom;         // n: r_i . F_i
+    double wall_k, wall_w; // wall_k = 0: no wall
+    double *forces;        // original order (nullable)
+    double *pot;           // (nullable)
+    double *eatom;         // 1/2 q_i phi_i + 1/2 E_lj,i
+    double *vatom;         // r_i . F_i
     const int *status;
 };
 template <typename T> int launch_interp(const InterpArgs<T> &a, cudaStream_t st);
 
 // ---- dynamics and reductions (k_md.cu) -------------------------------------
 struct ExclArgs {
-    int n_mol;
+    Batch bt;
+    int max_mol;
     const double *x;
     const double *q;
     double ke, a;
@@ -167,13 +182,16 @@ struct ExclArgs {
 };
 template <typename T> int launch_exclusions(const ExclArgs &a, cudaStream_t st);
 
-// Deterministic FP64 sum of m values per column (ncols arrays) into out[ncols].
-int launch_sum(int m, int ncols, const double *const *cols, double *partials, double *out, const int *status,
-               cudaStream_t st);
-int sum_partials_needed(int m);
+// Deterministic FP64 sums, per system: column c of system s sums its n values
+// in fixed chunks of SUM_CHUNK atoms (the same partition whatever the batch)
+// and writes out[s * out_stride + c].  part holds ncols * total_blocks values.
+int launch_sum(const Batch &bt, int max_n, int total_blocks, int ncols, const double *const *cols, double *part,
+               double *out, int out_stride, const int *status, cudaStream_t st);
+__host__ __device__ int sum_blocks(int n);
 
 struct VVArgs {
-    int n, n_mol;
+    Batch bt;
+    int max_units;         // molecules + single sites of the largest system
     double *x, *v;
     double *xo;            // scratch: positions before the drift
     const double *f, *m;
@@ -187,8 +205,11 @@ struct VVArgs {
 };
 template <typename T> int launch_vv_first(const VVArgs &a, cudaStream_t st);
 template <typename T> int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st);
-int launch_kinetic(const VVArgs &a, double *kin_atom, cudaStream_t st);
+int launch_kinetic(int n, const double *v, const double *m, double *kin_atom, cudaStream_t st);
 int launch_inverse(int n, const double *m, double *im, cudaStream_t st);
+// uk[s][step][2] <- (U_s, K_s) for every system; step from *ctr, then ++*ctr.
+int launch_record_uk(int B, const double *sums, int sums_stride, const double *kin, double *uk, int uk_stride,
+                     int *ctr, cudaStream_t st);
 
 int launch_parareal_update(int count, const double *f, const double *gnew, const double *gold, double *out,
                            const double *prev, double *dx_partials, cudaStream_t st);

@@ -1,8 +1,12 @@
 // msm_api.cu -- the C ABI of libmsm_gb300.so (declared in include/msm.h):
 // handle and scratch management, geometry and table set-up, and the
 // orchestration of one MSM evaluation (Sec. 3, worked example steps 1-9),
-// of velocity Verlet (Sec. 2) and of parareal (Sec. 4).
+// of velocity Verlet (Sec. 2) and of parareal (Sec. 4).  Every evaluation
+// and every MD step serves a batch of independent systems with one launch
+// per stage (a single system is the batch of one); MD steps after the first
+// replay a captured CUDA graph.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -18,6 +22,7 @@ using namespace msm;
 
 static thread_local char g_err[512] = "";
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_alloc_gen{0};     // bumped by every device (re)allocation
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -69,6 +74,7 @@ static int ensure(DevBuf &b, size_t bytes)
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
+    g_alloc_gen.fetch_add(1);
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -113,32 +119,72 @@ struct Profiler {
     long long cnt[N_STAGES] = {0};
 };
 
+// One system of a batch as the host sees it.
+struct SysIn {
+    int64_t n, n_mol;
+    double box[6];
+};
+
+// What a captured md step depends on: a replay is valid only while all of it
+// is unchanged (device buffers are identified by the allocation generation).
+struct GraphKey {
+    const void *x, *v, *f, *q, *m, *lj, *uk;
+    long long uk_stride, geom_gen, alloc_gen;
+    double dt;
+    int B, list_on;
+};
+
+// Brick shape chosen by timing, per system geometry (atoms, cells per axis).
+struct Tuned {
+    long long n;
+    int nc[3];
+    int bd[3];
+};
+
 struct msm_handle {
     msm_params p;
     Profiler prof;
     int precision;
-    // geometry of the current box
+    // batch geometry: B systems, concatenated atoms / cells / grids
     bool have_geom = false;
+    int B = 0;
+    std::vector<SysIn> sys_key;
+    std::vector<SysDesc> hsd;
+    std::vector<int> h_blk;
+    long long geom_gen = 0;
+    int N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, stiles = 0;
+    int max_n = 0, max_mol = 0, max_units = 0, max_bricks = 0, max_atiles = 0, max_top = 0;
+    int max_lev[MSM_MAX_LEVELS] = {0};
+    DevBuf sd_buf, blk_buf;
+    // system 0 of the batch (inspection and Verlet lists)
     double box[6] = {0, 0, 0, 0, 0, 0};
     CellGeom cg;
     GridGeom gg;
     double inv_h = 0;
     int bd[3] = {4, 2, 2}, nb[3] = {0, 0, 0}, nbricks = 0;
     int64_t last_n = 0;
+    // brick autotuner
+    std::vector<Tuned> tuned;
+    bool tune_pending = false;
     // tables
     bool stencil_ready = false;
     StencilGeom sg;
-    bool top_ready = false;
-    int top_n[3] = {0, 0, 0};
     // scratch
     DevBuf key, count, start, perm, bsum, rel, frac, apos, afrac, akey, aflag, sr, lj;
     DevBuf qgrid, ucut, ugrid, utop, ttop, wst_d, wst_t, rows;
-    DevBuf eatom, vatom, kin, partials, sums, status;
+    DevBuf eatom, vatom, kin, partials, sums, kin_s, status, ctr;
     DevBuf in_pos, in_q, in_lj, out_f, out_p;          // staging of host arrays
     DevBuf md_f, md_xo, md_x, md_v, md_q, md_m, md_lj, md_uk, md_im;
     int *h_status = nullptr;
     double *h_scal = nullptr;
-    // Verlet lists (md_run with list_skin > 0)
+    double *h_e = nullptr;                              // pinned, per-system energies
+    int h_e_cap = 0;
+    // CUDA graph of one md step
+    cudaStream_t cap_st = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    long long g_kernels = 0;                            // kernels per replayed step
+    // Verlet lists (md_run with list_skin > 0, single systems)
     bool list_on = false;
     DevBuf vl_perm, vl_start, vl_xref, vl_pos, grp_rows, grp_nrows, grp_j, vl_cnt, vl_cntlj, vl_nbr, vl_ctl;
     int vl_cap = 0, vl_jcap = 0, vl_rows = 0, vl_ngroups = 0;
@@ -208,6 +254,7 @@ extern "C" void msm_default_params(msm_params *p)
     p->gamma_kind = 0;
     p->basis_kind = 0;
     p->model = MSM_MODEL_CHARGES;
+    p->flags = MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE;
     p->lj_sigma = 0.315061;
     p->lj_epsilon = 0.6364;
     p->d_oh = 0.09572;
@@ -227,6 +274,7 @@ static int check_params(const msm_params *p)
     if (p->precision != MSM_FP32 && p->precision != MSM_FP64) return fail_msg(MSM_EINVAL, "unknown precision");
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
+    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE)) return fail_msg(MSM_EINVAL, "unknown flags");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
     int rad = 0;
@@ -244,6 +292,7 @@ extern "C" int msm_create(const msm_params *p, msm_handle **out)
     h->p = *p;
     if (!(h->p.coulomb_k > 0)) h->p.coulomb_k = 138.935458;
     h->precision = p->precision;
+    memset(&h->gkey, 0, sizeof h->gkey);
     cudaError_t e = cudaMallocHost(&h->h_status, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_scal, sizeof(double) * 8);
     if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(int) * 8);
@@ -263,15 +312,19 @@ extern "C" void msm_destroy(msm_handle *h)
     DevBuf *all[] = {&h->key, &h->count, &h->start, &h->perm, &h->bsum, &h->rel, &h->frac, &h->apos, &h->afrac,
                      &h->akey, &h->aflag, &h->sr, &h->lj, &h->qgrid, &h->ucut, &h->ugrid, &h->utop, &h->ttop,
                      &h->wst_d, &h->wst_t, &h->rows, &h->eatom, &h->vatom, &h->kin, &h->partials, &h->sums,
-                     &h->status, &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
+                     &h->kin_s, &h->status, &h->ctr, &h->sd_buf, &h->blk_buf,
+                     &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
                      &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk, &h->md_im,
                      &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->grp_rows, &h->grp_nrows,
                      &h->grp_j, &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_ctl};
     for (DevBuf *b : all) release(*b);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->h_e) cudaFreeHost(h->h_e);
     delete h;
 }
 
@@ -282,66 +335,183 @@ static int64_t floordiv64(int64_t a, int64_t b)
     return q;
 }
 
-// Grid extents per level (open boundaries): level 0 spans [-1, floor(L/h)+2];
-// level k+1 spans [ceil((lo-3)/2), floor((hi+3)/2)], every point with a
-// non-zero restriction weight from level k.
-static int set_geometry(msm_handle *h, const double box[6], cudaStream_t st)
+// Pinned host array of per-system energies, at least B entries.
+static int ensure_host_e(msm_handle *h, int B)
 {
-    for (int d = 0; d < 6; d++)
-        if (!std::isfinite(box[d])) return fail_msg(MSM_EINVAL, "box has a non-finite entry");
-    for (int d = 0; d < 3; d++)
-        if (!(box[3 + d] > 0)) return fail_msg(MSM_EINVAL, "box lengths must be positive");
-    if (h->have_geom && memcmp(box, h->box, sizeof(double) * 6) == 0) return MSM_OK;
-    const double hh = h->p.h;
-    CellGeom cg;
-    int64_t ncells = 1;
+    if (h->h_e_cap >= B) return MSM_OK;
+    if (h->h_e) cudaFreeHost(h->h_e);
+    h->h_e = nullptr;
+    h->h_e_cap = 0;
+    CUDA_TRY(cudaMallocHost(&h->h_e, sizeof(double) * (size_t)std::max(B, 8)));
+    h->h_e_cap = std::max(B, 8);
+    return MSM_OK;
+}
+
+// Brick shape for the short-range kernel: about 24 atoms per warp at the
+// system's mean density (one i atom per lane), unless the autotuner timed
+// this geometry.  The shape changes only the speed, never the results: each
+// i atom sums its j's in ascending slot order whatever the brick.
+static const int kBrickShapes[7][3] = {{1, 1, 1}, {2, 1, 1}, {2, 2, 1}, {2, 2, 2}, {4, 2, 2}, {4, 4, 2}, {4, 4, 4}};
+
+static int brick_heuristic(int64_t n, const CellGeom &g)
+{
+    const double per_cell = (double)n / (double)g.ncells;
+    int pick = 0;
+    for (int s = 0; s < 7; s++) {
+        const int vol = kBrickShapes[s][0] * kBrickShapes[s][1] * kBrickShapes[s][2];
+        if (per_cell * vol <= 24.0) pick = s;
+    }
+    return pick;
+}
+
+static void set_bricks(SysDesc &D, const int bd[3])
+{
     for (int d = 0; d < 3; d++) {
-        cg.origin[d] = box[d];
-        double nc = floor(box[3 + d] / hh) + 1.0;
-        if (nc > 4.0e6) return fail_msg(MSM_EINVAL, "box too large for h");
-        cg.nc[d] = (int)nc;
-        ncells *= cg.nc[d];
+        D.bd[d] = bd[d];
+        D.nb[d] = (D.g.nc[d] + bd[d] - 1) / bd[d];
     }
-    if (ncells > (int64_t)1 << 30) return fail_msg(MSM_EINVAL, "too many cells (%lld)", (long long)ncells);
-    cg.h = hh;
-    cg.ncells = (int)ncells;
-    GridGeom gg;
-    gg.levels = h->p.n_levels;
-    int64_t lo[3], hi[3], tot = 0;
-    for (int d = 0; d < 3; d++) { lo[d] = -1; hi[d] = (int64_t)floor(box[3 + d] / hh) + 2; }
-    for (int k = 0; k < gg.levels; k++) {
-        if (k > 0)
-            for (int d = 0; d < 3; d++) { lo[d] = -floordiv64(-(lo[d] - 3), 2); hi[d] = floordiv64(hi[d] + 3, 2); }
-        int64_t sz = 1;
-        for (int d = 0; d < 3; d++) { gg.L[k].lo[d] = (int)lo[d]; gg.L[k].n[d] = (int)(hi[d] - lo[d] + 1); sz *= gg.L[k].n[d]; }
-        gg.L[k].off = (int)tot;
-        tot += sz;
+    D.nbricks = D.nb[0] * D.nb[1] * D.nb[2];
+}
+
+static const Tuned *find_tuned(const msm_handle *h, int64_t n, const CellGeom &g)
+{
+    for (const Tuned &t : h->tuned)
+        if (t.n == n && t.nc[0] == g.nc[0] && t.nc[1] == g.nc[1] && t.nc[2] == g.nc[2]) return &t;
+    return nullptr;
+}
+
+// Geometry of a batch of systems: cells, grid levels and bricks per system,
+// their offsets in the concatenated buffers, the top-level tables (one per
+// distinct top shape) and the lattice-cutoff tile offsets of every (system,
+// level).  Grid extents per level (open boundaries): level 0 spans
+// [-1, floor(L/h)+2]; level k+1 spans [ceil((lo-3)/2), floor((hi+3)/2)], every
+// point with a non-zero restriction weight from level k.  Nothing is redone
+// while the systems' atom counts and boxes stay the same.
+static int ensure_atoms(msm_handle *h, int64_t n);
+
+static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
+{
+    if (B < 1) return fail_msg(MSM_EINVAL, "a batch needs at least one system");
+    for (int s = 0; s < B; s++) {
+        const SysIn &S = sys[s];
+        for (int d = 0; d < 6; d++)
+            if (!std::isfinite(S.box[d])) return fail_msg(MSM_EINVAL, "box of system %d has a non-finite entry", s);
+        for (int d = 0; d < 3; d++)
+            if (!(S.box[3 + d] > 0)) return fail_msg(MSM_EINVAL, "box lengths must be positive (system %d)", s);
+        if (S.n < 0 || S.n > ((int64_t)1 << 30)) return fail_msg(MSM_EINVAL, "atom count %lld out of range", (long long)S.n);
+        if (S.n_mol < 0 || 3 * S.n_mol > S.n) return fail_msg(MSM_EINVAL, "n_mol inconsistent with n (system %d)", s);
     }
-    if (tot > (int64_t)1 << 30) return fail_msg(MSM_EINVAL, "grids too large");
-    gg.total = (int)tot;
-    h->cg = cg;
-    h->gg = gg;
-    h->inv_h = 1.0 / hh;
-    memcpy(h->box, box, sizeof(double) * 6);
-    h->have_geom = true;
+    bool same = h->have_geom && B == h->B && !h->tune_pending;
+    for (int s = 0; same && s < B; s++)
+        same = sys[s].n == h->sys_key[s].n && sys[s].n_mol == h->sys_key[s].n_mol &&
+               memcmp(sys[s].box, h->sys_key[s].box, sizeof sys[s].box) == 0;
+    if (same) return MSM_OK;
+
+    const double hh = h->p.h;
+    const int l = h->p.n_levels;
+    std::vector<SysDesc> d((size_t)B);
+    std::vector<std::array<int, 4>> tops;          // (nx, ny, nz, table offset)
+    int64_t N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, ST = 0;
+    bool pending = false;
+    h->h_blk.clear();
+    for (int s = 0; s < B; s++) {
+        SysDesc &D = d[(size_t)s];
+        memset(&D, 0, sizeof D);
+        const SysIn &S = sys[s];
+        int64_t ncells = 1;
+        for (int k = 0; k < 3; k++) {
+            D.g.origin[k] = S.box[k];
+            const double nc = floor(S.box[3 + k] / hh) + 1.0;
+            if (nc > 4.0e6) return fail_msg(MSM_EINVAL, "box too large for h");
+            D.g.nc[k] = (int)nc;
+            ncells *= D.g.nc[k];
+            D.box_lo[k] = S.box[k];
+            D.box_hi[k] = S.box[k] + S.box[3 + k];
+        }
+        if (ncells > (int64_t)1 << 30) return fail_msg(MSM_EINVAL, "too many cells (%lld)", (long long)ncells);
+        D.g.h = hh;
+        D.g.ncells = (int)ncells;
+        D.inv_h = 1.0 / hh;
+        D.gg.levels = l;
+        int64_t lo[3], hi[3], tot = 0;
+        for (int k = 0; k < 3; k++) { lo[k] = -1; hi[k] = (int64_t)floor(S.box[3 + k] / hh) + 2; }
+        for (int k = 0; k < l; k++) {
+            if (k > 0)
+                for (int e = 0; e < 3; e++) { lo[e] = -floordiv64(-(lo[e] - 3), 2); hi[e] = floordiv64(hi[e] + 3, 2); }
+            int64_t sz = 1;
+            for (int e = 0; e < 3; e++) {
+                D.gg.L[k].lo[e] = (int)lo[e];
+                D.gg.L[k].n[e] = (int)(hi[e] - lo[e] + 1);
+                sz *= D.gg.L[k].n[e];
+            }
+            D.gg.L[k].off = (int)tot;
+            tot += sz;
+        }
+        if (tot > (int64_t)1 << 30) return fail_msg(MSM_EINVAL, "grids too large");
+        D.gg.total = (int)tot;
+        D.atom_off = (int)N;
+        D.n = (int)S.n;
+        D.n_mol = (int)S.n_mol;
+        N += S.n;
+        D.cell_off = (int)M;
+        M += ncells;
+        const Tuned *t = (h->p.flags & MSM_FLAG_AUTOTUNE) ? find_tuned(h, S.n, D.g) : nullptr;
+        if (t) set_bricks(D, t->bd);
+        else {
+            set_bricks(D, kBrickShapes[brick_heuristic(S.n, D.g)]);
+            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && B == 1 && S.n > 0) pending = true;
+        }
+        D.grid_off = (int)G;
+        G += tot;
+        const LevelGeom &Lt = D.gg.L[l - 1];
+        D.top_off = (int)UT;
+        UT += (int64_t)Lt.n[0] * Lt.n[1] * Lt.n[2];
+        int found = -1;
+        for (size_t k = 0; k < tops.size(); k++)
+            if (tops[k][0] == Lt.n[0] && tops[k][1] == Lt.n[1] && tops[k][2] == Lt.n[2]) found = (int)k;
+        if (found < 0) {
+            tops.push_back({Lt.n[0], Lt.n[1], Lt.n[2], (int)TT});
+            TT += (int64_t)(2 * Lt.n[0] - 1) * (2 * Lt.n[1] - 1) * (2 * Lt.n[2] - 1);
+            found = (int)tops.size() - 1;
+        }
+        D.ttab_off = tops[(size_t)found][3];
+        D.part_off = (int)PB;
+        PB += sum_blocks((int)S.n);
+        for (int k = 0; k + 1 < l; k++) {
+            h->h_blk.push_back((int)ST);
+            ST += stencil_tile_count(D.gg.L[k]);
+        }
+    }
+    h->h_blk.push_back((int)ST);
+    const int64_t lim = ((int64_t)1 << 31) - 1;
+    if (N > ((int64_t)1 << 30) || M >= lim || G >= lim || UT >= lim || TT >= lim || ST >= lim)
+        return fail_msg(MSM_EINVAL, "batch too large for 32-bit offsets");
 
     const size_t ts = h->precision == MSM_FP32 ? sizeof(float) : sizeof(double);
-    TRY(ensure(h->count, sizeof(int) * (size_t)(ncells + 1)));
-    TRY(ensure(h->start, sizeof(int) * (size_t)(ncells + 1)));
+    TRY(ensure(h->count, sizeof(int) * (size_t)(M + 1)));
+    TRY(ensure(h->start, sizeof(int) * (size_t)(M + 1)));
     TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints()));
-    TRY(ensure(h->qgrid, ts * (size_t)tot));
-    TRY(ensure(h->ucut, ts * (size_t)tot));
-    TRY(ensure(h->ugrid, ts * (size_t)tot));
-    const LevelGeom &top = gg.L[gg.levels - 1];
-    TRY(ensure(h->utop, sizeof(double) * (size_t)top.n[0] * top.n[1] * top.n[2]));
-    // top-level Toeplitz table g^{l-1} over all offsets (FP64), rebuilt when its extent changes
-    if (!h->top_ready || memcmp(h->top_n, top.n, sizeof h->top_n) != 0) {
-        const size_t m = (size_t)(2 * top.n[0] - 1) * (2 * top.n[1] - 1) * (2 * top.n[2] - 1);
-        TRY(ensure(h->ttop, sizeof(double) * m));
-        const double sc = ldexp(1.0, gg.levels - 1);
-        TRY(launch_top_table(top, sc * h->p.a, sc * hh, h->ttop.as<double>(), st));
-        memcpy(h->top_n, top.n, sizeof h->top_n);
-        h->top_ready = true;
+    TRY(ensure(h->qgrid, ts * (size_t)G));
+    TRY(ensure(h->ucut, ts * (size_t)G));
+    TRY(ensure(h->ugrid, ts * (size_t)G));
+    TRY(ensure(h->utop, sizeof(double) * (size_t)UT));
+    TRY(ensure(h->ttop, sizeof(double) * (size_t)TT));
+    TRY(ensure(h->partials, sizeof(double) * 4 * (size_t)PB));
+    TRY(ensure(h->sums, sizeof(double) * 4 * (size_t)B));
+    TRY(ensure(h->kin_s, sizeof(double) * (size_t)B));
+    TRY(ensure(h->status, sizeof(int) * 4));
+    TRY(ensure(h->ctr, sizeof(int) * 4));
+    TRY(ensure(h->sd_buf, sizeof(SysDesc) * (size_t)B));
+    TRY(ensure(h->blk_buf, sizeof(int) * h->h_blk.size()));
+    TRY(ensure_atoms(h, N));
+    TRY(ensure_host_e(h, B));
+    // top-level Toeplitz tables g^{l-1} over all offsets (FP64), one per distinct top shape
+    const double sc = ldexp(1.0, l - 1);
+    for (const std::array<int, 4> &t : tops) {
+        LevelGeom Lt;
+        memset(&Lt, 0, sizeof Lt);
+        for (int e = 0; e < 3; e++) Lt.n[e] = t[(size_t)e];
+        TRY(launch_top_table(Lt, sc * h->p.a, sc * hh, h->ttop.as<double>() + t[3], st));
     }
     // lattice-cutoff weights W[n] = g^0(|n| h), |n| h < 2a, and the rows of the tap sphere
     if (!h->stencil_ready) {
@@ -370,25 +540,38 @@ static int set_geometry(msm_handle *h, const double box[6], cudaStream_t st)
         CUDA_TRY(cudaStreamSynchronize(st));      // rows lives on the host stack
         h->stencil_ready = true;
     }
-    return MSM_OK;
-}
+    h->hsd.swap(d);
+    CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, h->hsd.data(), sizeof(SysDesc) * (size_t)B, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(h->blk_buf.p, h->h_blk.data(), sizeof(int) * h->h_blk.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));          // the host copies may change with the next batch
 
-// Brick shape for the short-range kernel: about 24 atoms per warp at the
-// system's mean density (one i atom per lane).
-static void choose_bricks(msm_handle *h, int64_t n)
-{
-    static const int shapes[7][3] = {{1, 1, 1}, {2, 1, 1}, {2, 2, 1}, {2, 2, 2}, {4, 2, 2}, {4, 4, 2}, {4, 4, 4}};
-    const double per_cell = (double)n / (double)h->cg.ncells;
-    int pick = 0;
-    for (int s = 0; s < 7; s++) {
-        const int vol = shapes[s][0] * shapes[s][1] * shapes[s][2];
-        if (per_cell * vol <= 24.0) pick = s;
+    h->B = B;
+    h->N = (int)N; h->M = (int)M; h->G = (int)G; h->UT = (int)UT; h->TT = (int)TT; h->PB = (int)PB;
+    h->stiles = (int)ST;
+    h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = 0;
+    for (int k = 0; k < MSM_MAX_LEVELS; k++) h->max_lev[k] = 0;
+    for (const SysDesc &D : h->hsd) {
+        h->max_n = std::max(h->max_n, D.n);
+        h->max_mol = std::max(h->max_mol, D.n_mol);
+        h->max_units = std::max(h->max_units, D.n_mol + (D.n - 3 * D.n_mol));
+        h->max_bricks = std::max(h->max_bricks, D.nbricks);
+        h->max_atiles = std::max(h->max_atiles, anterp_tiles(D.gg.L[0]));
+        for (int k = 0; k < l; k++) h->max_lev[k] = std::max(h->max_lev[k], D.gg.L[k].n[0] * D.gg.L[k].n[1] * D.gg.L[k].n[2]);
     }
-    for (int d = 0; d < 3; d++) {
-        h->bd[d] = shapes[pick][d];
-        h->nb[d] = (h->cg.nc[d] + h->bd[d] - 1) / h->bd[d];
-    }
-    h->nbricks = h->nb[0] * h->nb[1] * h->nb[2];
+    h->max_top = h->max_lev[l - 1];
+    const SysDesc &D0 = h->hsd[0];
+    h->cg = D0.g;
+    h->gg = D0.gg;
+    h->inv_h = D0.inv_h;
+    memcpy(h->box, sys[0].box, sizeof h->box);
+    for (int k = 0; k < 3; k++) { h->bd[k] = D0.bd[k]; h->nb[k] = D0.nb[k]; }
+    h->nbricks = D0.nbricks;
+    h->last_n = sys[0].n;
+    h->sys_key.assign(sys, sys + B);
+    h->tune_pending = pending;
+    h->have_geom = true;
+    h->geom_gen++;
+    return MSM_OK;
 }
 
 static int ensure_atoms(msm_handle *h, int64_t n)
@@ -404,46 +587,22 @@ static int ensure_atoms(msm_handle *h, int64_t n)
     TRY(ensure(h->apos, 4 * ts * nn));
     TRY(ensure(h->afrac, 4 * ts * nn));
     TRY(ensure(h->sr, 4 * ts * nn));
+    if (h->p.model == MSM_MODEL_WATER) TRY(ensure(h->lj, 4 * ts * nn));
     TRY(ensure(h->eatom, sizeof(double) * nn));
     TRY(ensure(h->vatom, sizeof(double) * nn));
     TRY(ensure(h->kin, sizeof(double) * nn));
-    TRY(ensure(h->partials, sizeof(double) * 4 * (size_t)sum_partials_needed((int)nn)));
-    TRY(ensure(h->sums, sizeof(double) * 8));
-    TRY(ensure(h->status, sizeof(int) * 4));
     return MSM_OK;
 }
 
-// One evaluation on device arrays.  eatom/vatom get per-atom energy and
-// virial; sums[0] = U, sums[1] = virial.  No host synchronisation.
-struct EvalIO {
-    int64_t n;
-    const double *pos, *q;
-    const uint8_t *lj;       // nullable (device)
-    int64_t n_mol;           // rigid triples for the exclusions (model 1)
-    double *forces, *pot;    // device, nullable
-};
+static Batch batch_of(const msm_handle *h) { return Batch{h->B, h->sd_buf.as<SysDesc>()}; }
 
+// Arguments of the short-range kernels for the current batch.
 template <typename T>
-static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
+static ShortArgs<T> short_args(msm_handle *h)
 {
-    const int n = (int)io.n;
-    int *status = h->status.as<int>();
-    const bool model = h->p.model == MSM_MODEL_WATER;
-    if (model) TRY(ensure(h->lj, sizeof(vec4<T>) * (size_t)(n > 0 ? n : 1)));
-
-    BinArgs<T> b;
-    b.n = n; b.pos = io.pos; b.q = io.q; b.lj = io.lj; b.g = h->cg; b.inv_h = h->inv_h;
-    b.key = h->key.as<int>(); b.count = h->count.as<int>(); b.start = h->start.as<int>(); b.perm = h->perm.as<int>();
-    b.bsum = h->bsum.as<int>(); b.rel = h->rel.as<vec4<T>>(); b.frac = h->frac.as<vec4<T>>();
-    b.apos = h->apos.as<vec4<T>>(); b.afrac = h->afrac.as<vec4<T>>(); b.akey = h->akey.as<int>();
-    b.aflag = h->aflag.as<int>(); b.n_mol = model ? (int)io.n_mol : 0; b.status = status;
-    { PROF(ST_BIN); TRY(launch_bin<T>(b, st)); }
-
-    // step 1: short range
     ShortArgs<T> s;
-    s.g = h->cg;
-    for (int d = 0; d < 3; d++) { s.bd[d] = h->bd[d]; s.nb[d] = h->nb[d]; }
-    s.nbricks = h->nbricks;
+    s.bt = batch_of(h);
+    s.max_bricks = h->max_bricks;
     s.start = h->start.as<int>(); s.apos = h->apos.as<vec4<T>>(); s.aflag = h->aflag.as<int>();
     const double a = h->p.a;
     s.a = (T)a; s.a2 = (T)(a * a); s.a_sel = (T)(a + 1e-3 * h->p.h);
@@ -454,11 +613,94 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     s.lj_s2 = (T)sg2; s.lj_4eps = (T)(4.0 * h->p.lj_epsilon); s.lj_24eps = (T)(24.0 * h->p.lj_epsilon);
     s.lj_shift = (T)(4.0 * h->p.lj_epsilon * (sa6 * sa6 - sa6));
     s.perm = h->perm.as<int>();
-    s.sr = h->sr.as<vec4<T>>(); s.lj = model ? h->lj.as<vec4<T>>() : nullptr; s.cnt = nullptr; s.status = status;
+    s.sr = h->sr.as<vec4<T>>();
+    s.lj = h->p.model == MSM_MODEL_WATER ? h->lj.as<vec4<T>>() : nullptr;
+    s.cnt = nullptr;
+    s.vl_ctl = nullptr;
+    s.status = h->status.as<int>();
+    return s;
+}
+
+// The brick autotuner: on the first evaluation of a single system's geometry,
+// time the short-range kernel for the brick shapes around the heuristic's
+// choice (after binning, on the real atoms) and keep the fastest.  It runs
+// outside any graph capture and synchronises the stream.
+template <typename T>
+static int autotune_bricks(msm_handle *h, cudaStream_t st)
+{
+    h->tune_pending = false;
+    SysDesc &D = h->hsd[0];
+    const int h0 = brick_heuristic(D.n, D.g);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_s = h0;
+    const bool model = h->p.model == MSM_MODEL_WATER;
+    for (int sidx = std::max(0, h0 - 1); sidx <= std::min(6, h0 + 1); sidx++) {
+        set_bricks(D, kBrickShapes[sidx]);
+        CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+        ShortArgs<T> s = short_args<T>(h);
+        s.max_bricks = D.nbricks;
+        TRY(launch_short<T>(s, model, st));                 // warm
+        CUDA_TRY(cudaEventRecord(e0, st));
+        TRY(launch_short<T>(s, model, st));
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_s = sidx; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_bricks(D, kBrickShapes[best_s]);
+    CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    Tuned t;
+    t.n = D.n;
+    for (int k = 0; k < 3; k++) { t.nc[k] = D.g.nc[k]; t.bd[k] = D.bd[k]; }
+    h->tuned.push_back(t);
+    h->max_bricks = D.nbricks;
+    for (int k = 0; k < 3; k++) { h->bd[k] = D.bd[k]; h->nb[k] = D.nb[k]; }
+    h->nbricks = D.nbricks;
+    h->geom_gen++;
+    return MSM_OK;
+}
+
+// One evaluation of the current batch on device arrays (systems concatenated).
+// eatom/vatom get per-atom energy and virial; sums[4 s + 0] = U_s,
+// sums[4 s + 1] = virial_s.  No host synchronisation (except the autotuner's,
+// once per geometry).
+struct EvalIO {
+    const double *pos, *q;
+    const uint8_t *lj;       // nullable (device)
+    double *forces, *pot;    // device, nullable
+};
+
+template <typename T>
+static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
+{
+    int *status = h->status.as<int>();
+    const bool model = h->p.model == MSM_MODEL_WATER;
+    const Batch bt = batch_of(h);
+
+    BinArgs<T> b;
+    b.bt = bt; b.n_total = h->N; b.m_total = h->M; b.max_n = h->max_n;
+    b.pos = io.pos; b.q = io.q; b.lj = io.lj;
+    b.key = h->key.as<int>(); b.count = h->count.as<int>(); b.start = h->start.as<int>(); b.perm = h->perm.as<int>();
+    b.bsum = h->bsum.as<int>(); b.rel = h->rel.as<vec4<T>>(); b.frac = h->frac.as<vec4<T>>();
+    b.apos = h->apos.as<vec4<T>>(); b.afrac = h->afrac.as<vec4<T>>(); b.akey = h->akey.as<int>();
+    b.aflag = h->aflag.as<int>(); b.status = status;
+    { PROF(ST_BIN); TRY(launch_bin<T>(b, st)); }
+    if (h->tune_pending) TRY(autotune_bricks<T>(h, st));
+
+    // step 1: short range
+    ShortArgs<T> s = short_args<T>(h);
     s.vl_ctl = h->list_on ? h->vl_ctl.as<int>() : nullptr;
     {
         ListArgs<T> la;
         if (h->list_on) {
+            const double a = h->p.a;
             la.g = h->cg;
             for (int d = 0; d < 3; d++) { la.bd[d] = h->bd[d]; la.nb[d] = h->nb[d]; }
             la.ng[0] = h->nb[0]; la.ng[1] = (h->nb[1] + 1) / 2; la.ng[2] = (h->nb[2] + 1) / 2;
@@ -469,7 +711,7 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             la.skin_half2 = (T)(0.25 * h->p.list_skin * h->p.list_skin);
             la.c0 = s.c0; la.c1 = s.c1; la.c2 = s.c2; la.d0 = s.d0; la.d1 = s.d1;
             la.lj_s2 = s.lj_s2; la.lj_4eps = s.lj_4eps; la.lj_24eps = s.lj_24eps; la.lj_shift = s.lj_shift;
-            la.model = model; la.n = n; la.x = io.pos; la.q = io.q;
+            la.model = model; la.n = h->N; la.x = io.pos; la.q = io.q;
             la.perm = h->perm.as<int>(); la.start = h->start.as<int>(); la.apos = h->apos.as<vec4<T>>();
             la.aflag = h->aflag.as<int>();
             la.vl_perm = h->vl_perm.as<int>(); la.vl_start = h->vl_start.as<int>(); la.vl_xref = h->vl_xref.as<double>();
@@ -488,76 +730,64 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     // step 2: anterpolation
     T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
     AnterpArgs<T> an;
-    an.cg = h->cg; an.L0 = h->gg.L[0]; an.start = h->start.as<int>(); an.afrac = h->afrac.as<vec4<T>>();
-    an.q0 = qg; an.status = status;
+    an.bt = bt; an.max_tiles = h->max_atiles; an.start = h->start.as<int>(); an.afrac = h->afrac.as<vec4<T>>();
+    an.q = qg; an.status = status;
     { PROF(ST_ANTERP); TRY(launch_anterp<T>(an, st)); }
 
     // steps 3-4: restriction down the levels, then the lattice cutoff of levels 0..l-2 in one launch
-    const int l = h->gg.levels;
+    const int l = h->p.n_levels;
     {
         PROF(ST_RESTRICT);
-        for (int k = 0; k + 1 < l; k++) TRY(launch_restrict<T>(h->gg.L[k], h->gg.L[k + 1], qg, qg, status, st));
+        for (int k = 0; k + 1 < l; k++) TRY(launch_restrict<T>(bt, k, h->max_lev[k + 1], qg, status, st));
     }
     if (l > 1) {
         StencilArgs<T> sa;
-        sa.gg = h->gg; sa.nlev = l - 1; sa.sg = h->sg;
-        sa.blk_off[0] = 0;
-        for (int k = 0; k < l - 1; k++) {
-            stencil_tiles(h->gg.L[k], sa.tiles[k]);
-            sa.blk_off[k + 1] = sa.blk_off[k] + sa.tiles[k][0] * sa.tiles[k][1] * sa.tiles[k][2];
-        }
+        sa.bt = bt; sa.nlev = l - 1; sa.blk_off = h->blk_buf.as<int>(); sa.total_tiles = h->stiles; sa.sg = h->sg;
         sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
         PROF(ST_STENCIL);
         TRY(launch_stencil<T>(sa, h->status.as<int>() + 2, st));
     }
     // step 5: top level in FP64
-    const LevelGeom &top = h->gg.L[l - 1];
-    { PROF(ST_TOP); TRY(launch_top<T>(top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
+    { PROF(ST_TOP); TRY(launch_top<T>(bt, h->max_top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
     // steps 6-7: prolongation back to level 0
     {
         PROF(ST_PROLONG);
         if (l == 1) {
-            const int m = top.n[0] * top.n[1] * top.n[2];
-            if (sizeof(T) == sizeof(float)) TRY(launch_cast_f64(m, h->utop.as<double>(), reinterpret_cast<float *>(ug), st));
-            else CUDA_TRY(cudaMemcpyAsync(ug, h->utop.p, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+            TRY(launch_top_to_grid<T>(bt, h->max_top, h->utop.as<double>(), ug, status, st));
         } else {
-            TRY((launch_prolong<T, double>(h->gg.L[l - 2], top, uc, h->utop.as<double>(), ug, status, st)));
+            TRY(launch_prolong<T>(bt, l - 2, h->max_lev[l - 2], uc, h->utop.as<double>(), true, ug, status, st));
             for (int k = l - 3; k >= 0; k--)
-                TRY((launch_prolong<T, T>(h->gg.L[k], h->gg.L[k + 1], uc, ug + h->gg.L[k + 1].off, ug, status, st)));
+                TRY(launch_prolong<T>(bt, k, h->max_lev[k], uc, h->utop.as<double>(), false, ug, status, st));
         }
     }
     // step 8-9: interpolation, totals, scatter to the caller's order
     InterpArgs<T> ia;
-    ia.n = n; ia.cg = h->cg; ia.L0 = h->gg.L[0]; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
+    ia.bt = bt; ia.max_n = h->max_n; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
     ia.afrac = h->afrac.as<vec4<T>>(); ia.sr = h->sr.as<vec4<T>>(); ia.lj = model ? h->lj.as<vec4<T>>() : nullptr;
-    ia.u0 = ug; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k; ia.self = GAMMA_C0 / a; ia.inv_h = h->inv_h;
-    for (int d = 0; d < 3; d++) { ia.box_lo[d] = h->box[d]; ia.box_hi[d] = h->box[d] + h->box[3 + d]; }
+    ia.u = ug; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k; ia.self = GAMMA_C0 / h->p.a;
     ia.wall_k = model ? h->p.wall_k : 0.0; ia.wall_w = h->p.wall_width;
     ia.forces = io.forces; ia.pot = io.pot; ia.eatom = h->eatom.as<double>(); ia.vatom = h->vatom.as<double>();
     ia.status = status;
     { PROF(ST_INTERP); TRY(launch_interp<T>(ia, st)); }
     PROF(ST_SUMS);
-    if (h->p.model == MSM_MODEL_WATER && io.n_mol > 0) {
+    if (model && h->max_mol > 0) {
         ExclArgs ex;
-        ex.n_mol = (int)io.n_mol; ex.x = io.pos; ex.q = io.q; ex.ke = h->p.coulomb_k; ex.a = h->p.a;
+        ex.bt = bt; ex.max_mol = h->max_mol; ex.x = io.pos; ex.q = io.q; ex.ke = h->p.coulomb_k; ex.a = h->p.a;
         ex.forces = io.forces; ex.pot = io.pot; ex.eatom = h->eatom.as<double>(); ex.vatom = h->vatom.as<double>();
         ex.status = status;
         TRY(launch_exclusions<T>(ex, st));
     }
     const double *cols[2] = {h->eatom.as<double>(), h->vatom.as<double>()};
-    TRY(launch_sum(n, 2, cols, h->partials.as<double>(), h->sums.as<double>(), status, st));
+    TRY(launch_sum(bt, h->max_n, h->PB, 2, cols, h->partials.as<double>(), h->sums.as<double>(), 4, status, st));
     return MSM_OK;
 }
 
-static int evaluate(msm_handle *h, const EvalIO &io, const double box[6], cudaStream_t st)
+static int evaluate(msm_handle *h, const EvalIO &io, int B, const SysIn *sys, cudaStream_t st)
 {
-    if (io.n < 0 || io.n > (int64_t)1 << 30) return fail_msg(MSM_EINVAL, "atom count %lld out of range", (long long)io.n);
-    if (h->p.model == MSM_MODEL_WATER && (io.n_mol < 0 || 3 * io.n_mol > io.n))
-        return fail_msg(MSM_EINVAL, "n_mol inconsistent with n");
-    TRY(set_geometry(h, box, st));
-    TRY(ensure_atoms(h, io.n));
-    choose_bricks(h, io.n);            // follows every change of n or of the box
-    h->last_n = io.n;
+    if (h->p.model != MSM_MODEL_WATER)
+        for (int s = 0; s < B; s++)
+            if (sys[s].n_mol) return fail_msg(MSM_EINVAL, "rigid molecules need the water model");
+    TRY(set_batch(h, B, sys, st));
     CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int) * 4, st));
     if (h->precision == MSM_FP32) return evaluate_t<float>(h, io, st);
     return evaluate_t<double>(h, io, st);
@@ -594,24 +824,29 @@ static int stage_in(DevBuf &buf, const void *src, size_t bytes, const void **dev
     return MSM_OK;
 }
 
-static int copy_scalar(double *dst, const double *dev_src, cudaStream_t st)
+// Per-system column c of sums (stride 4) to dst[0..B-1] (device or host).
+static int copy_sums(double *dst, const msm_handle *h, int c, cudaStream_t st)
 {
     if (!dst) return MSM_OK;
-    CUDA_TRY(cudaMemcpyAsync(dst, dev_src, sizeof(double), cudaMemcpyDefault, st));
+    CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(double), h->sums.as<double>() + c, 4 * sizeof(double), sizeof(double),
+                               (size_t)h->B, cudaMemcpyDefault, st));
     return MSM_OK;
 }
 
-static int forces_impl(msm_handle *h, int64_t n, int64_t n_mol, const double *pos, const double *q,
-                       const uint8_t *lj, const double box[6], double *energy, double *forces, double *pot,
-                       double *virial, cudaStream_t st)
+// One evaluation of B systems whose per-atom arrays are concatenated.
+static int forces_impl(msm_handle *h, int B, const SysIn *sys, const double *pos, const double *q,
+                       const uint8_t *lj, double *energies, double *forces, double *pot, double *virials,
+                       cudaStream_t st)
 {
     if (!h) return fail_msg(MSM_EINVAL, "handle is NULL");
-    if (!box) return fail_msg(MSM_EINVAL, "box is NULL");
-    if (n < 0) return fail_msg(MSM_EINVAL, "n < 0");
+    int64_t n = 0;
+    for (int s = 0; s < B; s++) {
+        if (sys[s].n < 0) return fail_msg(MSM_EINVAL, "n < 0");
+        n += sys[s].n;
+    }
     if (n > 0 && (!pos || !q)) return fail_msg(MSM_EINVAL, "pos and q are required");
     const size_t nn = (size_t)n;
     EvalIO io;
-    io.n = n; io.n_mol = n_mol;
     const void *dp, *dq, *dl;
     TRY(stage_in(h->in_pos, pos, sizeof(double) * 3 * nn, &dp, st));
     TRY(stage_in(h->in_q, q, sizeof(double) * nn, &dq, st));
@@ -622,11 +857,11 @@ static int forces_impl(msm_handle *h, int64_t n, int64_t n_mol, const double *po
     if (p_host) TRY(ensure(h->out_p, sizeof(double) * nn));
     io.forces = f_host ? h->out_f.as<double>() : forces;
     io.pot = p_host ? h->out_p.as<double>() : pot;
-    TRY(evaluate(h, io, box, st));
+    TRY(evaluate(h, io, B, sys, st));
     if (f_host && n > 0) CUDA_TRY(cudaMemcpyAsync(forces, h->out_f.p, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost, st));
     if (p_host && n > 0) CUDA_TRY(cudaMemcpyAsync(pot, h->out_p.p, sizeof(double) * nn, cudaMemcpyDeviceToHost, st));
-    TRY(copy_scalar(energy, h->sums.as<double>(), st));
-    TRY(copy_scalar(virial, h->sums.as<double>() + 1, st));
+    TRY(copy_sums(energies, h, 0, st));
+    TRY(copy_sums(virials, h, 1, st));
     return finish(h, st);
 }
 
@@ -635,47 +870,53 @@ extern "C" int msm_energy_forces(msm_handle *h, int64_t n, const double *pos, co
 {
     if (h && h->p.model != MSM_MODEL_CHARGES)
         return fail_msg(MSM_EINVAL, "msm_energy_forces evaluates point charges; use msm_system_forces for the water model");
-    return forces_impl(h, n, 0, pos, q, nullptr, box, energy, forces, potentials, virial, (cudaStream_t)stream);
+    if (!box) return fail_msg(MSM_EINVAL, "box is NULL");
+    SysIn s;
+    s.n = n; s.n_mol = 0;
+    memcpy(s.box, box, sizeof s.box);
+    return forces_impl(h, 1, &s, pos, q, nullptr, energy, forces, potentials, virial, (cudaStream_t)stream);
 }
 
 extern "C" int msm_system_forces(msm_handle *h, const msm_system *sys, double *energy, double *forces,
                                  double *potentials, void *stream)
 {
     if (!sys) return fail_msg(MSM_EINVAL, "system is NULL");
-    return forces_impl(h, sys->n, sys->n_mol, sys->x, sys->q, sys->lj, sys->box, energy, forces, potentials,
-                       nullptr, (cudaStream_t)stream);
+    SysIn s;
+    s.n = sys->n; s.n_mol = sys->n_mol;
+    memcpy(s.box, sys->box, sizeof s.box);
+    return forces_impl(h, 1, &s, sys->x, sys->q, sys->lj, energy, forces, potentials, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int msm_energy_forces_batched(msm_handle *h, int32_t n_sys, const int64_t *offsets, const double *pos,
                                          const double *q, const double *boxes, double *energies, double *forces,
                                          double *potentials, void *stream)
 {
-    if (!h || n_sys < 0 || (n_sys > 0 && (!offsets || !boxes))) return fail_msg(MSM_EINVAL, "bad batched arguments");
+    if (!h || n_sys < 1 || !offsets || !boxes) return fail_msg(MSM_EINVAL, "bad batched arguments");
     if (h->p.model != MSM_MODEL_CHARGES) return fail_msg(MSM_EINVAL, "batched evaluation takes point charges");
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool e_dev = energies && on_device(energies);
+    if (offsets[0] != 0) return fail_msg(MSM_EINVAL, "offsets must start at 0");
+    std::vector<SysIn> sys((size_t)n_sys);
     for (int s = 0; s < n_sys; s++) {
-        const int64_t o = offsets[s], m = offsets[s + 1] - offsets[s];
-        if (o < 0 || m < 0) return fail_msg(MSM_EINVAL, "offsets must be non-decreasing from 0");
-        double *e = energies ? (e_dev ? energies + s : &h->h_scal[2]) : nullptr;
-        TRY(forces_impl(h, m, 0, pos + 3 * o, q + o, nullptr, boxes + 6 * s, e, forces ? forces + 3 * o : nullptr,
-                        potentials ? potentials + o : nullptr, nullptr, st));
-        if (energies && !e_dev) energies[s] = h->h_scal[2];
+        if (offsets[s + 1] < offsets[s]) return fail_msg(MSM_EINVAL, "offsets must be non-decreasing from 0");
+        sys[(size_t)s].n = offsets[s + 1] - offsets[s];
+        sys[(size_t)s].n_mol = 0;
+        memcpy(sys[(size_t)s].box, boxes + 6 * s, sizeof sys[0].box);
     }
-    return MSM_OK;
+    return forces_impl(h, n_sys, sys.data(), pos, q, nullptr, energies, forces, potentials, nullptr,
+                       (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------------------- dynamics
 
-struct SysDev {
-    int64_t n, n_mol;
+// A batch of MD systems in concatenated device arrays.
+struct RunSys {
+    int B;
+    const SysIn *sys;
     double *x, *v;
     const double *q, *m;
     const uint8_t *lj;
-    double box[6];
-    double *f = nullptr;     // device forces carried in/out (nullable)
-    int f_valid = 0;
-    double energy = 0;
+    double *f = nullptr;      // device forces carried in/out (nullable)
+    bool f_valid = false;     // f and e0 hold F, U of the start positions
+    const double *e0 = nullptr;   // host, B energies when f_valid
 };
 
 // ------------------------------------------------------------ Verlet lists
@@ -697,39 +938,39 @@ static int list_alloc(msm_handle *h, int64_t n, size_t vsz)
     return MSM_OK;
 }
 
-// Size the lists for the system and invalidate them when the system changed or
-// the call does not continue a trajectory (fresh): md_run's results then depend
-// only on its inputs, never on what the handle ran before.
+// Size the lists for a single system and invalidate them when the system
+// changed or the call does not continue a trajectory (fresh): md_run's results
+// then depend only on its inputs, never on what the handle ran before.
 template <typename T>
-static int list_setup(msm_handle *h, const SysDev &s, bool fresh, cudaStream_t st)
+static int list_setup(msm_handle *h, const RunSys &s, bool fresh, cudaStream_t st)
 {
-    TRY(set_geometry(h, s.box, st));
-    choose_bricks(h, s.n);
+    TRY(set_batch(h, 1, s.sys, st));
+    const SysIn &S = s.sys[0];
     const double rl = h->p.a + h->p.list_skin, hh = h->p.h;
     const int R = (int)ceil((rl + 1e-3 * hh) / hh) + 1;
     const int rows = (2 * h->bd[1] + 2 * R + 1) * (2 * h->bd[2] + 2 * R + 1);
     const int ngroups = h->nb[0] * ((h->nb[1] + 1) / 2) * ((h->nb[2] + 1) / 2);
-    const bool changed = s.n != h->vl_key_n || s.n_mol != h->vl_key_nmol || s.lj != h->vl_key_lj ||
-                         memcmp(s.box, h->vl_key_box, sizeof h->vl_key_box) != 0 || rows > h->vl_rows ||
+    const bool changed = S.n != h->vl_key_n || S.n_mol != h->vl_key_nmol || s.lj != h->vl_key_lj ||
+                         memcmp(S.box, h->vl_key_box, sizeof h->vl_key_box) != 0 || rows > h->vl_rows ||
                          ngroups != h->vl_ngroups;
     if (!changed && !fresh && h->vl_ctl.p) return MSM_OK;
     if (h->vl_cap == 0) {
         // entries per atom: pairs within a + skin at 1.8x the box's mean density, at least 256
-        double vol = s.box[3] * s.box[4] * s.box[5];
-        const double dens = (double)s.n / vol;
+        const double vol = S.box[3] * S.box[4] * S.box[5];
+        const double dens = (double)S.n / vol;
         const double want = 1.8 * dens * 4.18879020478639 * rl * rl * rl + 32.0;
         h->vl_cap = ((std::max(256, (int)want) + 7) / 8) * 8;
-        h->vl_jcap = sizeof(T) == 4 ? 4608 : 4608;
+        h->vl_jcap = 4608;
     }
     h->vl_rows = std::max(h->vl_rows, rows);
     h->vl_ngroups = ngroups;
-    TRY(list_alloc(h, s.n, sizeof(vec4<T>)));
+    TRY(list_alloc(h, S.n, sizeof(vec4<T>)));
     CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
     const int invalid = 1;
     CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));                    // 'invalid' lives on the host stack
-    h->vl_key_n = s.n; h->vl_key_nmol = s.n_mol; h->vl_key_lj = s.lj;
-    memcpy(h->vl_key_box, s.box, sizeof h->vl_key_box);
+    h->vl_key_n = S.n; h->vl_key_nmol = S.n_mol; h->vl_key_lj = s.lj;
+    memcpy(h->vl_key_box, S.box, sizeof h->vl_key_box);
     return MSM_OK;
 }
 
@@ -754,80 +995,157 @@ static int list_grow(msm_handle *h, cudaStream_t st)
 template <typename T> static double shake_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-12; }
 template <typename T> static double rattle_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-14; }
 
-// n_steps of velocity Verlet on device arrays; uk (device, nullable) gets
-// (U, K) before the first and after every step.  No host synchronisation.
-template <typename T>
-static int run_md_t(msm_handle *h, const SysDev &s, double dt, int n_steps, double *uk, cudaStream_t st)
+// (U, K) of every system into uk at the device step counter, then advance it.
+static int record_uk(msm_handle *h, const RunSys &s, double *uk, int64_t uk_stride, cudaStream_t st)
 {
-    const size_t nn = (size_t)(s.n > 0 ? s.n : 1);
-    TRY(ensure(h->md_f, sizeof(double) * 3 * nn));
-    TRY(ensure(h->md_xo, sizeof(double) * 3 * nn));
-    EvalIO io;
-    io.n = s.n; io.n_mol = s.n_mol; io.pos = s.x; io.q = s.q; io.lj = s.lj;
-    io.forces = s.f ? s.f : h->md_f.as<double>();
-    io.pot = nullptr;
-    VVArgs va;
-    va.n = (int)s.n; va.n_mol = (int)s.n_mol; va.x = s.x; va.v = s.v; va.xo = h->md_xo.as<double>();
-    TRY(ensure(h->md_im, sizeof(double) * nn));
-    TRY(launch_inverse(int(s.n), s.m, h->md_im.as<double>(), st));
-    va.f = io.forces; va.m = s.m; va.im = h->md_im.as<double>(); va.dt = dt;
-    va.d_oh2 = h->p.d_oh * h->p.d_oh; va.d_hh2 = h->p.d_hh * h->p.d_hh;
-    va.tol = shake_tol<T>(); va.tol_v = rattle_tol<T>(); va.max_iter = sizeof(T) == 4 ? 200 : 1000;
-    h->list_on = false;
-    if (h->p.list_skin > 0 && s.n > 0) TRY(list_setup<T>(h, s, !(s.f && s.f_valid), st));
-    if (s.f && s.f_valid) {
-        // forces and energy of the start positions come with the system
-        TRY(set_geometry(h, s.box, st));
-        TRY(ensure_atoms(h, s.n));
-        choose_bricks(h, s.n);
-        h->last_n = s.n;
-        CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int) * 4, st));
-        h->h_scal[4] = s.energy;
-        CUDA_TRY(cudaMemcpyAsync(h->sums.p, &h->h_scal[4], sizeof(double), cudaMemcpyHostToDevice, st));
-    } else {
-        TRY(evaluate(h, io, s.box, st));
-    }
-    va.status = h->status.as<int>();
-    if (uk) {
-        CUDA_TRY(cudaMemcpyAsync(uk, h->sums.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        TRY(launch_kinetic(va, h->kin.as<double>(), st));
-        const double *cols[1] = {h->kin.as<double>()};
-        TRY(launch_sum((int)s.n, 1, cols, h->partials.as<double>(), uk + 1, va.status, st));
-    }
-    h->list_on = h->vl_ctl.p != nullptr && h->p.list_skin > 0 && s.n > 0;
-    for (int step = 0; step < n_steps; step++) {
-        { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
-        int rc = evaluate_t<T>(h, io, st);
-        if (rc) { h->list_on = false; return rc; }
-        { PROF(ST_VV2); TRY(launch_vv_second<T>(va, uk ? h->kin.as<double>() : nullptr, st)); }
-        if (uk) {
-            CUDA_TRY(cudaMemcpyAsync(uk + 2 * (step + 1), h->sums.p, sizeof(double), cudaMemcpyDeviceToDevice, st));
-            const double *cols[1] = {h->kin.as<double>()};
-            TRY(launch_sum((int)s.n, 1, cols, h->partials.as<double>(), uk + 2 * (step + 1) + 1, va.status, st));
-        }
-    }
-    h->list_on = false;
+    TRY(launch_kinetic(h->N, s.v, s.m, h->kin.as<double>(), st));
+    const double *cols[1] = {h->kin.as<double>()};
+    TRY(launch_sum(batch_of(h), h->max_n, h->PB, 1, cols, h->partials.as<double>(), h->kin_s.as<double>(), 1,
+                   h->status.as<int>(), st));
+    return launch_record_uk(h->B, h->sums.as<double>(), 4, h->kin_s.as<double>(), uk, (int)uk_stride,
+                            h->ctr.as<int>(), st);
+}
+
+// One velocity Verlet step of the batch: half kick + drift + SHAKE, forces,
+// half kick + RATTLE (+ the energies when recorded).
+template <typename T>
+static int md_step(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArgs &va, double *uk,
+                   int64_t uk_stride, cudaStream_t st)
+{
+    { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
+    TRY(evaluate_t<T>(h, io, st));
+    { PROF(ST_VV2); TRY(launch_vv_second<T>(va, nullptr, st)); }
+    if (uk) TRY(record_uk(h, s, uk, uk_stride, st));
     return MSM_OK;
 }
 
-static int run_md(msm_handle *h, const SysDev &s, double dt, int n_steps, double *uk, cudaStream_t st)
+// Capture one md step into a CUDA graph on the handle's own stream (capture
+// records the launches; nothing runs), or reuse the graph captured for the
+// same arrays, geometry and buffers.
+template <typename T>
+static int md_graph(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArgs &va, double dt, double *uk,
+                    int64_t uk_stride)
+{
+    GraphKey k;
+    memset(&k, 0, sizeof k);
+    k.x = s.x; k.v = s.v; k.f = io.forces; k.q = s.q; k.m = s.m; k.lj = s.lj; k.uk = uk;
+    k.uk_stride = uk_stride; k.geom_gen = h->geom_gen; k.alloc_gen = g_alloc_gen.load(); k.dt = dt;
+    k.B = s.B; k.list_on = h->list_on ? 1 : 0;
+    if (h->gexec && memcmp(&k, &h->gkey, sizeof k) == 0) return MSM_OK;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (!h->cap_st) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    const long long l0 = g_launches.load();
+    CUDA_TRY(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed));
+    const int rc = md_step<T>(h, s, io, va, uk, uk_stride, h->cap_st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+    h->g_kernels = g_launches.load() - l0;
+    g_launches.fetch_sub(h->g_kernels);                    // counted when replayed
+    if (rc != MSM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    const cudaError_t e2 = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) { h->gexec = nullptr; return fail_cuda(e2, "cudaGraphInstantiate", __FILE__, __LINE__); }
+    h->gkey = k;
+    return MSM_OK;
+}
+
+// n_steps of velocity Verlet on a batch in device arrays; uk (device,
+// nullable) gets (U, K) of system b before the first and after every step at
+// uk[b * uk_stride + 2 * step].  The first step runs launch by launch; with
+// graphs on (and the profiler off) the others replay one captured graph.
+// No host synchronisation.
+template <typename T>
+static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, double *uk, int64_t uk_stride,
+                    cudaStream_t st)
+{
+    int64_t n = 0;
+    for (int b = 0; b < s.B; b++) n += s.sys[b].n;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    TRY(ensure(h->md_xo, sizeof(double) * 3 * nn));
+    TRY(ensure(h->md_im, sizeof(double) * nn));
+    if (!s.f) TRY(ensure(h->md_f, sizeof(double) * 3 * nn));
+    h->list_on = false;
+    if (h->p.list_skin > 0 && s.B == 1 && n > 0) TRY(list_setup<T>(h, s, !(s.f && s.f_valid), st));
+    TRY(set_batch(h, s.B, s.sys, st));
+    EvalIO io;
+    io.pos = s.x; io.q = s.q; io.lj = s.lj;
+    io.forces = s.f ? s.f : h->md_f.as<double>();
+    io.pot = nullptr;
+    TRY(launch_inverse((int)n, s.m, h->md_im.as<double>(), st));
+    VVArgs va;
+    va.bt = batch_of(h); va.max_units = h->max_units;
+    va.x = s.x; va.v = s.v; va.xo = h->md_xo.as<double>();
+    va.f = io.forces; va.m = s.m; va.im = h->md_im.as<double>(); va.dt = dt;
+    va.d_oh2 = h->p.d_oh * h->p.d_oh; va.d_hh2 = h->p.d_hh * h->p.d_hh;
+    va.tol = shake_tol<T>(); va.tol_v = rattle_tol<T>(); va.max_iter = sizeof(T) == 4 ? 200 : 1000;
+    va.status = h->status.as<int>();
+    if (s.f && s.f_valid) {
+        // forces and energies of the start positions come with the systems
+        CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int) * 4, st));
+        for (int b = 0; b < s.B; b++) h->h_e[b] = s.e0[b];
+        CUDA_TRY(cudaMemcpy2DAsync(h->sums.p, 4 * sizeof(double), h->h_e, sizeof(double), sizeof(double),
+                                   (size_t)s.B, cudaMemcpyHostToDevice, st));
+    } else {
+        TRY(evaluate(h, io, s.B, s.sys, st));
+    }
+    if (uk) {
+        CUDA_TRY(cudaMemsetAsync(h->ctr.p, 0, sizeof(int), st));
+        TRY(record_uk(h, s, uk, uk_stride, st));
+    }
+    h->list_on = h->vl_ctl.p != nullptr && h->p.list_skin > 0 && s.B == 1 && n > 0;
+    const bool graphs = (h->p.flags & MSM_FLAG_GRAPHS) && !h->prof.on;
+    bool captured = false;
+    int rc = MSM_OK;
+    for (int step = 0; step < n_steps && rc == MSM_OK; step++) {
+        if (!graphs || step == 0 || h->tune_pending) {
+            rc = md_step<T>(h, s, io, va, uk, uk_stride, st);
+            continue;
+        }
+        if (!captured) {
+            rc = md_graph<T>(h, s, io, va, dt, uk, uk_stride);
+            captured = true;
+        }
+        if (rc == MSM_OK) {
+            const cudaError_t e = cudaGraphLaunch(h->gexec, st);
+            if (e != cudaSuccess) rc = fail_cuda(e, "cudaGraphLaunch", __FILE__, __LINE__);
+            else count_launch((int)h->g_kernels);
+        }
+    }
+    h->list_on = false;
+    return rc;
+}
+
+static int run_md(msm_handle *h, const RunSys &s, double dt, int n_steps, double *uk, int64_t uk_stride,
+                  cudaStream_t st)
 {
     if (!(dt > 0) || n_steps < 0) return fail_msg(MSM_EINVAL, "dt must be > 0 and n_steps >= 0");
-    if (s.n_mol > 0 && h->p.model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "rigid molecules need the water model");
-    if (h->precision == MSM_FP32) return run_md_t<float>(h, s, dt, n_steps, uk, st);
-    return run_md_t<double>(h, s, dt, n_steps, uk, st);
+    for (int b = 0; b < s.B; b++)
+        if (s.sys[b].n_mol > 0 && h->p.model != MSM_MODEL_WATER)
+            return fail_msg(MSM_EINVAL, "rigid molecules need the water model");
+    if (h->precision == MSM_FP32) return run_md_t<float>(h, s, dt, n_steps, uk, uk_stride, st);
+    return run_md_t<double>(h, s, dt, n_steps, uk, uk_stride, st);
+}
+
+static int check_system(const msm_system *sys)
+{
+    if (!sys) return fail_msg(MSM_EINVAL, "system is NULL");
+    if (sys->n < 0 || sys->n_mol < 0 || 3 * sys->n_mol > sys->n) return fail_msg(MSM_EINVAL, "bad atom counts");
+    if (sys->n > 0 && (!sys->x || !sys->v || !sys->q || !sys->m)) return fail_msg(MSM_EINVAL, "x, v, q, m are required");
+    return MSM_OK;
 }
 
 extern "C" int md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps, double *uk, void *stream)
 {
-    if (!h || !sys) return fail_msg(MSM_EINVAL, "handle or system is NULL");
-    if (sys->n < 0 || sys->n_mol < 0 || 3 * sys->n_mol > sys->n) return fail_msg(MSM_EINVAL, "bad atom counts");
-    if (sys->n > 0 && (!sys->x || !sys->v || !sys->q || !sys->m)) return fail_msg(MSM_EINVAL, "x, v, q, m are required");
+    if (!h) return fail_msg(MSM_EINVAL, "handle is NULL");
+    TRY(check_system(sys));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nn = (size_t)sys->n;
-    SysDev s;
-    s.n = sys->n; s.n_mol = sys->n_mol;
-    memcpy(s.box, sys->box, sizeof s.box);
+    SysIn si;
+    si.n = sys->n; si.n_mol = sys->n_mol;
+    memcpy(si.box, sys->box, sizeof si.box);
+    RunSys s;
+    s.B = 1; s.sys = &si;
     const bool x_host = sys->x && !on_device(sys->x), v_host = sys->v && !on_device(sys->v);
     if (x_host) {
         TRY(ensure(h->md_x, sizeof(double) * 3 * nn));
@@ -849,6 +1167,7 @@ extern "C" int md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps
     if (uk_host) TRY(ensure(h->md_uk, sizeof(double) * ukn));
     double *ukd = uk_host ? h->md_uk.as<double>() : uk;
     const bool f_host = sys->f && !on_device(sys->f);
+    double e0 = sys->energy;
     if (sys->f) {
         if (f_host) {
             TRY(ensure(h->out_f, sizeof(double) * 3 * nn));
@@ -856,10 +1175,10 @@ extern "C" int md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps
                 CUDA_TRY(cudaMemcpyAsync(h->out_f.p, sys->f, sizeof(double) * 3 * nn, cudaMemcpyHostToDevice, st));
             s.f = h->out_f.as<double>();
         } else s.f = sys->f;
-        s.f_valid = sys->f_valid;
-        s.energy = sys->energy;
+        s.f_valid = sys->f_valid != 0;
+        s.e0 = &e0;
     }
-    TRY(run_md(h, s, dt, n_steps, ukd, st));
+    TRY(run_md(h, s, dt, n_steps, ukd, (int64_t)ukn, st));
     if (x_host) CUDA_TRY(cudaMemcpyAsync(sys->x, s.x, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost, st));
     if (v_host) CUDA_TRY(cudaMemcpyAsync(sys->v, s.v, sizeof(double) * 3 * nn, cudaMemcpyDeviceToHost, st));
     if (uk_host) CUDA_TRY(cudaMemcpyAsync(uk, ukd, sizeof(double) * ukn, cudaMemcpyDeviceToHost, st));
@@ -867,6 +1186,120 @@ extern "C" int md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps
     if (sys->f) CUDA_TRY(cudaMemcpyAsync(&h->h_scal[5], h->sums.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY(finish(h, st));
     if (sys->f) { sys->f_valid = 1; sys->energy = h->h_scal[5]; }
+    return MSM_OK;
+}
+
+// Gather a batch of caller systems into the handle's concatenated buffers.
+static int gather_systems(msm_handle *h, int B, const msm_system *systems, std::vector<SysIn> &sys,
+                          std::vector<int64_t> &off, bool need_v, cudaStream_t st)
+{
+    sys.resize((size_t)B);
+    off.assign((size_t)B + 1, 0);
+    for (int b = 0; b < B; b++) {
+        const msm_system &S = systems[b];
+        if (S.n < 0 || S.n_mol < 0 || 3 * S.n_mol > S.n) return fail_msg(MSM_EINVAL, "bad atom counts (system %d)", b);
+        if (S.n > 0 && (!S.x || !S.q || (need_v && (!S.v || !S.m))))
+            return fail_msg(MSM_EINVAL, "system %d lacks x, v, q or m", b);
+        sys[(size_t)b].n = S.n; sys[(size_t)b].n_mol = S.n_mol;
+        memcpy(sys[(size_t)b].box, S.box, sizeof S.box);
+        off[(size_t)b + 1] = off[(size_t)b] + S.n;
+    }
+    const size_t n = (size_t)off[(size_t)B], nn = n > 0 ? n : 1;
+    TRY(ensure(h->md_x, sizeof(double) * 3 * nn));
+    TRY(ensure(h->md_q, sizeof(double) * nn));
+    TRY(ensure(h->md_lj, nn));
+    if (need_v) {
+        TRY(ensure(h->md_v, sizeof(double) * 3 * nn));
+        TRY(ensure(h->md_m, sizeof(double) * nn));
+    }
+    for (int b = 0; b < B; b++) {
+        const msm_system &S = systems[b];
+        const size_t o = (size_t)off[(size_t)b], m = (size_t)S.n;
+        if (!m) continue;
+        CUDA_TRY(cudaMemcpyAsync(h->md_x.as<double>() + 3 * o, S.x, sizeof(double) * 3 * m, cudaMemcpyDefault, st));
+        CUDA_TRY(cudaMemcpyAsync(h->md_q.as<double>() + o, S.q, sizeof(double) * m, cudaMemcpyDefault, st));
+        if (S.lj) CUDA_TRY(cudaMemcpyAsync(h->md_lj.as<uint8_t>() + o, S.lj, m, cudaMemcpyDefault, st));
+        else CUDA_TRY(cudaMemsetAsync(h->md_lj.as<uint8_t>() + o, 0, m, st));
+        if (need_v) {
+            CUDA_TRY(cudaMemcpyAsync(h->md_v.as<double>() + 3 * o, S.v, sizeof(double) * 3 * m, cudaMemcpyDefault, st));
+            CUDA_TRY(cudaMemcpyAsync(h->md_m.as<double>() + o, S.m, sizeof(double) * m, cudaMemcpyDefault, st));
+        }
+    }
+    return MSM_OK;
+}
+
+extern "C" int msm_system_forces_batched(msm_handle *h, int32_t n_sys, msm_system *systems, double *energies,
+                                         void *stream)
+{
+    if (!h || n_sys < 1 || !systems) return fail_msg(MSM_EINVAL, "bad batched arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<SysIn> sys;
+    std::vector<int64_t> off;
+    TRY(gather_systems(h, n_sys, systems, sys, off, false, st));
+    const size_t n = (size_t)off[(size_t)n_sys];
+    TRY(ensure(h->md_f, sizeof(double) * 3 * (n > 0 ? n : 1)));
+    EvalIO io;
+    io.pos = h->md_x.as<double>(); io.q = h->md_q.as<double>(); io.lj = h->md_lj.as<uint8_t>();
+    io.forces = h->md_f.as<double>(); io.pot = nullptr;
+    TRY(evaluate(h, io, n_sys, sys.data(), st));
+    for (int b = 0; b < n_sys; b++)
+        if (systems[b].f && systems[b].n > 0)
+            CUDA_TRY(cudaMemcpyAsync(systems[b].f, h->md_f.as<double>() + 3 * off[(size_t)b],
+                                     sizeof(double) * 3 * (size_t)systems[b].n, cudaMemcpyDefault, st));
+    TRY(copy_sums(h->h_e, h, 0, st));
+    TRY(finish(h, st));
+    for (int b = 0; b < n_sys; b++) {
+        if (energies) energies[b] = h->h_e[b];
+        if (systems[b].f) { systems[b].f_valid = 1; systems[b].energy = h->h_e[b]; }
+    }
+    return MSM_OK;
+}
+
+extern "C" int md_run_batched(msm_handle *h, int32_t n_sys, msm_system *systems, double dt, int32_t n_steps,
+                              double *uk, void *stream)
+{
+    if (!h || n_sys < 1 || !systems) return fail_msg(MSM_EINVAL, "bad batched arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<SysIn> sys;
+    std::vector<int64_t> off;
+    TRY(gather_systems(h, n_sys, systems, sys, off, true, st));
+    const size_t n = (size_t)off[(size_t)n_sys];
+    // forces carried in only when every system brings valid ones
+    bool carry = true;
+    for (int b = 0; b < n_sys; b++) carry = carry && systems[b].f && systems[b].f_valid;
+    bool want_f = false;
+    for (int b = 0; b < n_sys; b++) want_f = want_f || systems[b].f;
+    TRY(ensure(h->out_f, sizeof(double) * 3 * (n > 0 ? n : 1)));
+    std::vector<double> e0((size_t)n_sys, 0.0);
+    if (carry)
+        for (int b = 0; b < n_sys; b++) {
+            e0[(size_t)b] = systems[b].energy;
+            if (systems[b].n > 0)
+                CUDA_TRY(cudaMemcpyAsync(h->out_f.as<double>() + 3 * off[(size_t)b], systems[b].f,
+                                         sizeof(double) * 3 * (size_t)systems[b].n, cudaMemcpyDefault, st));
+        }
+    RunSys s;
+    s.B = n_sys; s.sys = sys.data();
+    s.x = h->md_x.as<double>(); s.v = h->md_v.as<double>(); s.q = h->md_q.as<double>(); s.m = h->md_m.as<double>();
+    s.lj = h->md_lj.as<uint8_t>();
+    s.f = h->out_f.as<double>(); s.f_valid = carry; s.e0 = e0.data();
+    const int64_t ukn = 2 * (int64_t)(n_steps + 1);
+    const bool uk_host = uk && !on_device(uk);
+    if (uk_host) TRY(ensure(h->md_uk, sizeof(double) * (size_t)(ukn * n_sys)));
+    double *ukd = uk_host ? h->md_uk.as<double>() : uk;
+    TRY(run_md(h, s, dt, n_steps, ukd, ukn, st));
+    for (int b = 0; b < n_sys; b++) {
+        const size_t o = (size_t)off[(size_t)b], m = (size_t)systems[b].n;
+        if (!m) continue;
+        CUDA_TRY(cudaMemcpyAsync(systems[b].x, s.x + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDefault, st));
+        CUDA_TRY(cudaMemcpyAsync(systems[b].v, s.v + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDefault, st));
+        if (systems[b].f) CUDA_TRY(cudaMemcpyAsync(systems[b].f, s.f + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDefault, st));
+    }
+    if (uk_host) CUDA_TRY(cudaMemcpyAsync(uk, ukd, sizeof(double) * (size_t)(ukn * n_sys), cudaMemcpyDeviceToHost, st));
+    if (want_f) TRY(copy_sums(h->h_e, h, 0, st));
+    TRY(finish(h, st));
+    for (int b = 0; b < n_sys; b++)
+        if (systems[b].f) { systems[b].f_valid = 1; systems[b].energy = h->h_e[b]; }
     return MSM_OK;
 }
 
@@ -902,22 +1335,19 @@ template <typename T>
 static int count_pairs_t(msm_handle *h, int64_t *out)
 {
     cudaStream_t st = 0;
-    ShortArgs<T> s;
-    s.g = h->cg;
-    for (int d = 0; d < 3; d++) { s.bd[d] = h->bd[d]; s.nb[d] = h->nb[d]; }
-    s.nbricks = h->nbricks;
-    s.start = h->start.as<int>(); s.apos = h->apos.as<vec4<T>>(); s.aflag = h->aflag.as<int>();
-    const double a = h->p.a;
-    s.a = (T)a; s.a2 = (T)(a * a); s.a_sel = (T)(a + 1e-3 * h->p.h);
-    s.perm = h->perm.as<int>(); s.vl_ctl = nullptr;
-    s.sr = nullptr; s.lj = nullptr; s.cnt = h->eatom.as<double>(); s.status = h->status.as<int>();
-    CUDA_TRY(cudaMemsetAsync(h->eatom.p, 0, sizeof(double) * (size_t)(h->last_n > 0 ? h->last_n : 1), st));
+    ShortArgs<T> s = short_args<T>(h);
+    s.sr = nullptr; s.lj = nullptr; s.cnt = h->eatom.as<double>();
+    CUDA_TRY(cudaMemsetAsync(h->eatom.p, 0, sizeof(double) * (size_t)(h->N > 0 ? h->N : 1), st));
     TRY(launch_count_pairs<T>(s, st));
     const double *cols[1] = {h->eatom.as<double>()};
-    TRY(launch_sum((int)h->last_n, 1, cols, h->partials.as<double>(), h->sums.as<double>() + 2, h->status.as<int>(), st));
-    CUDA_TRY(cudaMemcpyAsync(&h->h_scal[3], h->sums.as<double>() + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(launch_sum(batch_of(h), h->max_n, h->PB, 1, cols, h->partials.as<double>(), h->kin_s.as<double>(), 1,
+                   h->status.as<int>(), st));
+    TRY(ensure_host_e(h, h->B));
+    CUDA_TRY(cudaMemcpyAsync(h->h_e, h->kin_s.p, sizeof(double) * (size_t)h->B, cudaMemcpyDeviceToHost, st));
     TRY(finish(h, st));
-    *out = (int64_t)h->h_scal[3];
+    double t = 0;
+    for (int b = 0; b < h->B; b++) t += h->h_e[b];
+    *out = (int64_t)t;
     return MSM_OK;
 }
 
@@ -931,6 +1361,12 @@ extern "C" int msm_count_pairs(msm_handle *h, int64_t *ordered_pairs)
 
 // ----------------------------------------------------------------- parareal
 
+// F of every slice that is not yet exact runs as one batch (all slices in the
+// same launches); G runs slice by slice, as the correction sweep requires.
+// For slices n < k after k iterations the correction is exactly zero (the
+// bracket G(lambda^{k+1}_n) - G(lambda^k_n) vanishes bitwise because both
+// states are equal and G is deterministic), so those slices are copied
+// instead of recomputed: the result is bitwise what recomputing gives.
 extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F, double dtF,
                             int32_t stepsF, const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
                             double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx, void *stream)
@@ -966,33 +1402,38 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         TRY(ensure(f_v, sizeof(double) * n3 * ns));
         TRY(ensure(tmp_x, sizeof(double) * n3));
         TRY(ensure(tmp_v, sizeof(double) * n3));
-        TRY(ensure(q, sizeof(double) * nn));
-        TRY(ensure(m, sizeof(double) * nn));
-        TRY(ensure(lj, nn));
+        TRY(ensure(q, sizeof(double) * nn * ns));          // per-slice copies for the batched F
+        TRY(ensure(m, sizeof(double) * nn * ns));
+        TRY(ensure(lj, nn * ns));
         const size_t nblk = (n3 + 255) / 256;
         TRY(ensure(part, sizeof(double) * nblk * ns));
         TRY(ensure(dx, sizeof(double)));
         CUDA_TRY(cudaMemcpyAsync(lam_x.p, s0.x, sizeof(double) * n3, cudaMemcpyDefault, st));
         CUDA_TRY(cudaMemcpyAsync(lam_v.p, s0.v, sizeof(double) * n3, cudaMemcpyDefault, st));
-        CUDA_TRY(cudaMemcpyAsync(q.p, s0.q, sizeof(double) * nn, cudaMemcpyDefault, st));
-        CUDA_TRY(cudaMemcpyAsync(m.p, s0.m, sizeof(double) * nn, cudaMemcpyDefault, st));
-        if (s0.lj) CUDA_TRY(cudaMemcpyAsync(lj.p, s0.lj, nn, cudaMemcpyDefault, st));
-        else CUDA_TRY(cudaMemsetAsync(lj.p, 0, nn, st));
+        for (size_t k = 0; k < ns; k++) {
+            CUDA_TRY(cudaMemcpyAsync(q.as<double>() + k * nn, s0.q, sizeof(double) * nn, cudaMemcpyDefault, st));
+            CUDA_TRY(cudaMemcpyAsync(m.as<double>() + k * nn, s0.m, sizeof(double) * nn, cudaMemcpyDefault, st));
+            if (s0.lj) CUDA_TRY(cudaMemcpyAsync(lj.as<uint8_t>() + k * nn, s0.lj, nn, cudaMemcpyDefault, st));
+            else CUDA_TRY(cudaMemsetAsync(lj.as<uint8_t>() + k * nn, 0, nn, st));
+        }
         auto X = [&](DevBuf &b, size_t k) { return b.as<double>() + k * n3; };
-        SysDev sd;
-        sd.n = s0.n; sd.n_mol = s0.n_mol; sd.q = q.as<double>(); sd.m = m.as<double>(); sd.lj = lj.as<uint8_t>();
-        memcpy(sd.box, s0.box, sizeof sd.box);
-        auto run = [&](msm_handle *hh, double *x, double *v, double dt, int steps) -> int {
-            SysDev t = sd;
-            t.x = x; t.v = v;
-            TRY(run_md(hh, t, dt, steps, nullptr, st));
-            return finish(hh, st);
+        SysIn si;
+        si.n = s0.n; si.n_mol = s0.n_mol;
+        memcpy(si.box, s0.box, sizeof si.box);
+        std::vector<SysIn> sis(ns, si);
+        // one system, G, on tmp
+        auto runG = [&]() -> int {
+            RunSys t;
+            t.B = 1; t.sys = &si; t.x = tmp_x.as<double>(); t.v = tmp_v.as<double>();
+            t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
+            TRY(run_md(hG, t, dtG, stepsG, nullptr, 0, st));
+            return finish(hG, st);
         };
         // init row: lambda^0_{n+1} = G(lambda^0_n)
         for (size_t k = 0; k < ns; k++) {
             CUDA_TRY(cudaMemcpyAsync(tmp_x.p, X(lam_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(tmp_v.p, X(lam_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            TRY(run(hG, tmp_x.as<double>(), tmp_v.as<double>(), dtG, stepsG));
+            TRY(runG());
             CUDA_TRY(cudaMemcpyAsync(X(gold_x, k), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(X(gold_v, k), tmp_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(X(lam_x, k + 1), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
@@ -1001,19 +1442,25 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         int done = 0;
         double dxh = INFINITY;
         for (int it = 0; it < max_iter; it++) {
-            // f_n = F(lambda^k_n) for every slice (independent)
-            for (size_t k = 0; k < ns; k++) {
-                CUDA_TRY(cudaMemcpyAsync(X(f_x, k), X(lam_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                CUDA_TRY(cudaMemcpyAsync(X(f_v, k), X(lam_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                TRY(run(hF, X(f_x, k), X(f_v, k), dtF, stepsF));
+            const size_t k0 = (size_t)std::min(it, n_slices);    // slices k < it are exact
+            // f_n = F(lambda^k_n) for every slice n >= it: one batch
+            if (k0 < ns) {
+                CUDA_TRY(cudaMemcpyAsync(X(f_x, k0), X(lam_x, k0), sizeof(double) * n3 * (ns - k0), cudaMemcpyDeviceToDevice, st));
+                CUDA_TRY(cudaMemcpyAsync(X(f_v, k0), X(lam_v, k0), sizeof(double) * n3 * (ns - k0), cudaMemcpyDeviceToDevice, st));
+                RunSys t;
+                t.B = (int)(ns - k0); t.sys = sis.data(); t.x = X(f_x, k0); t.v = X(f_v, k0);
+                t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
+                TRY(run_md(hF, t, dtF, stepsF, nullptr, 0, st));
+                TRY(finish(hF, st));
             }
-            // sequential correction sweep
-            CUDA_TRY(cudaMemcpyAsync(new_x.p, lam_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(new_v.p, lam_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            for (size_t k = 0; k < ns; k++) {
+            // sequential correction sweep over the slices that are not exact yet
+            CUDA_TRY(cudaMemcpyAsync(new_x.p, lam_x.p, sizeof(double) * n3 * (k0 + 1), cudaMemcpyDeviceToDevice, st));
+            CUDA_TRY(cudaMemcpyAsync(new_v.p, lam_v.p, sizeof(double) * n3 * (k0 + 1), cudaMemcpyDeviceToDevice, st));
+            CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * nblk * ns, st));
+            for (size_t k = k0; k < ns; k++) {
                 CUDA_TRY(cudaMemcpyAsync(tmp_x.p, X(new_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
                 CUDA_TRY(cudaMemcpyAsync(tmp_v.p, X(new_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                TRY(run(hG, tmp_x.as<double>(), tmp_v.as<double>(), dtG, stepsG));
+                TRY(runG());
                 TRY(launch_parareal_update((int)n3, X(f_x, k), tmp_x.as<double>(), X(gold_x, k), X(new_x, k + 1),
                                            X(lam_x, k + 1), part.as<double>() + k * nblk, st));
                 TRY(launch_parareal_update((int)n3, X(f_v, k), tmp_v.as<double>(), X(gold_v, k), X(new_v, k + 1),
