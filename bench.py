@@ -15,7 +15,10 @@ starts; the working set (~0.3 GB) is larger than L2, so no flush is needed.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica
-of the workload (the path does not shard; "replicas only").
+of the workload (the path does not shard; "replicas only").  Besides the timed
+1M-atom run the line carries the FP64 GPU path, the force error against the
+oracle, an end-to-end run through host buffers, the uneven 7-box batch and the
+10,000-atom parareal run.
 """
 from __future__ import annotations
 
@@ -54,6 +57,9 @@ def args_parse():
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-oracle", action="store_true", help="skip the oracle force error and CPU baseline")
+    p.add_argument("--profile-steps", type=int, default=30, help="eager profiled steps after the timed region")
+    p.add_argument("--batch-steps", type=int, default=100, help="steps of the uneven 7-box batch (0: skip)")
+    p.add_argument("--parareal", type=int, default=1, help="run the 10,000-atom parareal leg (0: skip)")
     return p.parse_args()
 
 
@@ -193,8 +199,6 @@ def run_ours(a):
         bus = None
     clocks = ClockSampler(bus) if rank == 0 else None
     time.sleep(0.5 if clocks else 0)
-    m32.profile(True)
-    m32.profile_read(reset=True)
     l0 = api.kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -210,8 +214,15 @@ def run_ours(a):
         clocks.mark_end()
     launches = api.kernel_launches() - l0
     t_ms = ev0.elapsed_time(ev1)
+    # per-stage CUDA-event times: the same trajectory continued for a few eager
+    # (profiled, graph-free) steps right after the timed region
+    m32.profile(True)
+    m32.profile_read(reset=True)
+    m32.md_run(d, DT, a.profile_steps, record=True)
+    torch.cuda.synchronize()
     m32.profile(False)
     prof = m32.profile_read(reset=True)
+    t_prof = sum(v[0] for v in prof.values())
     if world > 1:
         tt = torch.tensor([t_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -220,7 +231,6 @@ def run_ours(a):
     uk = uk.cpu().numpy()
     etot = uk.sum(1)
     pairs = m32.count_pairs()
-    lstats = m32.list_stats()
 
     value = n * a.steps * world / (t_ms / 1e3)
 
@@ -278,6 +288,9 @@ def run_ours(a):
            "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes + hf.nbytes + hq.nbytes + hm.nbytes + hl.nbytes),
            "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes + hf.nbytes + 2 * 2 * 8)}
 
+    batched = run_batch_leg(a, torch, api, inputs, dev) if a.batch_steps > 0 else None
+    parareal = run_parareal_leg(a, torch, api, inputs, dev) if a.parareal else None
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -293,7 +306,7 @@ def run_ours(a):
     achieved = pairs * FLOPS_PER_PAIR / sr_avg_s / 1e12
     traffic = short_range_traffic(n)
     stage_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]}
-    step_share = {k: round(v[0] / t_ms, 4) for k, v in prof.items() if v[1]}
+    step_share = {k: round(v[0] / t_prof, 4) for k, v in prof.items() if v[1]}
     drift = float(etot[-1] - etot[0])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -304,7 +317,9 @@ def run_ours(a):
                      "kernel": "k_short (short-range g* sum)",
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                                     "(max SM clock from MEASURED_PEAKS.json)",
-                     "work": f"{pairs} ordered pairs within a per launch x {FLOPS_PER_PAIR} flops"},
+                     "work": f"{pairs} ordered pairs within a per launch x {FLOPS_PER_PAIR} flops",
+                     "duration": f"{sr_avg_s * 1e3:.4f} ms average of {sr_n} launches (CUDA events on the "
+                                 f"launching stream, {a.profile_steps} eager steps continuing the timed run)"},
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -314,13 +329,110 @@ def run_ours(a):
         "force_error": err,
         "nve": {"steps": a.steps, "energy_drift_kj_mol": drift,
                 "max_abs_dev_kj_mol": float(np.abs(etot - etot[0]).max()), "kinetic_kj_mol": float(uk[-1, 1])},
-        "verlet_list": lstats,
         "stage_ms_per_launch": stage_ms,
         "stage_share_of_step": step_share,
+        "timed_region": "CUDA-graph replay of every step after the first (profiler off)",
+        "uneven_batch": batched,
+        "parareal": parareal,
     }
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ extra legs
+
+BATCH_SIZES = (20_000, 50_000, 100_000, 150_000, 200_000, 230_000, 250_000)
+
+
+def run_batch_leg(a, torch, api, inputs, dev):
+    """The uneven batch: 7 independent water boxes (20k ... 250k atoms, 1.02 M in
+    total, density of the 1M box) stepped together, one launch per stage."""
+    dens = 1_000_000 / 21.5 ** 3
+    boxes = [inputs.water_box(n, (n / dens) ** (1 / 3), margin=1.0, seed=100 + k, vel_seed=200 + k)
+             for k, n in enumerate(BATCH_SIZES)]
+    m = api.MSM(a=A, h=H, levels=5, precision="fp32", model="water", **WALL)
+    devs = [dev_system(torch, s, dev) for s in boxes]
+    m.md_run_batched(devs, DT, 5, record=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = api.kernel_launches()
+    e0.record(stream)
+    uk = m.md_run_batched(devs, DT, a.batch_steps, record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    launches = api.kernel_launches() - l0
+    n = sum(s.n for s in boxes)
+    etot = uk.sum(-1).cpu().numpy()
+    return {"value": n * a.batch_steps / (t / 1e3), "unit": UNIT, "atoms": n, "systems": list(BATCH_SIZES),
+            "steps": a.batch_steps, "ms_per_step": t / a.batch_steps, "gpu_launches": launches,
+            "launches_per_step": launches / a.batch_steps,
+            "max_energy_drift_kj_mol": float(np.abs(etot[:, -1] - etot[:, 0]).max()),
+            "layout": "one launch per stage for all 7 systems; steps after the first replay a CUDA graph"}
+
+
+KB = 0.0083144626              # kJ/mol/K
+
+
+def relaxed_state(api, inputs, s, steps=40, chunk=50, temp=300.0):
+    """The jittered-lattice start relaxes violently (the potential energy falls by
+    ~10^5 kJ/mol in the first picoseconds).  Parareal is run from a relaxed state:
+    `steps` x `chunk` fine steps with the velocities rescaled to `temp` between
+    chunks (a plain velocity-rescaling thermostat; not timed)."""
+    dof = 6 * s.n_mol + 3 * (s.n - 3 * s.n_mol)
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32", model="water", **WALL)
+    hs = inputs.System(pos=s.pos.copy(), q=s.q, mass=s.mass, box=s.box, vel=s.vel.copy(), n_mol=s.n_mol, lj=s.lj)
+    for _ in range(steps):
+        uk = m.md_run(hs, DT, chunk)
+        hs.vel *= np.sqrt(0.5 * dof * KB * temp / uk[-1, 1])
+    return hs
+
+
+def run_parareal_leg(a, torch, api, inputs, dev):
+    """Parareal on the 10,000-atom box from a relaxed 300 K state: 32 slices of
+    50 fine steps (a = 1.2 nm, h = 0.25 nm, 3 levels, 2 fs) corrected by the
+    coarse propagator (a = 0.8 nm, h = 0.5 nm, 2 levels, 4 fs), FP32 bulk with
+    FP64 corrections, iterated until max |dx| <= 1e-6 nm (at the latest after 32
+    iterations, when every slice is exact), against the serial fine trajectory;
+    and the same with 4 fine steps per slice."""
+    s0 = inputs.water_box(10_000, 4.65, margin=1.0, seed=0, vel_seed=1)
+    s = relaxed_state(api, inputs, s0)
+    n_slices, tol = 32, 1e-6
+    out = {"atoms": s.n, "slices": n_slices, "tol_nm": tol,
+           "start": "relaxed: 2 ps of fine dynamics with velocities rescaled to 300 K every 0.1 ps"}
+    stream = torch.cuda.current_stream()
+    for fsteps in (50, 4):
+        F = dict(a=1.2, h=0.25, levels=3, dt=0.002, steps=fsteps, **WALL)
+        G = dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=fsteps // 2, **WALL)
+        mf = api.MSM(a=F["a"], h=F["h"], levels=F["levels"], precision="fp32", model="water", **WALL)
+        d = dev_system(torch, s, dev)
+        mf.md_run(d, F["dt"], 2, record=False)                  # warm (graph capture, autotune)
+        d = dev_system(torch, s, dev)
+        serial = [d.pos.clone()]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n_slices):
+            mf.md_run(d, F["dt"], F["steps"], record=False)
+            serial.append(d.pos.clone())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_serial = e0.elapsed_time(e1) / 1e3
+        serial = torch.stack(serial).cpu().numpy()
+        hs = inputs.System(pos=s.pos.copy(), q=s.q, mass=s.mass, box=s.box, vel=s.vel.copy(), n_mol=s.n_mol,
+                           lj=s.lj)
+        t = time.perf_counter()
+        xs, vs, it, dx, conv = api.parareal_run(G, F, hs, n_slices, n_slices, tol, precision="fp32")
+        t_par = time.perf_counter() - t
+        out[f"fine_steps_{fsteps}"] = {
+            "iterations": it, "converged": bool(conv), "last_max_dx_nm": dx,
+            "max_error_vs_serial_nm": float(np.abs(xs - serial).max()),
+            "serial_fine_s": t_serial, "parareal_s": t_par, "speedup": t_serial / t_par}
+    out["note"] = ("speedup = serial fine time / parareal time, both on this one GPU; F of all open slices runs "
+                   "as one batch, G slice by slice")
+    return out
 
 
 # -------------------------------------------------------------- reference

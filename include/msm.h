@@ -212,7 +212,12 @@ MSM_API int  md_run_batched(msm_handle *h, int32_t n_sys, msm_system *systems, d
  * (device or host, (n_slices+1)*n*3 each) receive lambda_0..lambda_{n_slices}
  * of the last iterate.  Stops when max |x^{k+1} - x^k| <= tol (nm) or after
  * max_iter iterations; *iters_done and *last_dx (host) report the outcome.
- * Returns MSM_ENOCONV if tol was not met (results still written). */
+ * The water completion's rigid molecules are projected back onto their
+ * constraints after every correction when a correction distorted them by more
+ * than 10x the fine propagator's SHAKE tolerance (exact states pass unchanged).
+ * Returns MSM_ENOCONV, with a message starting "parareal:", if tol was not met
+ * or if the coarse propagator broke down on a corrected state (the iteration
+ * diverged); the last complete iterate is written either way. */
 MSM_API int  parareal_run(const msm_params *G, double dtG, int32_t stepsG,
                   const msm_params *F, double dtF, int32_t stepsF,
                   const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,

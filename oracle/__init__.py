@@ -78,6 +78,8 @@ def lib():
         L.orc_parareal.restype = i
         L.orc_parareal.argtypes = [p, p, i64, i64, p, p, p, p, i, i, d, p, p, p, p]
         L.orc_num_threads.restype = i; L.orc_num_threads.argtypes = []
+        L.orc_project_rigid.restype = i
+        L.orc_project_rigid.argtypes = [i64, i64, p, d, d, p, p]
         _lib = L
     return _lib
 
@@ -301,6 +303,17 @@ def md_run(sys, a, h, levels, dt, n_steps, ke=KE, x=None, v=None, **kw):
     _check(lib().orc_md_run(_ptr(mdp), int(levels), n, int(sys.n_mol), _ptr(x), _ptr(v), _ptr(_f64(sys.q)),
                             _ptr(_f64(sys.mass)), _ptr(lj), _ptr(_f64(sys.box)), float(dt), int(n_steps), _ptr(uk)))
     return x, v, uk
+
+
+def project_rigid(x, v, mass, n_mol, d_oh=0.09572, d_hh=None):
+    """Project distorted rigid triples of (x, v) back onto the constraints (copies;
+    molecules within the threshold are returned unchanged).  Returns (x, v)."""
+    import math
+    if d_hh is None:
+        d_hh = 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
+    x = _f64(x).copy(); v = _f64(v).copy()
+    _check(lib().orc_project_rigid(len(mass), int(n_mol), _ptr(_f64(mass)), float(d_oh), float(d_hh), _ptr(x), _ptr(v)))
+    return x, v
 
 
 def parareal(sys, G: dict, F: dict, n_slices, max_iter, tol, ke=KE):

@@ -29,6 +29,8 @@
  *   orc_md_run .............. Sec. 2, F = -dU/dr and velocity Verlet
  *   orc_parareal ............ Sec. 4, lambda^{k+1}_{n+1} = G(lambda^{k+1}_n)
  *                                       + F(lambda^k_n) - G(lambda^k_n)
+ *   orc_project_rigid ....... water completion: corrected parareal states
+ *                             projected back onto the rigid constraints
  * Readings of points the paper leaves open (self-interaction, open boundaries,
  * grid extents, the force formula, exclusions, parareal order) are stated
  * beside the code that takes them.
@@ -836,6 +838,78 @@ int orc_md_run(const double *mdp, int l, int64_t n, int64_t n_mol, double *x, do
  *   stop when max_{n,i,d} |x^{k+1} - x^k| <= tol, or after max_iter iterations.
  * slices_x/v: (n_slices+1) * n * 3, slot 0 holds state0 on entry.
  * gp/fp: {mdp (9 values), dt, steps, levels}. */
+/* Parareal's correction F + (G_new - G_old) adds positions of rigid molecules
+ * taken from different trajectories, so the corrected molecules need not have
+ * the rigid bond lengths; a grossly distorted one would start the next coarse
+ * propagation outside SHAKE's reach.  Reading for the water completion (the
+ * paper has no constraints): every molecule whose squared bond lengths miss
+ * the rigid ones by more than 10x the SHAKE tolerance (1e-11 relative) is
+ * projected back -- positions by SHAKE iterations along the molecule's own
+ * current bond vectors with inverse-mass weights, until every bond is within
+ * 1e-12 relative, then velocities by the RATTLE velocity stage.  Molecules
+ * within the threshold are left untouched, bit for bit, so states the fine
+ * propagator produced pass through unchanged. */
+static int project_rigid(const orc_model *md, double *x, double *v)
+{
+    static const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+    const double d2[3] = {md->d_oh * md->d_oh, md->d_oh * md->d_oh, md->d_hh * md->d_hh};
+    int bad = 0;
+    for (int64_t mo = 0; mo < md->n_mol; mo++) {
+        int off = 0;
+        for (int c = 0; c < 3; c++) {
+            int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
+            double r2 = 0;
+            for (int d = 0; d < 3; d++) { double t = x[3 * i + d] - x[3 * j + d]; r2 += t * t; }
+            if (fabs(d2[c] - r2) > 1e-11 * d2[c]) off = 1;
+        }
+        if (!off) continue;
+        int it, ok = 0;
+        for (it = 0; it < 1000 && !ok; it++) {
+            ok = 1;
+            for (int c = 0; c < 3; c++) {
+                int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
+                double r[3], r2 = 0;
+                for (int d = 0; d < 3; d++) { r[d] = x[3 * i + d] - x[3 * j + d]; r2 += r[d] * r[d]; }
+                double diff = d2[c] - r2;
+                if (fabs(diff) <= 1e-12 * d2[c]) continue;
+                ok = 0;
+                double wi = 1.0 / md->m[i], wj = 1.0 / md->m[j];
+                double g = diff / (2.0 * r2 * (wi + wj));
+                for (int d = 0; d < 3; d++) { x[3 * i + d] += g * wi * r[d]; x[3 * j + d] -= g * wj * r[d]; }
+            }
+        }
+        if (!ok) { bad += 1; continue; }
+        for (it = 0, ok = 0; it < 1000 && !ok; it++) {
+            ok = 1;
+            for (int c = 0; c < 3; c++) {
+                int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
+                double r[3], r2 = 0, rv = 0;
+                for (int d = 0; d < 3; d++) {
+                    r[d] = x[3 * i + d] - x[3 * j + d];
+                    r2 += r[d] * r[d];
+                    rv += r[d] * (v[3 * i + d] - v[3 * j + d]);
+                }
+                if (fabs(rv) <= 1e-14) continue;
+                ok = 0;
+                double wi = 1.0 / md->m[i], wj = 1.0 / md->m[j];
+                double k = rv / (r2 * (wi + wj));
+                for (int d = 0; d < 3; d++) { v[3 * i + d] -= k * wi * r[d]; v[3 * j + d] += k * wj * r[d]; }
+            }
+        }
+        if (!ok) bad += 1;
+    }
+    return bad ? ORC_ENOCONV : ORC_OK;
+}
+
+/* The projection alone, for its tests: n_mol leading triples of x, v (in place). */
+int orc_project_rigid(int64_t n, int64_t n_mol, const double *m, double d_oh, double d_hh, double *x, double *v)
+{
+    orc_model md;
+    memset(&md, 0, sizeof md);
+    md.n = n; md.n_mol = n_mol; md.m = m; md.d_oh = d_oh; md.d_hh = d_hh;
+    return project_rigid(&md, x, v);
+}
+
 int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
                  const double *q, const double *m, const unsigned char *lj, const double *box,
                  int n_slices, int max_iter, double tol, double *slices_x, double *slices_v,
@@ -873,11 +947,14 @@ int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
         for (int s = 0; s < n_slices; s++) {                               /* sequential correction */
             memcpy(tx, nx + sz * s, sizeof(double) * sz);
             memcpy(tv, nv + sz * s, sizeof(double) * sz);
-            if ((rc = md_steps(&G, tx, tv, dtG, sG, NULL))) goto out;
+            /* a coarse propagation that breaks down on a corrected state means the
+             * iteration diverged: stop with the last complete iterate in slices_x/v */
+            if (md_steps(&G, tx, tv, dtG, sG, NULL)) { rc = ORC_ENOCONV; goto out; }
             for (size_t e = 0; e < sz; e++) {
                 nx[sz * (s + 1) + e] = f_x[sz * s + e] + (tx[e] - gold_x[sz * s + e]);
                 nv[sz * (s + 1) + e] = f_v[sz * s + e] + (tv[e] - gold_v[sz * s + e]);
             }
+            if ((rc = project_rigid(&F, nx + sz * (s + 1), nv + sz * (s + 1)))) goto out;
             memcpy(gold_x + sz * s, tx, sizeof(double) * sz); memcpy(gold_v + sz * s, tv, sizeof(double) * sz);
         }
         double dx = 0;

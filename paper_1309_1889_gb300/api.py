@@ -427,8 +427,8 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
     rc = lib().parareal_run(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
                             int(F["steps"]), C.byref(s), int(n_slices), int(max_iter), float(tol), _ptr(xs),
                             _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
-    if rc not in (0, -6):
-        _check(rc)
+    if rc != 0 and not (rc == -6 and lib().msm_last_error().decode().startswith("parareal:")):
+        _check(rc)                     # a propagator failed (not merely a slow convergence)
     return xs, vs, it.value, dx.value, rc == 0
 
 

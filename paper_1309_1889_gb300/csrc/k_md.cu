@@ -235,7 +235,7 @@ __global__ void k_vv_first(const VVArgs A)
             }
         }
     }
-    if (!ok) set_status(A.status, MSM_ENOCONV);
+    if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 1); atomicCAS(A.status + 3, 0, i0 + 1); }
     const double inv_dt = 1.0 / dt;
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -300,13 +300,21 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
     bool ok = false;
     for (int it = 0; it < A.max_iter && !ok; it++) {
         ok = true;
+        // FP64: |rv| <= tol (absolute, as the oracle).  FP32: |rv| <= tol |r| (|v_a| + |v_b|):
+        // the rounding of rv = r.(v_a - v_b) grows with the atoms' speeds (not with their
+        // difference, which can be tiny), so an absolute or |v_a - v_b|-relative test can stall
+        T spd[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            spd[a] = sizeof(T) == 4 ? sqrt(wv[a][0] * wv[a][0] + wv[a][1] * wv[a][1] + wv[a][2] * wv[a][2]) : T(0);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             const int a = bond_i(c), b = bond_j(c);
             T rv = 0;
 #pragma unroll
             for (int d = 0; d < 3; d++) rv += r[c][d] * (wv[a][d] - wv[b][d]);
-            if (fabs(rv) > tol) {
+            const T lim = sizeof(T) == 4 ? tol * sqrt(r2[c]) * (spd[a] + spd[b]) : tol;
+            if (fabs(rv) > lim) {
                 ok = false;
                 const T k = rv / (r2[c] * (wm[a] + wm[b]));
 #pragma unroll
@@ -314,7 +322,7 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
             }
         }
     }
-    if (!ok) set_status(A.status, MSM_ENOCONV);
+    if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 2); atomicCAS(A.status + 3, 0, i0 + 1); }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         const int i = i0 + a;
@@ -443,6 +451,127 @@ int launch_parareal_update(int count, const double *f, const double *gnew, const
 {
     if (count <= 0) return MSM_OK;
     k_pr_update<<<(count + PR_T - 1) / PR_T, PR_T, 0, st>>>(count, f, gnew, gold, out, prev, dx_partials);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// Rigid-molecule projection after a parareal correction (the water
+// completion's reading; the paper has no constraints): the correction
+// F + (G_new - G_old) adds molecules from different trajectories, so a
+// molecule whose squared bond lengths miss the rigid ones by more than
+// `thresh` (relative) is projected back -- positions by SHAKE iterations along
+// its own current bond vectors (inverse-mass weights) until every bond is
+// within `tol`, then velocities by the RATTLE velocity stage (|rv| <= tol_v).
+// Other molecules are not touched, bit for bit.  FP64, one thread per molecule.
+__global__ void k_pr_project(int n_mol, double *__restrict__ x, double *__restrict__ v, const double *__restrict__ m,
+                             double d_oh2, double d_hh2, double thresh, double tol, double tol_v, int max_iter,
+                             int *__restrict__ status)
+{
+    const int mo = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mo >= n_mol) return;
+    const int i0 = 3 * mo;
+    const double d2[3] = {d_oh2, d_oh2, d_hh2};
+    double p[3][3], w[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        w[a] = 1.0 / m[i0 + a];
+#pragma unroll
+        for (int d = 0; d < 3; d++) p[a][d] = x[3 * (i0 + a) + d];
+    }
+    bool off = false;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int a = bond_i(c), b = bond_j(c);
+        double r2 = 0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) { const double t = p[a][d] - p[b][d]; r2 += t * t; }
+        if (fabs(d2[c] - r2) > thresh * d2[c]) off = true;
+    }
+    if (!off) return;
+    bool ok = false;
+    for (int it = 0; it < max_iter && !ok; it++) {
+        ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int a = bond_i(c), b = bond_j(c);
+            double r[3], r2 = 0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) { r[d] = p[a][d] - p[b][d]; r2 += r[d] * r[d]; }
+            const double diff = d2[c] - r2;
+            if (fabs(diff) <= tol * d2[c]) continue;
+            ok = false;
+            const double g = diff / (2.0 * r2 * (w[a] + w[b]));
+#pragma unroll
+            for (int d = 0; d < 3; d++) { p[a][d] += g * w[a] * r[d]; p[b][d] -= g * w[b] * r[d]; }
+        }
+    }
+    if (!ok) { atomicCAS(status, 0, MSM_ENOCONV); return; }
+    double u[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) u[a][d] = v[3 * (i0 + a) + d];
+    ok = false;
+    for (int it = 0; it < max_iter && !ok; it++) {
+        ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int a = bond_i(c), b = bond_j(c);
+            double r[3], r2 = 0, rv = 0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                r[d] = p[a][d] - p[b][d];
+                r2 += r[d] * r[d];
+                rv += r[d] * (u[a][d] - u[b][d]);
+            }
+            if (fabs(rv) <= tol_v) continue;
+            ok = false;
+            const double k = rv / (r2 * (w[a] + w[b]));
+#pragma unroll
+            for (int d = 0; d < 3; d++) { u[a][d] -= k * w[a] * r[d]; u[b][d] += k * w[b] * r[d]; }
+        }
+    }
+    if (!ok) atomicCAS(status, 0, MSM_ENOCONV);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int d = 0; d < 3; d++) { x[3 * (i0 + a) + d] = p[a][d]; v[3 * (i0 + a) + d] = u[a][d]; }
+}
+
+int launch_pr_project(int n_mol, double *x, double *v, const double *m, double d_oh2, double d_hh2, double thresh,
+                      double tol, double tol_v, int *status, cudaStream_t st)
+{
+    if (n_mol <= 0) return MSM_OK;
+    k_pr_project<<<(n_mol + 127) / 128, 128, 0, st>>>(n_mol, x, v, m, d_oh2, d_hh2, thresh, tol, tol_v, 1000, status);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// Per-block max |a_i - b_i| (the parareal convergence measure).
+__global__ void k_absdiff_partials(int count, const double *__restrict__ a, const double *__restrict__ b,
+                                   double *__restrict__ part)
+{
+    __shared__ double ws[PR_T / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dx = i < count ? fabs(a[i] - b[i]) : 0.0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dx = fmax(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+    if (lane == 0) ws[w] = dx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0;
+        for (int k = 0; k < PR_T / 32; k++) r = fmax(r, ws[k]);
+        part[blockIdx.x] = r;
+    }
+}
+
+int launch_absdiff_partials(int count, const double *a, const double *b, double *part, cudaStream_t st)
+{
+    if (count <= 0) return MSM_OK;
+    k_absdiff_partials<<<(count + PR_T - 1) / PR_T, PR_T, 0, st>>>(count, a, b, part);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

@@ -199,9 +199,11 @@ struct VVArgs {
     double dt;
     double d_oh2, d_hh2;
     double tol;            // relative tolerance on squared bond lengths (SHAKE)
-    double tol_v;          // absolute tolerance on (v_i - v_j).(x_i - x_j) (RATTLE), nm^2/ps
+    double tol_v;          // RATTLE tolerance on (v_i - v_j).(x_i - x_j): absolute (nm^2/ps) in FP64,
+                           // relative to |x_i - x_j| (|v_i| + |v_j|) in FP32
     int max_iter;
-    int *status;
+    int *status;           // on a constraint failure status[1] = 1 (SHAKE) or 2 (RATTLE) and
+                           // status[3] = 1 + the molecule's first atom
 };
 template <typename T> int launch_vv_first(const VVArgs &a, cudaStream_t st);
 template <typename T> int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st);
@@ -214,5 +216,9 @@ int launch_record_uk(int B, const double *sums, int sums_stride, const double *k
 int launch_parareal_update(int count, const double *f, const double *gnew, const double *gold, double *out,
                            const double *prev, double *dx_partials, cudaStream_t st);
 int launch_max_reduce(int m, const double *v, double *out, cudaStream_t st);
+// Rigid-molecule projection of a corrected parareal state (x, v of n_mol leading triples).
+int launch_pr_project(int n_mol, double *x, double *v, const double *m, double d_oh2, double d_hh2, double thresh,
+                      double tol, double tol_v, int *status, cudaStream_t st);
+int launch_absdiff_partials(int count, const double *a, const double *b, double *part, cudaStream_t st);
 
 }  // namespace msm

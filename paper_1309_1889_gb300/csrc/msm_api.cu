@@ -798,7 +798,7 @@ static int list_grow(msm_handle *h, cudaStream_t st);
 // Copy the device status word to the host, synchronise, translate.
 static int finish(msm_handle *h, cudaStream_t st)
 {
-    CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(h->h_status, h->status.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
     if (h->vl_ctl.p) CUDA_TRY(cudaMemcpyAsync(h->h_ctl, h->vl_ctl.p, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     prof_resolve(h);
@@ -810,6 +810,9 @@ static int finish(msm_handle *h, cudaStream_t st)
         if (h->h_ctl[1]) TRY(list_grow(h, st));
     }
     const int s = h->h_status[0];
+    if (s == MSM_ENOCONV && h->h_status[1])
+        return fail_msg(s, "%s did not converge (molecule starting at atom %d of the batch)",
+                        h->h_status[1] == 1 ? "SHAKE" : "RATTLE", h->h_status[3] - 1);
     if (s != 0) return fail_msg(s, "%s", status_text(s));
     return MSM_OK;
 }
@@ -1384,9 +1387,10 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
     int rc = msm_create(F, &hF);
     if (rc) { msm_destroy(hG); return rc; }
     const size_t n3 = 3 * (size_t)s0.n, nn = (size_t)s0.n, ns = (size_t)n_slices;
-    DevBuf lam_x, lam_v, new_x, new_v, gold_x, gold_v, f_x, f_v, tmp_x, tmp_v, q, m, lj, part, dx;
+    DevBuf lam_x, lam_v, new_x, new_v, gold_x, gold_v, f_x, f_v, tmp_x, tmp_v, q, m, lj, part, dx, pst;
     auto cleanup = [&]() {
-        DevBuf *all[] = {&lam_x, &lam_v, &new_x, &new_v, &gold_x, &gold_v, &f_x, &f_v, &tmp_x, &tmp_v, &q, &m, &lj, &part, &dx};
+        DevBuf *all[] = {&lam_x, &lam_v, &new_x, &new_v, &gold_x, &gold_v, &f_x, &f_v, &tmp_x, &tmp_v, &q, &m, &lj,
+                         &part, &dx, &pst};
         for (DevBuf *b : all) release(*b);
         msm_destroy(hG);
         msm_destroy(hF);
@@ -1408,6 +1412,11 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         const size_t nblk = (n3 + 255) / 256;
         TRY(ensure(part, sizeof(double) * nblk * ns));
         TRY(ensure(dx, sizeof(double)));
+        TRY(ensure(pst, sizeof(int)));
+        CUDA_TRY(cudaMemsetAsync(pst.p, 0, sizeof(int), st));
+        // projection of corrected states: threshold 10x, target 1x the fine propagator's SHAKE tolerance
+        const double ptol = F->precision == MSM_FP32 ? shake_tol<float>() : shake_tol<double>();
+        const double d_oh2 = F->d_oh * F->d_oh, d_hh2 = F->d_hh * F->d_hh;
         CUDA_TRY(cudaMemcpyAsync(lam_x.p, s0.x, sizeof(double) * n3, cudaMemcpyDefault, st));
         CUDA_TRY(cudaMemcpyAsync(lam_v.p, s0.v, sizeof(double) * n3, cudaMemcpyDefault, st));
         for (size_t k = 0; k < ns; k++) {
@@ -1426,8 +1435,14 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
             RunSys t;
             t.B = 1; t.sys = &si; t.x = tmp_x.as<double>(); t.v = tmp_v.as<double>();
             t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
-            TRY(run_md(hG, t, dtG, stepsG, nullptr, 0, st));
-            return finish(hG, st);
+            int r = run_md(hG, t, dtG, stepsG, nullptr, 0, st);
+            if (r == MSM_OK) r = finish(hG, st);
+            if (r != MSM_OK) {
+                char m[512];
+                snprintf(m, sizeof m, "%s", msm_last_error());
+                return fail_msg(r, "coarse propagator G: %s", m);
+            }
+            return MSM_OK;
         };
         // init row: lambda^0_{n+1} = G(lambda^0_n)
         for (size_t k = 0; k < ns; k++) {
@@ -1441,6 +1456,7 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         }
         int done = 0;
         double dxh = INFINITY;
+        bool diverged = false;
         for (int it = 0; it < max_iter; it++) {
             const size_t k0 = (size_t)std::min(it, n_slices);    // slices k < it are exact
             // f_n = F(lambda^k_n) for every slice n >= it: one batch
@@ -1450,8 +1466,13 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
                 RunSys t;
                 t.B = (int)(ns - k0); t.sys = sis.data(); t.x = X(f_x, k0); t.v = X(f_v, k0);
                 t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
-                TRY(run_md(hF, t, dtF, stepsF, nullptr, 0, st));
-                TRY(finish(hF, st));
+                int r = run_md(hF, t, dtF, stepsF, nullptr, 0, st);
+                if (r == MSM_OK) r = finish(hF, st);
+                if (r != MSM_OK) {
+                    char m[512];
+                    snprintf(m, sizeof m, "%s", msm_last_error());
+                    return fail_msg(r, "fine propagator F: %s", m);
+                }
             }
             // sequential correction sweep over the slices that are not exact yet
             CUDA_TRY(cudaMemcpyAsync(new_x.p, lam_x.p, sizeof(double) * n3 * (k0 + 1), cudaMemcpyDeviceToDevice, st));
@@ -1460,17 +1481,33 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
             for (size_t k = k0; k < ns; k++) {
                 CUDA_TRY(cudaMemcpyAsync(tmp_x.p, X(new_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
                 CUDA_TRY(cudaMemcpyAsync(tmp_v.p, X(new_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                TRY(runG());
+                const int rg = runG();
+                if (rg != MSM_OK) {
+                    // the coarse propagator broke down on a corrected state: the iteration
+                    // diverged; hand back the last complete iterate
+                    char m[512];
+                    snprintf(m, sizeof m, "%s", msm_last_error());
+                    diverged = true;
+                    fail_msg(MSM_ENOCONV, "parareal: diverged at iteration %d, slice %zu (%s)", it + 1, k, m);
+                    break;
+                }
                 TRY(launch_parareal_update((int)n3, X(f_x, k), tmp_x.as<double>(), X(gold_x, k), X(new_x, k + 1),
-                                           X(lam_x, k + 1), part.as<double>() + k * nblk, st));
+                                           nullptr, nullptr, st));
                 TRY(launch_parareal_update((int)n3, X(f_v, k), tmp_v.as<double>(), X(gold_v, k), X(new_v, k + 1),
                                            nullptr, nullptr, st));
+                TRY(launch_pr_project((int)s0.n_mol, X(new_x, k + 1), X(new_v, k + 1), m.as<double>(), d_oh2, d_hh2,
+                                      10.0 * ptol, ptol, 1e-14, pst.as<int>(), st));
+                TRY(launch_absdiff_partials((int)n3, X(new_x, k + 1), X(lam_x, k + 1), part.as<double>() + k * nblk, st));
                 CUDA_TRY(cudaMemcpyAsync(X(gold_x, k), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
                 CUDA_TRY(cudaMemcpyAsync(X(gold_v, k), tmp_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
             }
+            if (diverged) break;
             TRY(launch_max_reduce((int)(nblk * ns), part.as<double>(), dx.as<double>(), st));
             CUDA_TRY(cudaMemcpyAsync(&hF->h_scal[0], dx.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(hF->h_status + 2, pst.p, sizeof(int), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
+            if (hF->h_status[2]) return fail_msg(MSM_ENOCONV, "projection of a corrected slice onto the rigid "
+                                                              "constraints did not converge");
             dxh = hF->h_scal[0];
             std::swap(lam_x, new_x);
             std::swap(lam_v, new_v);
@@ -1482,6 +1519,7 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         CUDA_TRY(cudaStreamSynchronize(st));
         if (iters_done) *iters_done = done;
         if (last_dx) *last_dx = dxh;
+        if (diverged) return MSM_ENOCONV;                     // message set above
         if (max_iter > 0 && !(dxh <= tol)) return fail_msg(MSM_ENOCONV, "parareal: max |dx| = %g after %d iterations", dxh, done);
         return MSM_OK;
     };

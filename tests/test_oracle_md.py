@@ -134,3 +134,40 @@ def test_wall_bounce_is_elastic():
     ep = oracle.model_forces(sw, 1.2, 0.25, 2, pos=pp, wall_k=5000.0, wall_width=0.5)["energy"]
     em = oracle.model_forces(sw, 1.2, 0.25, 2, pos=pm, wall_k=5000.0, wall_width=0.5)["energy"]
     assert f[0, 0] == pytest.approx(-(ep - em) / (2 * d), rel=1e-6)
+
+
+def test_projection_restores_rigid_geometry_and_conserves_momenta():
+    """The projection of a corrected parareal state (water completion): every
+    distorted molecule gets its rigid bond lengths and zero bond-parallel relative
+    velocities back; each correction moves two atoms by opposite mass-weighted
+    amounts along their bond, so the centre of mass and the linear momentum are
+    conserved exactly, and the velocity stage conserves the angular momentum
+    taken at the projected positions."""
+    s = inputs.water_box(60, 1.0, margin=0.5, seed=11, vel_seed=12)
+    rng = np.random.default_rng(3)
+    x = s.pos.copy(); v = s.vel.copy()
+    k = 3 * s.n_mol
+    x[:k] += rng.normal(0.0, 0.004, (k, 3))           # distort every molecule
+    v[:k] += rng.normal(0.0, 0.5, (k, 3))
+    xp, vp = oracle.project_rigid(x, v, s.mass, s.n_mol)
+    oh1, oh2, hh = _bonds(xp, s.n_mol)
+    assert np.allclose(oh1, inputs.D_OH, rtol=1e-12, atol=0) and np.allclose(oh2, inputs.D_OH, rtol=1e-12, atol=0)
+    assert np.allclose(hh, inputs.d_hh(), rtol=1e-12, atol=0)
+    m3 = xp[:k].reshape(-1, 3, 3); w3 = vp[:k].reshape(-1, 3, 3)
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        assert np.abs(((m3[:, i] - m3[:, j]) * (w3[:, i] - w3[:, j])).sum(-1)).max() <= 1e-14
+    mm = s.mass[:k].reshape(-1, 3, 1)
+    com0 = (mm * x[:k].reshape(-1, 3, 3)).sum(1); com1 = (mm * m3).sum(1)
+    p0 = (mm * v[:k].reshape(-1, 3, 3)).sum(1); p1 = (mm * w3).sum(1)
+    assert np.abs(com1 - com0).max() < 1e-13 and np.abs(p1 - p0).max() < 1e-12
+    L_mid = np.cross(m3, mm * v[:k].reshape(-1, 3, 3)).sum(1)     # new positions, old velocities
+    L1 = np.cross(m3, mm * w3).sum(1)
+    assert np.abs(L1 - L_mid).max() < 1e-12
+    assert np.array_equal(xp[k:], x[k:]) and np.array_equal(vp[k:], v[k:])   # single sites untouched
+
+
+def test_projection_leaves_rigid_molecules_bitwise_unchanged():
+    s = inputs.water_box(60, 1.0, margin=0.5, seed=11, vel_seed=12)
+    x, v, _ = oracle.md_run(s, dt=0.002, n_steps=3, **FINE)       # SHAKE/RATTLE output
+    xp, vp = oracle.project_rigid(x, v, s.mass, s.n_mol)
+    assert np.array_equal(xp, x) and np.array_equal(vp, v)
