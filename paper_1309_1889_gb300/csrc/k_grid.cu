@@ -261,38 +261,60 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
 // (the plane plus an x/y halo of rad points); every plane row (y + dy) is read
 // into registers once and applied to the ST_RZ output planes it reaches
 // (dz = z' - z), walking the tap row (dy, dz) of the sphere with compile-time
-// offsets.  The weight table W[n] = g^0(|n| h) sits in shared memory; the level
-// factor 2^{-k} is applied at the end.  CTAs take tiles from a counter.
+// offsets.  The weights W[n] = g^0(|n| h) depend on |n| only, so one octant of
+// the table sits in shared memory (small enough for many resident CTAs); the
+// level factor 2^{-k} is applied at the end.  CTAs take tiles from a counter.
 constexpr int ST_RX = 4, ST_RZ = 4;
 constexpr int ST_TXT = 8, ST_TYT = 8;                 // threads along x and y
 constexpr int ST_TX = ST_TXT * ST_RX, ST_TY = ST_TYT, ST_TZ = ST_RZ;
 constexpr int ST_THREADS = ST_TXT * ST_TYT;
 constexpr int ST_MAXRAD = 12;
 
-__host__ __device__ constexpr int st_px(int rad) { return ST_TX + 2 * rad; }
+// Plane rows and weight rows are padded to multiples of 4 values so that rows
+// start on 16-byte boundaries and are read four values per load.
+__host__ __device__ constexpr int st_up4(int v) { return (v + 3) & ~3; }
+__host__ __device__ constexpr int st_px(int rad) { return st_up4(ST_TX + 2 * rad); }
 __host__ __device__ constexpr int st_py(int rad) { return ST_TY + 2 * rad; }
+__host__ __device__ constexpr int st_r1p(int rad) { return st_up4(rad + 1); }
 
+// Shared memory of one CTA: the weight octant W[|dz|][|dy|][|dx|] ((rad+1)^2
+// rows of st_r1p values; the weights depend on |n| only), one input plane with
+// its halo, and the half-widths of the tap rows by (|dz|, |dy|).
 template <typename T> size_t stencil_smem_bytes(int rad)
 {
-    const int wd = 2 * rad + 1;
-    return sizeof(T) * ((size_t)wd * wd * wd + (size_t)st_px(rad) * st_py(rad)) + sizeof(int) * (size_t)(wd * wd + 4);
+    const size_t r1 = (size_t)rad + 1;
+    return sizeof(T) * (r1 * r1 * (size_t)st_r1p(rad) + (size_t)st_px(rad) * st_py(rad)) + sizeof(int) * (r1 * r1 + 4);
 }
 template size_t stencil_smem_bytes<float>(int);
 template size_t stencil_smem_bytes<double>(int);
 
+// Values of one plane row in registers: ST_RX + 2 RAD used, rounded up to 4.
+template <int RAD> struct StRow { static constexpr int N = st_up4(ST_RX + 2 * RAD); };
+
 template <int W, int RAD, typename T>
-__device__ __forceinline__ void stencil_row(const T (&v)[ST_RX + 2 * RAD], const T *__restrict__ wr, T (&acc)[ST_RX])
+__device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T *__restrict__ wr, T (&acc)[ST_RX])
 {
+    constexpr int NW = st_up4(W + 1);
+    T w[NW];                                                   // octant row |dx| = 0..W (16-byte aligned)
+    if (sizeof(T) == sizeof(float)) {
+#pragma unroll
+        for (int k = 0; k < NW; k += 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(wr + k);
+            w[k] = f.x; w[k + 1] = f.y; w[k + 2] = f.z; w[k + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k <= W; k++) w[k] = wr[k];
+    }
 #pragma unroll
     for (int d = -W; d <= W; d++) {
-        const T w = wr[d];
 #pragma unroll
-        for (int r = 0; r < ST_RX; r++) acc[r] = fma(w, v[r + d + RAD], acc[r]);
+        for (int r = 0; r < ST_RX; r++) acc[r] = fma(w[d < 0 ? -d : d], v[r + d + RAD], acc[r]);
     }
 }
 
 template <int RAD, typename T>
-__device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[ST_RX + 2 * RAD], const T *wr, T (&acc)[ST_RX])
+__device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<RAD>::N], const T *wr, T (&acc)[ST_RX])
 {
     switch (w) {
 #define ST_CASE(k) case k: if (k <= RAD) stencil_row<(k <= RAD ? k : 0), RAD>(v, wr, acc); break;
@@ -306,20 +328,23 @@ __device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[ST_RX +
 template <typename T, int RAD>
 __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, int *__restrict__ counter)
 {
-    constexpr int WD = 2 * RAD + 1, PX = st_px(RAD), PY = st_py(RAD);
+    constexpr int WD = 2 * RAD + 1, R1 = RAD + 1, R1P = st_r1p(RAD), PX = st_px(RAD), PY = st_py(RAD);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *wt = reinterpret_cast<T *>(smem_raw);                 // WD^3 weights
-    T *plane = wt + WD * WD * WD;                            // PY x PX input plane
-    int *hw = reinterpret_cast<int *>(plane + PX * PY);      // WD^2 half widths (-1: empty row)
+    T *wt = reinterpret_cast<T *>(smem_raw);                 // R1 x R1 rows of R1P weights W[|dz|][|dy|][|dx|]
+    T *plane = wt + R1 * R1 * R1P;                           // PY x PX input plane
+    int *hw = reinterpret_cast<int *>(plane + PX * PY);      // R1^2 half widths by (|dz|, |dy|) (-1: empty)
     __shared__ int s_tile, s_ent;
     if (failed(A.status)) return;
     const int t = threadIdx.x;
-    for (int e = t; e < WD * WD * WD; e += ST_THREADS) wt[e] = A.w[e];
-    for (int e = t; e < WD * WD; e += ST_THREADS) hw[e] = -1;
+    for (int e = t; e < R1 * R1 * R1P; e += ST_THREADS) {
+        const int ax = e % R1P, ay = (e / R1P) % R1, az = e / (R1P * R1);
+        wt[e] = ax < R1 ? A.w[((az + RAD) * WD + (ay + RAD)) * WD + (ax + RAD)] : T(0);
+    }
+    for (int e = t; e < R1 * R1; e += ST_THREADS) hw[e] = -1;
     __syncthreads();
     for (int e = t; e < A.sg.nrows; e += ST_THREADS) {
         const int4 r = A.rows[e];
-        hw[(r.y + RAD) * WD + (r.x + RAD)] = r.z;
+        if (r.x >= 0 && r.y >= 0) hw[r.y * R1 + r.x] = r.z;
     }
     const int lx = t % ST_TXT, ly = t / ST_TXT;
     const int total = A.total_tiles, nent = A.bt.B * A.nlev;
@@ -366,17 +391,27 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
             if (!zin) continue;
 #pragma unroll 1
             for (int dy = -RAD; dy <= RAD; dy++) {
-                T v[ST_RX + 2 * RAD];
-                const T *row = plane + (ly + RAD + dy) * PX + lx * ST_RX;
+                constexpr int NV = StRow<RAD>::N;
+                T v[NV];
+                const T *row = plane + (ly + RAD + dy) * PX + lx * ST_RX;    // 16-byte aligned
+                if (sizeof(T) == sizeof(float)) {
 #pragma unroll
-                for (int i = 0; i < ST_RX + 2 * RAD; i++) v[i] = row[i];
+                    for (int i = 0; i < NV; i += 4) {
+                        const float4 f = *reinterpret_cast<const float4 *>(row + i);
+                        v[i] = f.x; v[i + 1] = f.y; v[i + 2] = f.z; v[i + 3] = f.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NV; i++) v[i] = row[i];
+                }
 #pragma unroll
                 for (int s = 0; s < ST_RZ; s++) {
                     const int dz = zp - (z0 + s);
                     if (dz < -RAD || dz > RAD) continue;
-                    const int w = hw[(dz + RAD) * WD + (dy + RAD)];
+                    const int adz = dz < 0 ? -dz : dz, ady = dy < 0 ? -dy : dy;
+                    const int w = hw[adz * R1 + ady];
                     if (w < 0) continue;
-                    stencil_row_dispatch<RAD>(w, v, wt + ((dz + RAD) * WD + (dy + RAD)) * WD + RAD, acc[s]);
+                    stencil_row_dispatch<RAD>(w, v, wt + (adz * R1 + ady) * R1P, acc[s]);
                 }
             }
         }

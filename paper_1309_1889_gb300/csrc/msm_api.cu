@@ -351,15 +351,18 @@ static int ensure_host_e(msm_handle *h, int B)
 // system's mean density (one i atom per lane), unless the autotuner timed
 // this geometry.  The shape changes only the speed, never the results: each
 // i atom sums its j's in ascending slot order whatever the brick.
-static const int kBrickShapes[7][3] = {{1, 1, 1}, {2, 1, 1}, {2, 2, 1}, {2, 2, 2}, {4, 2, 2}, {4, 4, 2}, {4, 4, 4}};
+static const int kNumShapes = 11;
+static const int kBrickShapes[kNumShapes][3] = {{1, 1, 1}, {2, 1, 1}, {2, 2, 1}, {2, 2, 2}, {3, 2, 2}, {4, 2, 2},
+                                                {3, 3, 2}, {5, 2, 2}, {4, 3, 2}, {4, 4, 2}, {4, 4, 4}};
 
+// The largest shape (by volume) that holds at most ~28 atoms at the mean density.
 static int brick_heuristic(int64_t n, const CellGeom &g)
 {
     const double per_cell = (double)n / (double)g.ncells;
     int pick = 0;
-    for (int s = 0; s < 7; s++) {
+    for (int s = 0; s < kNumShapes; s++) {
         const int vol = kBrickShapes[s][0] * kBrickShapes[s][1] * kBrickShapes[s][2];
-        if (per_cell * vol <= 24.0) pick = s;
+        if (per_cell * vol <= 28.0) pick = s;
     }
     return pick;
 }
@@ -622,7 +625,7 @@ static ShortArgs<T> short_args(msm_handle *h)
 }
 
 // The brick autotuner: on the first evaluation of a single system's geometry,
-// time the short-range kernel for the brick shapes around the heuristic's
+// time the short-range kernel for the five brick shapes around the heuristic's
 // choice (after binning, on the real atoms) and keep the fastest.  It runs
 // outside any graph capture and synchronises the stream.
 template <typename T>
@@ -637,7 +640,7 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
     float best = 1e30f;
     int best_s = h0;
     const bool model = h->p.model == MSM_MODEL_WATER;
-    for (int sidx = std::max(0, h0 - 1); sidx <= std::min(6, h0 + 1); sidx++) {
+    for (int sidx = std::max(0, h0 - 2); sidx <= std::min(kNumShapes - 1, h0 + 2); sidx++) {
         set_bricks(D, kBrickShapes[sidx]);
         CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
         ShortArgs<T> s = short_args<T>(h);
