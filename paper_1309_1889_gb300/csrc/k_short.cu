@@ -17,8 +17,8 @@
 // it stages by binary search over the offsets.  All lanes then read each
 // staged j by broadcast.  Per candidate a lane evaluates one rsqrt and ~20
 // FP32 FMA-pipe instructions; pairs beyond a, the pair j = i and pairs inside
-// one rigid molecule are masked by substitution (exact zero contributions),
-// never by divergence.  More rows than the list holds are taken in segments.
+// one rigid molecule get charge zero (exact zero contributions), never a
+// branch.  More rows than the list holds are taken in segments.
 //
 // Each i adds its in-range j's in ascending slot order into one accumulator,
 // whatever the brick shape or chunking: results are bitwise reproducible and
@@ -56,6 +56,13 @@ __device__ __forceinline__ T warp_max(T v)
     return v;
 }
 
+// Added to every r^2 (through the FMA chain, so it costs no instruction): keeps
+// rsqrt and 1/r^3 finite for the pair j = i, whose charge is masked to zero.
+// Far below one ulp of any real pair distance squared, so no real pair changes.
+template <typename T> __device__ __forceinline__ T r2_eps();
+template <> __device__ __forceinline__ float r2_eps<float>() { return 1e-12f; }
+template <> __device__ __forceinline__ double r2_eps<double>() { return 1e-30; }
+
 template <typename T> struct ShortSmem {
     int rs0[SR_WARPS][SR_MAXROWS];      // first slot of each kept row
     int rend[SR_WARPS][SR_MAXROWS];     // running end of each row in the concatenation
@@ -67,7 +74,7 @@ template <typename T> struct ShortSmem {
 // exclusion kernel removes their smooth part), LJ between flagged sites.
 // COUNT: diagnostics only -- count the pairs inside the cutoff instead of summing.
 template <typename T, bool MODEL, bool COUNT>
-__global__ void __launch_bounds__(SR_WARPS * 32) k_short(const ShortArgs<T> A)
+__global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -184,12 +191,14 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_short(const ShortArgs<T> A)
                 for (int k = 0; k < cnt; k++) {
                     const vec4<T> pj = S.sj[wid][k];
                     const T dx = pj.x - pi.x, dyy = pj.y - pi.y, dzz = pj.z - pi.z;
-                    const T r2 = fma(dx, dx, fma(dyy, dyy, dzz * dzz));
-                    bool in = (r2 < A.a2) & (r2 > T(0));
+                    const T r2s = fma(dx, dx, fma(dyy, dyy, fma(dzz, dzz, r2_eps<T>())));
+                    bool in = r2s < A.a2;
                     int fj = 0;
+                    // j = i: the water model's molecule test excludes it (an atom is in its own
+                    // molecule); bare charges test the distance
                     if (MODEL) { fj = S.sf[wid][k]; in = in & ((unsigned)(fi ^ fj) >= 2u); }
+                    else in = in & (r2s > T(2) * r2_eps<T>());
                     if (COUNT) { npair += in ? 1 : 0; continue; }
-                    const T r2s = in ? r2 : A.a2;
                     const T qj = in ? pj.w : T(0);
                     const T ri = rsqrt_t<T>(r2s);
                     const T ri2 = ri * ri;
@@ -200,8 +209,9 @@ __global__ void __launch_bounds__(SR_WARPS * 32) k_short(const ShortArgs<T> A)
                     ax = fma(sc, dx, ax); ay = fma(sc, dyy, ay); az = fma(sc, dzz, az);
                     if (MODEL) {
                         if (fj & 1) {                           // uniform: j is broadcast
-                            const T m = ((fi & 1) && in) ? T(1) : T(0);
-                            const T sr2 = A.lj_s2 * ri2;
+                            const bool on = (fi & 1) && in;
+                            const T m = on ? T(1) : T(0);
+                            const T sr2 = A.lj_s2 * (on ? ri2 : T(0));  // masked pairs (j = i: r^2 = eps) stay finite
                             const T sr6 = sr2 * sr2 * sr2;
                             le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
                             const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
