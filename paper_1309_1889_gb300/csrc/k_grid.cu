@@ -88,11 +88,38 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
         S.cell_off[e + 1] = c;
     }
     __syncthreads();
-    if (t == 0) {
-        int acc = 0;
-        S.cell_off[0] = 0;
-        for (int e = 1; e <= AC_N; e++) { acc += S.cell_off[e]; S.cell_off[e] = acc; }
-        s_total = acc;
+    {
+        // inclusive prefix sum of the counts in place (cell_off[e] becomes the first
+        // staged atom of cell e): AT_PER consecutive cells per thread, then a block scan
+        constexpr int AT_PER = (AC_N + AT_THREADS - 1) / AT_THREADS;
+        __shared__ int ws[AT_THREADS / 32];
+        int loc[AT_PER], sum = 0;
+#pragma unroll
+        for (int k = 0; k < AT_PER; k++) {
+            const int e = t * AT_PER + k;
+            loc[k] = e < AC_N ? S.cell_off[e + 1] : 0;
+            sum += loc[k];
+        }
+        const int lane = t & 31, w = t >> 5;
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) ws[w] = inc;
+        __syncthreads();
+        int wbase = 0;
+        for (int k = 0; k < w; k++) wbase += ws[k];
+        int run = wbase + inc - sum;                       // exclusive prefix of this thread's cells
+#pragma unroll
+        for (int k = 0; k < AT_PER; k++) {
+            const int e = t * AT_PER + k;
+            run += loc[k];
+            if (e < AC_N) S.cell_off[e + 1] = run;
+        }
+        if (t == 0) S.cell_off[0] = 0;
+        if (t == AT_THREADS - 1) s_total = run;
     }
     __syncthreads();
     const bool staged = s_total <= AT_CAP;
@@ -118,15 +145,16 @@ __global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
     const int mx = L.lo[0] + ix, my = L.lo[1] + iy, mz = L.lo[2] + iz;
     T acc = 0;
     // point mu receives weight index O = mu - c + 1 from an atom in cell c
-#pragma unroll
+    // runtime loops: the unrolled 64-cell body does not fit the instruction cache
+#pragma unroll 1
     for (int oz = 0; oz < 4; oz++) {
         const int cz = mz + 1 - oz;
         if (cz < 0 || cz >= nz) continue;
-#pragma unroll
+#pragma unroll 1
         for (int oy = 0; oy < 4; oy++) {
             const int cy = my + 1 - oy;
             if (cy < 0 || cy >= ny) continue;
-#pragma unroll
+#pragma unroll 1
             for (int ox = 0; ox < 4; ox++) {
                 const int cx = mx + 1 - ox;
                 if (cx < 0 || cx >= nx) continue;
