@@ -280,10 +280,11 @@ MSM_API int  msm_cell_list_noalloc(int64_t n, const double *pos, const double bo
                                    void *stream);
 
 /* Verlet-list statistics of h since its creation (up to max values):
- * builds, overflows (a capacity was exceeded: that step used the cell search
- * and the capacity grew), entries-per-atom capacity, neighbourhood capacity,
- * row slots per group, and the largest entries per atom, neighbourhood and
- * row count seen at a build. */
+ * builds, overflows (a capacity was exceeded or a brick could not be encoded:
+ * that step used the cell search and the capacity grew), entries-per-atom
+ * capacity, O-O entries-per-atom capacity, row slots per brick, and the
+ * largest entries per atom, O-O entries per atom and row count seen at a
+ * build. */
 MSM_API int  msm_list_stats(msm_handle *h, int64_t *out, int32_t max);
 
 /* Number of kernels this library launched since load (all handles). */

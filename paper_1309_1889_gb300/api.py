@@ -327,8 +327,8 @@ class MSM:
     def list_stats(self) -> dict:
         v = np.zeros(8, dtype=np.int64)
         _check(lib().msm_list_stats(self._h, _ptr(v), 8))
-        keys = ("builds", "overflows", "cap_entries", "cap_neighbourhood", "row_slots", "max_entries_seen",
-                "max_neighbourhood_seen", "max_rows_seen")
+        keys = ("builds", "overflows", "cap_entries", "cap_lj_entries", "row_slots", "max_entries_seen",
+                "max_lj_entries_seen", "max_rows_seen")
         return {k: int(x) for k, x in zip(keys, v)}
 
     def count_pairs(self) -> int:

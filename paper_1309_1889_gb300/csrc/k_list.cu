@@ -6,20 +6,28 @@
 // stays exact while no atom has moved more than skin/2 since the build: every
 // pair inside a is then in it, and the r < a test is still applied per pair.
 //
-// Reference frame: at a build, the current cell sort (perm, cell_start) is
-// frozen as the list's reference order.  A group = 2 x 2 bricks in (y, z)
-// (one brick per warp, the bricks of the cell-search kernel) shares one
-// neighbourhood J: the cell rows within a + skin of the group's atom bounding
-// box, each one contiguous range of reference slots.  List entries are uint16
-// indices into J, which is staged in shared memory every step; Coulomb
-// entries run forward from slot * cap, O-O LJ entries backward from
-// slot * cap + cap - 1.  Intramolecular pairs of the water completion are
-// left out at build time.
+// Reference frame: at a build the current cell sort (perm, cell_start) is
+// frozen as the list's reference order, and every step gathers that step's
+// positions into it (vl_pos).  The build runs the cell search of k_short -- one
+// warp per brick, the brick's candidate rows (within a + skin of its atoms'
+// bounding box) compacted into a row table, the row stream staged 32 atoms at
+// a time and broadcast -- but instead of summing it appends every j within
+// a + skin (other molecules only) to the lane's list.  An entry is 16 bits:
+// the row's index in the brick's row table (9 bits) and the atom's offset in
+// the row (7 bits).  Entries go four to a 64-bit word, and word q of slot s is
+// stored at [q * n + s], so that the lanes of a warp read their words side by
+// side.  O-O pairs of the water completion also go to a second, shorter list
+// for the LJ term.
+//
+// The force kernel is one warp per brick again: the brick's row table in
+// shared memory, each lane walking its own list and reading its j positions
+// through the L1 cache.  Each lane adds its pairs in list order, i.e. in
+// ascending reference slot order.
 //
 // Device flags (ctl): [0] max displacement^2 bits this step, [1] overflow
 // (sticky until the host grows the buffers), [2] list invalid, [3] rebuild
-// this step, [4] largest entries per atom seen, [5] largest neighbourhood
-// seen, [6] largest row count seen.  No kernel waits on another: each one
+// this step, [4] largest entries per atom seen, [5] largest O-O entries seen,
+// [6] largest row count seen, [7] builds.  No kernel waits on another: each
 // reads the flags written by earlier launches in the stream and returns early
 // when it has nothing to do, so a step never needs a host synchronisation.
 #include <stdint.h>
@@ -30,7 +38,7 @@
 
 namespace msm {
 
-constexpr int VL_WARPS = 4;         // bricks (by + wy, bz + wz), wy, wz in {0, 1}
+constexpr int VL_WARPS = 4;         // bricks per CTA
 
 __device__ __forceinline__ bool vl_rebuild(const int *ctl) { return ctl[3] != 0; }
 __device__ __forceinline__ bool vl_usable(const int *ctl) { return ctl[1] == 0 && ctl[2] == 0; }
@@ -38,6 +46,10 @@ __device__ __forceinline__ bool vl_usable(const int *ctl) { return ctl[1] == 0 &
 template <typename T> __device__ __forceinline__ T vl_rsqrt(T x);
 template <> __device__ __forceinline__ float vl_rsqrt<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double vl_rsqrt<double>(double x) { return rsqrt(x); }
+// added to r^2 through the FMA chain: keeps rsqrt finite for masked entries
+template <typename T> __device__ __forceinline__ T vl_eps();
+template <> __device__ __forceinline__ float vl_eps<float>() { return 1e-12f; }
+template <> __device__ __forceinline__ double vl_eps<double>() { return 1e-30; }
 
 // ------------------------------------------------------------ displacement
 
@@ -84,23 +96,8 @@ __global__ void k_list_snapshot(ListArgs<T> A)
 
 // ------------------------------------------------------------------ build
 
-struct VLRow { int y, z, s0, len, base, xlo, xhi, pad; };
-
-template <typename T>
-__device__ __forceinline__ void warp_bbox(bool valid, const vec4<T> &p, T lo[3], T hi[3])
-{
-    const T inf = (T)1e30;
-    T v[6] = {valid ? p.x : inf, valid ? p.y : inf, valid ? p.z : inf,
-              valid ? -p.x : inf, valid ? -p.y : inf, valid ? -p.z : inf};
-#pragma unroll
-    for (int k = 0; k < 6; k++)
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
-    lo[0] = v[0]; lo[1] = v[1]; lo[2] = v[2]; hi[0] = -v[3]; hi[1] = -v[4]; hi[2] = -v[5];
-}
-
-// i atoms of brick (bx, by, bz) in the order of the cell-search kernel; returns their count and,
-// for lane-th atom of chunk base, its slot (or -1)
+// i atoms of brick (bx, by, bz) in the order of the cell-search kernel; returns
+// the want-th atom's slot (or -1) and, in *count, the brick's atom count
 __device__ __forceinline__ int brick_slot(const int *__restrict__ start, const CellGeom &g, const int bd[3], int bx,
                                           int by, int bz, int want, int *count)
 {
@@ -121,184 +118,178 @@ __device__ __forceinline__ int brick_slot(const int *__restrict__ start, const C
 }
 
 template <typename T>
+__device__ __forceinline__ T warp_minv(T v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+struct VLBuildSmem {
+    int rs0[VL_WARPS][VL_ROWS];     // first slot of each candidate row
+    int rend[VL_WARPS][VL_ROWS];    // running end of each row in the row stream
+};
+
+template <typename T>
 __global__ void __launch_bounds__(VL_WARPS * 32) k_list_build(ListArgs<T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ VLBuildSmem S;
+    __shared__ vec4<T> sj[VL_WARPS][32];
+    __shared__ int sf[VL_WARPS][32], ss[VL_WARPS][32], sc[VL_WARPS][32];
     if (!vl_rebuild(A.ctl) || failed(A.status)) return;
-    vec4<T> *sJ = reinterpret_cast<vec4<T> *>(smem_raw);                  // jcap
-    int *sF = reinterpret_cast<int *>(sJ + A.jcap);                        // jcap flags
-    VLRow *sR = reinterpret_cast<VLRow *>(sF + A.jcap);                    // max_rows
-    uint16_t *sB = reinterpret_cast<uint16_t *>(sR + A.max_rows);          // VL_WARPS x 32 x 16 write buffers
-    __shared__ T s_bb[VL_WARPS][6];
-    __shared__ int s_cnt[VL_WARPS];
-    __shared__ int s_nrows, s_J, s_bad;
-
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int g = blockIdx.x;
-    const int gx = g % A.ng[0], gyb = (g / A.ng[0]) % A.ng[1], gzb = g / (A.ng[0] * A.ng[1]);
-    const int bx = gx, by = 2 * gyb + (wid & 1), bz = 2 * gzb + (wid >> 1);
-    const bool brick_ok = by < A.nb[1] && bz < A.nb[2];
+    const int brick = blockIdx.x * VL_WARPS + wid;
+    if (brick >= A.nbricks) return;
+    const unsigned lt = (1u << lane) - 1u;
     const CellGeom &G = A.g;
+    const int nx = G.nc[0], ny = G.nc[1], nz = G.nc[2];
+    const int bx = brick % A.nb[0], by = (brick / A.nb[0]) % A.nb[1], bz = brick / (A.nb[0] * A.nb[1]);
     const T h = (T)G.h, inv_h = T(1) / h;
 
-    // bounding box of each brick's atoms (all chunks)
+    // bounding box of all the brick's atoms
     int n_i = 0;
-    if (brick_ok) brick_slot(A.start, G, A.bd, bx, by, bz, 0, &n_i);
-    T blo[3] = {(T)1e30, (T)1e30, (T)1e30}, bhi[3] = {(T)-1e30, (T)-1e30, (T)-1e30};
+    brick_slot(A.start, G, A.bd, bx, by, bz, 0, &n_i);
+    if (n_i == 0) { if (lane == 0) A.rtn[brick] = 0; return; }
+    T lo[3] = {(T)1e30, (T)1e30, (T)1e30}, nhi[3] = {(T)1e30, (T)1e30, (T)1e30};   // nhi: -max
     for (int base = 0; base < n_i; base += 32) {
         int c;
         const int sl = brick_slot(A.start, G, A.bd, bx, by, bz, base + lane, &c);
-        const vec4<T> p = sl >= 0 ? A.apos[sl] : vec4<T>{0, 0, 0, 0};
-        T lo[3], hi[3];
-        warp_bbox(sl >= 0, p, lo, hi);
+        const bool ok = sl >= 0;
+        const vec4<T> p = ok ? A.apos[sl] : vec4<T>{(T)0, (T)0, (T)0, (T)0};
+        lo[0] = min(lo[0], warp_minv(ok ? p.x : (T)1e30));
+        lo[1] = min(lo[1], warp_minv(ok ? p.y : (T)1e30));
+        lo[2] = min(lo[2], warp_minv(ok ? p.z : (T)1e30));
+        nhi[0] = min(nhi[0], warp_minv(ok ? -p.x : (T)1e30));
+        nhi[1] = min(nhi[1], warp_minv(ok ? -p.y : (T)1e30));
+        nhi[2] = min(nhi[2], warp_minv(ok ? -p.z : (T)1e30));
+    }
+    const T hi[3] = {-nhi[0], -nhi[1], -nhi[2]};
+
+    // candidate rows within a + skin of the box, compacted into the row table
+    const T rs = A.rl_sel, rs2 = rs * rs;
+    const int zlo = max(0, (int)floor((lo[2] - rs) * inv_h)), zhi = min(nz - 1, (int)floor((hi[2] + rs) * inv_h));
+    const int ylo = max(0, (int)floor((lo[1] - rs) * inv_h)), yhi = min(ny - 1, (int)floor((hi[1] + rs) * inv_h));
+    const int nyr = yhi - ylo + 1, nr_all = max(0, zhi - zlo + 1) * max(0, nyr);
+    int nrows = 0, total = 0;
+    bool bad = false;
+    for (int r0 = 0; r0 < nr_all; r0 += 32) {
+        const int r = r0 + lane;
+        int s0 = 0, len = 0;
+        if (r < nr_all) {
+            const int cz = zlo + r / nyr, cy = ylo + r % nyr;
+            const T dz = max(T(0), max(T(cz) * h - hi[2], lo[2] - T(cz + 1) * h));
+            const T dy = max(T(0), max(T(cy) * h - hi[1], lo[1] - T(cy + 1) * h));
+            const T d2 = dy * dy + dz * dz;
+            if (d2 < rs2) {
+                const T rx = sqrt(rs2 - d2);
+                const int xlo = max(0, (int)floor((lo[0] - rx) * inv_h));
+                const int xhi = min(nx - 1, (int)floor((hi[0] + rx) * inv_h));
+                if (xlo <= xhi) {
+                    const int rb = (cz * ny + cy) * nx;
+                    s0 = A.start[rb + xlo];
+                    len = A.start[rb + xhi + 1] - s0;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, len > 0);
+        bad = bad || __any_sync(0xffffffffu, len >= VL_OFFS);
+        int incl = len;
 #pragma unroll
-        for (int d = 0; d < 3; d++) { blo[d] = min(blo[d], lo[d]); bhi[d] = max(bhi[d], hi[d]); }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int pos = nrows + __popc(m & lt);
+        if (len > 0 && pos < VL_ROWS) {
+            S.rs0[wid][pos] = s0;
+            S.rend[wid][pos] = total + incl;
+            A.rtab[(size_t)brick * VL_ROWS + pos] = s0;
+        }
+        nrows += __popc(m);
+        total += __shfl_sync(0xffffffffu, incl, 31);
     }
     if (lane == 0) {
-        s_cnt[wid] = n_i;
-#pragma unroll
-        for (int d = 0; d < 3; d++) { s_bb[wid][d] = blo[d]; s_bb[wid][3 + d] = bhi[d]; }
+        atomicMax(&A.ctl[6], nrows);
+        A.rtn[brick] = min(nrows, VL_ROWS);
     }
-    __syncthreads();
-
-    // union rows (warp 0): cell rows within a + skin of the union box
-    if (wid == 0) {
-        T ulo[3] = {(T)1e30, (T)1e30, (T)1e30}, uhi[3] = {(T)-1e30, (T)-1e30, (T)-1e30};
-        int tot = 0;
-        for (int w = 0; w < VL_WARPS; w++)
-            if (s_cnt[w] > 0) {
-                tot += s_cnt[w];
-#pragma unroll
-                for (int d = 0; d < 3; d++) { ulo[d] = min(ulo[d], s_bb[w][d]); uhi[d] = max(uhi[d], s_bb[w][3 + d]); }
-            }
-        int nrows = 0, J = 0, bad = 0;
-        if (tot > 0) {
-            const T rs = A.rl_sel, rs2 = rs * rs;
-            const int zlo = max(0, (int)floor((ulo[2] - rs) * inv_h)), zhi = min(G.nc[2] - 1, (int)floor((uhi[2] + rs) * inv_h));
-            const int ylo = max(0, (int)floor((ulo[1] - rs) * inv_h)), yhi = min(G.nc[1] - 1, (int)floor((uhi[1] + rs) * inv_h));
-            const int ny = yhi - ylo + 1, cnt_rows = (zhi - zlo + 1) * ny;
-            for (int r0 = 0; r0 < cnt_rows; r0 += 32) {
-                const int r = r0 + lane;
-                int keep = 0, s0 = 0, len = 0, xlo = 0, xhi = -1, cy = 0, cz = 0;
-                if (r < cnt_rows) {
-                    cz = zlo + r / ny; cy = ylo + r % ny;
-                    const T dz = max(T(0), max(T(cz) * h - uhi[2], ulo[2] - T(cz + 1) * h));
-                    const T dy = max(T(0), max(T(cy) * h - uhi[1], ulo[1] - T(cy + 1) * h));
-                    const T d2 = dy * dy + dz * dz;
-                    if (d2 < rs2) {
-                        const T rx = sqrt(rs2 - d2);
-                        xlo = max(0, (int)floor((ulo[0] - rx) * inv_h));
-                        xhi = min(G.nc[0] - 1, (int)floor((uhi[0] + rx) * inv_h));
-                        if (xlo <= xhi) {
-                            const int rb = (cz * G.nc[1] + cy) * G.nc[0];
-                            s0 = A.start[rb + xlo];
-                            len = A.start[rb + xhi + 1] - s0;
-                            keep = 1;
-                        }
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                int incl = len;                                        // inclusive scan of len over kept lanes
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(0xffffffffu, incl, o); if (lane >= o) incl += y; }
-                const int pos = nrows + __popc(m & ((1u << lane) - 1));
-                if (keep) {
-                    if (pos < A.max_rows) {
-                        VLRow row;
-                        row.y = cy; row.z = cz; row.s0 = s0; row.len = len; row.base = J + incl - len;
-                        row.xlo = xlo; row.xhi = xhi; row.pad = 0;
-                        sR[pos] = row;
-                        A.grp_rows[(size_t)g * A.max_rows + pos] = make_int2(s0, len);
-                    }
-                }
-                nrows += __popc(m);
-                J += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            if (nrows > A.max_rows || J > A.jcap) bad = 1;
-        }
-        if (lane == 0) {
-            s_nrows = nrows; s_J = J; s_bad = bad;
-            A.grp_nrows[g] = bad ? 0 : nrows;
-            A.grp_j[g] = bad ? 0 : J;
-            if (bad) { A.ctl[1] = 1; atomicMax(&A.ctl[5], J); atomicMax(&A.ctl[6], nrows); }
-        }
+    if (nrows > VL_ROWS || bad) {                 // the entry code cannot address this brick
+        if (lane == 0) A.ctl[1] = 1;
+        return;
     }
-    __syncthreads();
-    if (s_bad || s_J == 0) return;
-    const int nrows = s_nrows;
+    __syncwarp();
 
-    // stage the neighbourhood: positions and (molecule, LJ) flags
-    for (int r = wid; r < nrows; r += VL_WARPS) {
-        const VLRow row = sR[r];
-        for (int k = lane; k < row.len; k += 32) {
-            sJ[row.base + k] = A.apos[row.s0 + k];
-            sF[row.base + k] = A.aflag[row.s0 + k];
-        }
-    }
-    __syncthreads();
-    if (!brick_ok || n_i == 0) return;
-
-    const T rl2 = A.rl2, rs = A.rl_sel, rs2 = rs * rs;
-    uint16_t *bufC = sB + (wid * 2 + 0) * 32 * 8 + lane * 8;   // 8-entry write buffers per lane
-    uint16_t *bufL = sB + (wid * 2 + 1) * 32 * 8 + lane * 8;
+    const T rl2 = A.rl2;
+    const size_t n = (size_t)A.n;
     for (int base = 0; base < n_i; base += 32) {
         int dummy;
         const int sI = brick_slot(A.start, G, A.bd, bx, by, bz, base + lane, &dummy);
         const bool valid = sI >= 0;
-        const vec4<T> pi = valid ? A.apos[sI] : vec4<T>{(T)1e30, (T)1e30, (T)1e30, 0};
+        const vec4<T> pi = valid ? A.apos[sI] : vec4<T>{(T)1e30, (T)1e30, (T)1e30, (T)0};
         const int fi = valid ? A.aflag[sI] : -2;
-        T lo[3], hi[3];
-        warp_bbox(valid, pi, lo, hi);
-        uint16_t *row_out = A.nbr + (size_t)(valid ? sI : 0) * A.cap;
+        unsigned long long qc = 0ull, ql = 0ull;
         int c = 0, cl = 0;
         bool over = false;
-        for (int r = 0; r < nrows; r++) {
-            const VLRow row = sR[r];
-            // trim the union row to this chunk's box
-            const T dz = max(T(0), max(T(row.z) * h - hi[2], lo[2] - T(row.z + 1) * h));
-            const T dy = max(T(0), max(T(row.y) * h - hi[1], lo[1] - T(row.y + 1) * h));
-            const T d2 = dy * dy + dz * dz;
-            if (d2 >= rs2) continue;
-            const T rx = sqrt(rs2 - d2);
-            const int xlo = max(row.xlo, (int)floor((lo[0] - rx) * inv_h));
-            const int xhi = min(row.xhi, (int)floor((hi[0] + rx) * inv_h));
-            if (xlo > xhi) continue;
-            const int rb = (row.z * G.nc[1] + row.y) * G.nc[0];
-            const int j0 = row.base + (A.start[rb + xlo] - row.s0), j1 = row.base + (A.start[rb + xhi + 1] - row.s0);
-            for (int j = j0; j < j1; j++) {
-                const vec4<T> pj = sJ[j];
-                const int fj = sF[j];
-                const T ddx = pj.x - pi.x, ddy = pj.y - pi.y, ddz = pj.z - pi.z;
-                const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                const bool take = valid && r2 < rl2 && r2 > T(0) && (!A.model || ((fi ^ fj) >> 1) != 0);
-                if (take && !over) {
-                    if (c + cl + 16 > A.cap) {
-                        over = true;
-                    } else {
-                        bufC[c & 7] = (uint16_t)j;
-                        if ((c & 7) == 7) *reinterpret_cast<uint4 *>(row_out + (c & ~7)) = *reinterpret_cast<uint4 *>(bufC);
-                        c++;
-                        if (A.model && (fi & fj & 1)) {
-                            bufL[cl & 7] = (uint16_t)j;
-                            if ((cl & 7) == 7) *reinterpret_cast<uint4 *>(row_out + A.cap - 8 - (cl & ~7)) = *reinterpret_cast<uint4 *>(bufL);
-                            cl++;
-                        }
+        for (int cb = 0; cb < total; cb += 32) {
+            const int cnt = min(32, total - cb);
+            if (lane < cnt) {
+                const int want = cb + lane;
+                int lo_r = 0, hi_r = nrows - 1;
+                while (lo_r < hi_r) {
+                    const int mid = (lo_r + hi_r) >> 1;
+                    if (S.rend[wid][mid] > want) hi_r = mid; else lo_r = mid + 1;
+                }
+                const int off = want - (lo_r ? S.rend[wid][lo_r - 1] : 0);
+                const int js = S.rs0[wid][lo_r] + off;
+                sj[wid][lane] = A.apos[js];
+                sf[wid][lane] = A.aflag[js];
+                ss[wid][lane] = js;
+                sc[wid][lane] = (lo_r << 7) | off;
+            }
+            __syncwarp();
+            for (int k = 0; k < cnt; k++) {
+                const vec4<T> pj = sj[wid][k];
+                const int fj = sf[wid][k];
+                const T dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                bool take = valid && r2 < rl2;
+                if (A.model) take = take && ((unsigned)(fi ^ fj) >= 2u);     // other molecules (and j != i)
+                else take = take && ss[wid][k] != sI;
+                if (take) {
+                    const unsigned long long code = (unsigned long long)sc[wid][k];
+                    if (c < A.cap) {
+                        qc |= code << (16 * (c & 3));
+                        if ((c & 3) == 3) { A.nbr[(size_t)(c >> 2) * n + sI] = qc; qc = 0ull; }
+                    } else over = true;
+                    c++;
+                    if (A.model && (fi & fj & 1)) {
+                        if (cl < A.cap_lj) {
+                            ql |= code << (16 * (cl & 3));
+                            if ((cl & 3) == 3) { A.nbr_lj[(size_t)(cl >> 2) * n + sI] = ql; ql = 0ull; }
+                        } else over = true;
+                        cl++;
                     }
                 }
             }
+            __syncwarp();
         }
-        // flush partial buffers (the unused tail entries are never read: counts bound every read)
-        if (valid && !over) {
-            if (c & 7) *reinterpret_cast<uint4 *>(row_out + (c & ~7)) = *reinterpret_cast<uint4 *>(bufC);
-            if (cl & 7) *reinterpret_cast<uint4 *>(row_out + A.cap - 8 - (cl & ~7)) = *reinterpret_cast<uint4 *>(bufL);
+        if (valid) {
+            if ((c & 3) && c < A.cap) A.nbr[(size_t)(c >> 2) * n + sI] = qc;
+            if ((cl & 3) && cl < A.cap_lj) A.nbr_lj[(size_t)(cl >> 2) * n + sI] = ql;
             A.cnt[sI] = c;
             A.cntlj[sI] = cl;
         }
-        int used = valid ? c + cl + (over ? 1 : 0) : 0;
+        int mc = valid ? c : 0, ml = valid ? cl : 0;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) used = max(used, __shfl_xor_sync(0xffffffffu, used, o));
-        if (lane == 0 && used > 0) atomicMax(&A.ctl[4], used);
-        if (over) A.ctl[1] = 1;
+        for (int o = 16; o; o >>= 1) {
+            mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+            ml = max(ml, __shfl_xor_sync(0xffffffffu, ml, o));
+        }
+        const bool any_over = __any_sync(0xffffffffu, over);
+        if (lane == 0) {
+            atomicMax(&A.ctl[4], mc);
+            atomicMax(&A.ctl[5], ml);
+            if (any_over) A.ctl[1] = 1;
+        }
     }
 }
 
@@ -321,79 +312,51 @@ __global__ void k_list_gather(ListArgs<T> A)
 template <typename T, bool MODEL>
 __global__ void __launch_bounds__(VL_WARPS * 32) k_short_list(ListArgs<T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int rt[VL_WARPS][VL_ROWS];
     if (!vl_usable(A.ctl) || failed(A.status)) return;
-    vec4<T> *sJ = reinterpret_cast<vec4<T> *>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int g = blockIdx.x;
-    const int J = A.grp_j[g];
-    if (J == 0) return;
-    const int nrows = A.grp_nrows[g];
-    const int2 *rows = A.grp_rows + (size_t)g * A.max_rows;
-    // stage the group's neighbourhood from this step's reference-ordered positions
-    {
-        // rows are contiguous in the local index space in row order: recompute bases with a warp scan
-        int base = 0;
-        for (int r0 = 0; r0 < nrows; r0 += 32) {
-            const int r = r0 + lane;
-            const int2 rw = r < nrows ? rows[r] : make_int2(0, 0);
-            int incl = rw.y;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(0xffffffffu, incl, o); if (lane >= o) incl += y; }
-            const int b = base + incl - rw.y;
-            // each warp copies a quarter of the rows of this round
-            for (int k = 0; k < 32; k++) {
-                const int rr = r0 + k;
-                if (rr >= nrows) break;
-                const int bb = __shfl_sync(0xffffffffu, b, k);
-                const int s0 = __shfl_sync(0xffffffffu, rw.x, k), len = __shfl_sync(0xffffffffu, rw.y, k);
-                if ((k & (VL_WARPS - 1)) != wid) continue;
-                for (int t = lane; t < len; t += 32) sJ[bb + t] = A.vl_pos[s0 + t];
-            }
-            base += __shfl_sync(0xffffffffu, incl, 31);
-        }
-    }
-    __syncthreads();
-    const int gx = g % A.ng[0], gyb = (g / A.ng[0]) % A.ng[1], gzb = g / (A.ng[0] * A.ng[1]);
-    const int bx = gx, by = 2 * gyb + (wid & 1), bz = 2 * gzb + (wid >> 1);
-    if (by >= A.nb[1] || bz >= A.nb[2]) return;
+    const int brick = blockIdx.x * VL_WARPS + wid;
+    if (brick >= A.nbricks) return;
+    const int nrows = A.rtn[brick];
+    if (nrows == 0) return;
+    for (int r = lane; r < nrows; r += 32) rt[wid][r] = A.rtab[(size_t)brick * VL_ROWS + r];
+    __syncwarp();
+    const int bx = brick % A.nb[0], by = (brick / A.nb[0]) % A.nb[1], bz = brick / (A.nb[0] * A.nb[1]);
     int n_i = 0;
     brick_slot(A.vl_start, A.g, A.bd, bx, by, bz, 0, &n_i);
     const T a2 = A.a2;
+    const size_t n = (size_t)A.n;
+    const vec4<T> *__restrict__ P = A.vl_pos;
     for (int base = 0; base < n_i; base += 32) {
         int dummy;
         const int sI = brick_slot(A.vl_start, A.g, A.bd, bx, by, bz, base + lane, &dummy);
         const bool valid = sI >= 0;
-        const vec4<T> pi = valid ? A.vl_pos[sI] : vec4<T>{(T)1e30, (T)1e30, (T)1e30, 0};
+        const int self = valid ? sI : 0;
+        const vec4<T> pi = valid ? P[sI] : vec4<T>{(T)1e30, (T)1e30, (T)1e30, (T)0};
         const int cnt = valid ? A.cnt[sI] : 0;
         int maxc = cnt;
 #pragma unroll
         for (int o = 16; o; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
-        const uint16_t *lst = A.nbr + (size_t)(valid ? sI : 0) * A.cap;
         T phi = 0, ax = 0, ay = 0, az = 0;
-        uint4 nxt = make_uint4(0, 0, 0, 0);
-        if (0 < cnt) nxt = __ldcs(reinterpret_cast<const uint4 *>(lst));
-        for (int k8 = 0; k8 < maxc; k8 += 8) {
-            const uint4 v = nxt;
-            if (k8 + 8 < cnt) nxt = __ldcs(reinterpret_cast<const uint4 *>(lst + k8 + 8));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        unsigned long long nxt = cnt > 0 ? A.nbr[self] : 0ull;
+        for (int k4 = 0; k4 < maxc; k4 += 4) {
+            const unsigned long long w = nxt;
+            if (k4 + 4 < cnt) nxt = A.nbr[(size_t)((k4 >> 2) + 1) * n + sI];
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const int j = (w[e >> 1] >> ((e & 1) * 16)) & 0xffff;
-                const bool act = k8 + e < cnt;
-                const vec4<T> pj = sJ[act ? j : 0];
+            for (int e = 0; e < 4; e++) {
+                const int code = (int)((w >> (16 * e)) & 0xffffull);
+                const bool act = k4 + e < cnt;
+                const vec4<T> pj = P[act ? rt[wid][code >> 7] + (code & 127) : self];
                 const T dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                const bool in = act & (r2 < a2);
-                const T r2s = in ? r2 : a2;
-                const T qj = in ? pj.w : T(0);
+                const T r2s = fma(dx, dx, fma(dy, dy, fma(dz, dz, vl_eps<T>())));
+                const T qj = (act && r2s < a2) ? pj.w : T(0);
                 const T ri = vl_rsqrt<T>(r2s);
                 const T ri2 = ri * ri;
                 const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
                 phi = fma(qj, ri - poly, phi);
                 const T fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
-                const T s = qj * fs;
-                ax = fma(s, dx, ax); ay = fma(s, dy, ay); az = fma(s, dz, az);
+                const T sc = qj * fs;
+                ax = fma(sc, dx, ax); ay = fma(sc, dy, ay); az = fma(sc, dz, az);
             }
         }
         T lx = 0, ly = 0, lz = 0, le = 0;
@@ -402,27 +365,25 @@ __global__ void __launch_bounds__(VL_WARPS * 32) k_short_list(ListArgs<T> A)
             int maxl = cl;
 #pragma unroll
             for (int o = 16; o; o >>= 1) maxl = max(maxl, __shfl_xor_sync(0xffffffffu, maxl, o));
-            uint4 nl = make_uint4(0, 0, 0, 0);
-            if (0 < cl) nl = __ldcs(reinterpret_cast<const uint4 *>(lst + A.cap - 8));
-            for (int k8 = 0; k8 < maxl; k8 += 8) {
-                const uint4 v = nl;
-                if (k8 + 8 < cl) nl = __ldcs(reinterpret_cast<const uint4 *>(lst + A.cap - 16 - k8));
-                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+            unsigned long long nl = cl > 0 ? A.nbr_lj[self] : 0ull;
+            for (int k4 = 0; k4 < maxl; k4 += 4) {
+                const unsigned long long w = nl;
+                if (k4 + 4 < cl) nl = A.nbr_lj[(size_t)((k4 >> 2) + 1) * n + sI];
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    // LJ entry k sits at cap - 8 - 8 floor(k/8) + (k mod 8): position e of block k8
-                    const int j = (w[e >> 1] >> ((e & 1) * 16)) & 0xffff;
-                    const bool act = k8 + e < cl;
-                    const vec4<T> pj = sJ[act ? j : 0];
+                for (int e = 0; e < 4; e++) {
+                    const int code = (int)((w >> (16 * e)) & 0xffffull);
+                    const bool act = k4 + e < cl;
+                    const vec4<T> pj = P[act ? rt[wid][code >> 7] + (code & 127) : self];
                     const T dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    const bool in = act & (r2 < a2);
-                    const T ir2 = T(1) / (in ? r2 : a2);
+                    const T r2s = fma(dx, dx, fma(dy, dy, fma(dz, dz, vl_eps<T>())));
+                    const bool on = act && r2s < a2;
+                    const T ri = vl_rsqrt<T>(r2s);
+                    const T ir2 = on ? ri * ri : T(0);
                     const T sr2 = A.lj_s2 * ir2;
                     const T sr6 = sr2 * sr2 * sr2;
-                    const T m = in ? T(1) : T(0);
+                    const T m = on ? T(1) : T(0);
                     le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
-                    const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ir2;
+                    const T fl = A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ir2;
                     lx = fma(-fl, dx, lx); ly = fma(-fl, dy, ly); lz = fma(-fl, dz, lz);
                 }
             }
@@ -437,13 +398,6 @@ __global__ void __launch_bounds__(VL_WARPS * 32) k_short_list(ListArgs<T> A)
 
 // ---------------------------------------------------------------- launches
 
-template <typename T> size_t list_build_smem(const ListArgs<T> &a)
-{
-    return (size_t)a.jcap * (sizeof(vec4<T>) + sizeof(int)) + (size_t)a.max_rows * sizeof(VLRow) +
-           (size_t)VL_WARPS * 2 * 32 * 8 * sizeof(uint16_t);
-}
-template <typename T> size_t list_force_smem(const ListArgs<T> &a) { return (size_t)a.jcap * sizeof(vec4<T>); }
-
 template <typename T>
 int launch_list_maintain(const ListArgs<T> &a, cudaStream_t st)
 {
@@ -452,11 +406,9 @@ int launch_list_maintain(const ListArgs<T> &a, cudaStream_t st)
     if (n > 0) k_list_disp<T><<<(n + 255) / 256, 256, 0, st>>>(a);
     const int m = std::max(n, a.g.ncells + 1);
     k_list_snapshot<T><<<(m + 255) / 256, 256, 0, st>>>(a);
-    const size_t sb = list_build_smem(a);
-    CUDA_TRY(cudaFuncSetAttribute(k_list_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-    k_list_build<T><<<a.ngroups, VL_WARPS * 32, sb, st>>>(a);
+    if (a.nbricks > 0) k_list_build<T><<<(a.nbricks + VL_WARPS - 1) / VL_WARPS, VL_WARPS * 32, 0, st>>>(a);
     k_list_gather<T><<<(n + 255) / 256 + 1, 256, 0, st>>>(a);
-    count_launch(n > 0 ? 4 : 3);
+    count_launch((n > 0 ? 3 : 2) + (a.nbricks > 0 ? 1 : 0));
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
 }
@@ -464,14 +416,10 @@ int launch_list_maintain(const ListArgs<T> &a, cudaStream_t st)
 template <typename T>
 int launch_list_force(const ListArgs<T> &a, cudaStream_t st)
 {
-    const size_t sf = list_force_smem(a);
-    if (a.model) {
-        CUDA_TRY(cudaFuncSetAttribute(k_short_list<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-        k_short_list<T, true><<<a.ngroups, VL_WARPS * 32, sf, st>>>(a);
-    } else {
-        CUDA_TRY(cudaFuncSetAttribute(k_short_list<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-        k_short_list<T, false><<<a.ngroups, VL_WARPS * 32, sf, st>>>(a);
-    }
+    const int grid = (a.nbricks + VL_WARPS - 1) / VL_WARPS;
+    if (grid <= 0) return MSM_OK;
+    if (a.model) k_short_list<T, true><<<grid, VL_WARPS * 32, 0, st>>>(a);
+    else k_short_list<T, false><<<grid, VL_WARPS * 32, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -481,7 +429,5 @@ template int launch_list_maintain<float>(const ListArgs<float> &, cudaStream_t);
 template int launch_list_maintain<double>(const ListArgs<double> &, cudaStream_t);
 template int launch_list_force<float>(const ListArgs<float> &, cudaStream_t);
 template int launch_list_force<double>(const ListArgs<double> &, cudaStream_t);
-template size_t list_build_smem<float>(const ListArgs<float> &);
-template size_t list_build_smem<double>(const ListArgs<double> &);
 
 }  // namespace msm

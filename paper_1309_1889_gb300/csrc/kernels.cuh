@@ -69,12 +69,13 @@ template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t
 // for cutoff a_sel and cell edge h.
 bool short_rows_fit(const int bd[3], double a_sel, double h);
 
-// ---- Verlet lists (k_list.cu) --------------------------------------------
+// ---- Verlet lists (k_list.cu, single systems) -----------------------------
+constexpr int VL_ROWS = 512;       // candidate rows per brick (9 bits of an entry)
+constexpr int VL_OFFS = 128;       // atoms per row segment (7 bits of an entry)
 template <typename T> struct ListArgs {
     CellGeom g;
-    int bd[3], nb[3];      // bricks of the short-range kernel
-    int ng[3], ngroups;    // groups of 1 x 2 x 2 bricks
-    int max_rows, jcap, cap;   // row slots per group, staged atoms per group, list entries per atom
+    int bd[3], nb[3], nbricks; // bricks of the short-range kernel (frozen with the list)
+    int cap, cap_lj;       // entries per atom (multiples of 4): all partners, O-O partners
     T a2, rl2, rl_sel, skin_half2;
     T c0, c1, c2, d0, d1;
     T lj_s2, lj_4eps, lj_24eps, lj_shift;
@@ -86,11 +87,11 @@ template <typename T> struct ListArgs {
     const int *aflag;
     int *vl_perm, *vl_start;   // reference order of the last build
     double *vl_xref;
-    vec4<T> *vl_pos;
-    int2 *grp_rows;
-    int *grp_nrows, *grp_j;
-    int *cnt, *cntlj;
-    uint16_t *nbr;         // n x cap
+    vec4<T> *vl_pos;       // this step's positions in reference order
+    int *rtab;             // nbricks x VL_ROWS: first reference slot of each candidate row
+    int *rtn;              // nbricks: candidate rows of each brick
+    int *cnt, *cntlj;      // entries per reference slot
+    unsigned long long *nbr, *nbr_lj;   // entry quads: quad q of slot s at [q * n + s]
     int *ctl;
     vec4<T> *sr, *lj;      // outputs by atom
     const int *status;

@@ -186,8 +186,8 @@ struct msm_handle {
     long long g_kernels = 0;                            // kernels per replayed step
     // Verlet lists (md_run with list_skin > 0, single systems)
     bool list_on = false;
-    DevBuf vl_perm, vl_start, vl_xref, vl_pos, grp_rows, grp_nrows, grp_j, vl_cnt, vl_cntlj, vl_nbr, vl_ctl;
-    int vl_cap = 0, vl_jcap = 0, vl_rows = 0, vl_ngroups = 0;
+    DevBuf vl_perm, vl_start, vl_xref, vl_pos, vl_rtab, vl_rtn, vl_cnt, vl_cntlj, vl_nbr, vl_nbr_lj, vl_ctl;
+    int vl_cap = 0, vl_cap_lj = 0, vl_nbricks = 0;
     int64_t vl_key_n = -1, vl_key_nmol = -1;
     double vl_key_box[6] = {0, 0, 0, 0, 0, 0};
     const void *vl_key_lj = nullptr;
@@ -315,8 +315,8 @@ extern "C" void msm_destroy(msm_handle *h)
                      &h->kin_s, &h->status, &h->ctr, &h->sd_buf, &h->blk_buf,
                      &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
                      &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk, &h->md_im,
-                     &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->grp_rows, &h->grp_nrows,
-                     &h->grp_j, &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_ctl};
+                     &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->vl_rtab, &h->vl_rtn,
+                     &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_nbr_lj, &h->vl_ctl};
     for (DevBuf *b : all) release(*b);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -699,6 +699,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
 
     // step 1: short range
     ShortArgs<T> s = short_args<T>(h);
+    // the lists address the bricks they were built for: never use them on another brick set
+    if (h->list_on && h->nbricks != h->vl_nbricks) h->list_on = false;
     s.vl_ctl = h->list_on ? h->vl_ctl.as<int>() : nullptr;
     {
         ListArgs<T> la;
@@ -706,9 +708,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             const double a = h->p.a;
             la.g = h->cg;
             for (int d = 0; d < 3; d++) { la.bd[d] = h->bd[d]; la.nb[d] = h->nb[d]; }
-            la.ng[0] = h->nb[0]; la.ng[1] = (h->nb[1] + 1) / 2; la.ng[2] = (h->nb[2] + 1) / 2;
-            la.ngroups = h->vl_ngroups;
-            la.max_rows = h->vl_rows; la.jcap = h->vl_jcap; la.cap = h->vl_cap;
+            la.nbricks = h->nbricks;
+            la.cap = h->vl_cap; la.cap_lj = h->vl_cap_lj;
             const double rl = a + h->p.list_skin;
             la.a2 = s.a2; la.rl2 = (T)(rl * rl); la.rl_sel = (T)(rl + 1e-3 * h->p.h);
             la.skin_half2 = (T)(0.25 * h->p.list_skin * h->p.list_skin);
@@ -718,9 +719,9 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             la.perm = h->perm.as<int>(); la.start = h->start.as<int>(); la.apos = h->apos.as<vec4<T>>();
             la.aflag = h->aflag.as<int>();
             la.vl_perm = h->vl_perm.as<int>(); la.vl_start = h->vl_start.as<int>(); la.vl_xref = h->vl_xref.as<double>();
-            la.vl_pos = h->vl_pos.as<vec4<T>>(); la.grp_rows = h->grp_rows.as<int2>();
-            la.grp_nrows = h->grp_nrows.as<int>(); la.grp_j = h->grp_j.as<int>();
-            la.cnt = h->vl_cnt.as<int>(); la.cntlj = h->vl_cntlj.as<int>(); la.nbr = h->vl_nbr.as<uint16_t>();
+            la.vl_pos = h->vl_pos.as<vec4<T>>(); la.rtab = h->vl_rtab.as<int>(); la.rtn = h->vl_rtn.as<int>();
+            la.cnt = h->vl_cnt.as<int>(); la.cntlj = h->vl_cntlj.as<int>();
+            la.nbr = h->vl_nbr.as<unsigned long long>(); la.nbr_lj = h->vl_nbr_lj.as<unsigned long long>();
             la.ctl = h->vl_ctl.as<int>(); la.sr = s.sr; la.lj = s.lj; la.status = status;
             PROF(ST_LIST);
             TRY(launch_list_maintain<T>(la, st));
@@ -934,13 +935,22 @@ static int list_alloc(msm_handle *h, int64_t n, size_t vsz)
     TRY(ensure(h->vl_start, sizeof(int) * ((size_t)h->cg.ncells + 1)));
     TRY(ensure(h->vl_xref, sizeof(double) * 3 * nn));
     TRY(ensure(h->vl_pos, vsz * nn));
-    TRY(ensure(h->grp_rows, sizeof(int2) * (size_t)h->vl_ngroups * h->vl_rows));
-    TRY(ensure(h->grp_nrows, sizeof(int) * (size_t)h->vl_ngroups));
-    TRY(ensure(h->grp_j, sizeof(int) * (size_t)h->vl_ngroups));
+    TRY(ensure(h->vl_rtab, sizeof(int) * (size_t)VL_ROWS * (size_t)(h->vl_nbricks > 0 ? h->vl_nbricks : 1)));
+    TRY(ensure(h->vl_rtn, sizeof(int) * (size_t)(h->vl_nbricks > 0 ? h->vl_nbricks : 1)));
     TRY(ensure(h->vl_cnt, sizeof(int) * nn));
     TRY(ensure(h->vl_cntlj, sizeof(int) * nn));
     TRY(ensure(h->vl_nbr, sizeof(uint16_t) * nn * (size_t)h->vl_cap));
+    TRY(ensure(h->vl_nbr_lj, sizeof(uint16_t) * nn * (size_t)(h->vl_cap_lj > 0 ? h->vl_cap_lj : 4)));
     TRY(ensure(h->vl_ctl, sizeof(int) * 8));
+    return MSM_OK;
+}
+
+static int list_invalidate(msm_handle *h, cudaStream_t st)
+{
+    CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
+    const int invalid = 1;
+    CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));                    // 'invalid' lives on the host stack
     return MSM_OK;
 }
 
@@ -952,50 +962,39 @@ static int list_setup(msm_handle *h, const RunSys &s, bool fresh, cudaStream_t s
 {
     TRY(set_batch(h, 1, s.sys, st));
     const SysIn &S = s.sys[0];
-    const double rl = h->p.a + h->p.list_skin, hh = h->p.h;
-    const int R = (int)ceil((rl + 1e-3 * hh) / hh) + 1;
-    const int rows = (2 * h->bd[1] + 2 * R + 1) * (2 * h->bd[2] + 2 * R + 1);
-    const int ngroups = h->nb[0] * ((h->nb[1] + 1) / 2) * ((h->nb[2] + 1) / 2);
+    const double rl = h->p.a + h->p.list_skin;
     const bool changed = S.n != h->vl_key_n || S.n_mol != h->vl_key_nmol || s.lj != h->vl_key_lj ||
-                         memcmp(S.box, h->vl_key_box, sizeof h->vl_key_box) != 0 || rows > h->vl_rows ||
-                         ngroups != h->vl_ngroups;
+                         memcmp(S.box, h->vl_key_box, sizeof h->vl_key_box) != 0 || h->nbricks != h->vl_nbricks;
     if (!changed && !fresh && h->vl_ctl.p) return MSM_OK;
     if (h->vl_cap == 0) {
-        // entries per atom: pairs within a + skin at 1.8x the box's mean density, at least 256
+        // entries per atom: pairs within a + skin at 1.3x the box's mean density
         const double vol = S.box[3] * S.box[4] * S.box[5];
         const double dens = (double)S.n / vol;
-        const double want = 1.8 * dens * 4.18879020478639 * rl * rl * rl + 32.0;
-        h->vl_cap = ((std::max(256, (int)want) + 7) / 8) * 8;
-        h->vl_jcap = 4608;
+        const double want = 1.3 * dens * 4.18879020478639 * rl * rl * rl + 32.0;
+        h->vl_cap = ((std::max(64, (int)want) + 3) / 4) * 4;
+        h->vl_cap_lj = h->p.model == MSM_MODEL_WATER ? ((h->vl_cap / 2 + 3) / 4) * 4 : 4;
     }
-    h->vl_rows = std::max(h->vl_rows, rows);
-    h->vl_ngroups = ngroups;
+    h->vl_nbricks = h->nbricks;
     TRY(list_alloc(h, S.n, sizeof(vec4<T>)));
-    CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
-    const int invalid = 1;
-    CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));                    // 'invalid' lives on the host stack
+    TRY(list_invalidate(h, st));
     h->vl_key_n = S.n; h->vl_key_nmol = S.n_mol; h->vl_key_lj = s.lj;
     memcpy(h->vl_key_box, S.box, sizeof h->vl_key_box);
     return MSM_OK;
 }
 
-// After an overflow: grow the exceeded capacity, invalidate, resume with lists next time.
+// After an overflow: grow the exceeded capacity, invalidate, resume with lists
+// next time; a brick the 16-bit entries cannot address (more than VL_ROWS rows
+// or a row of VL_OFFS atoms or more) turns the lists off for this handle.
 static int list_grow(msm_handle *h, cudaStream_t st)
 {
     const int *c = h->h_ctl;
     const size_t vsz = h->precision == MSM_FP32 ? sizeof(vec4<float>) : sizeof(vec4<double>);
-    const int max_jcap = h->precision == MSM_FP32 ? 10240 : 5120;   // shared memory of one CTA
-    if (c[4] + 16 > h->vl_cap) h->vl_cap = (((int)(1.25 * c[4]) + 32 + 7) / 8) * 8;
-    if (c[5] > h->vl_jcap) h->vl_jcap = std::min(max_jcap, (((int)(1.2 * c[5]) + 64) + 7) / 8 * 8);
-    if (c[6] > h->vl_rows) h->vl_rows = c[6] + 16;
-    if (c[5] > max_jcap) h->p.list_skin = 0.0;              // too dense for staged lists: cell search only
+    bool grew = false;
+    if (c[4] > h->vl_cap) { h->vl_cap = (((int)(1.2 * c[4]) + 16 + 3) / 4) * 4; grew = true; }
+    if (c[5] > h->vl_cap_lj) { h->vl_cap_lj = (((int)(1.2 * c[5]) + 16 + 3) / 4) * 4; grew = true; }
+    if (!grew) h->p.list_skin = 0.0;                        // not a capacity: cell search from now on
     TRY(list_alloc(h, h->vl_key_n, vsz));
-    CUDA_TRY(cudaMemsetAsync(h->vl_ctl.p, 0, sizeof(int) * 8, st));
-    const int invalid = 1;
-    CUDA_TRY(cudaMemcpyAsync(h->vl_ctl.as<int>() + 2, &invalid, sizeof(int), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    return MSM_OK;
+    return list_invalidate(h, st);
 }
 
 template <typename T> static double shake_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-12; }
@@ -1072,7 +1071,6 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
     TRY(ensure(h->md_im, sizeof(double) * nn));
     if (!s.f) TRY(ensure(h->md_f, sizeof(double) * 3 * nn));
     h->list_on = false;
-    if (h->p.list_skin > 0 && s.B == 1 && n > 0) TRY(list_setup<T>(h, s, !(s.f && s.f_valid), st));
     TRY(set_batch(h, s.B, s.sys, st));
     EvalIO io;
     io.pos = s.x; io.q = s.q; io.lj = s.lj;
@@ -1086,15 +1084,18 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
     va.d_oh2 = h->p.d_oh * h->p.d_oh; va.d_hh2 = h->p.d_hh * h->p.d_hh;
     va.tol = shake_tol<T>(); va.tol_v = rattle_tol<T>(); va.max_iter = sizeof(T) == 4 ? 200 : 1000;
     va.status = h->status.as<int>();
-    if (s.f && s.f_valid) {
+    if (s.f && s.f_valid && !h->tune_pending) {
         // forces and energies of the start positions come with the systems
         CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int) * 4, st));
         for (int b = 0; b < s.B; b++) h->h_e[b] = s.e0[b];
         CUDA_TRY(cudaMemcpy2DAsync(h->sums.p, 4 * sizeof(double), h->h_e, sizeof(double), sizeof(double),
                                    (size_t)s.B, cudaMemcpyHostToDevice, st));
     } else {
+        // (also when the autotuner still has to run: it settles the bricks before
+        // the lists are sized for them; the forces it recomputes are bitwise the same)
         TRY(evaluate(h, io, s.B, s.sys, st));
     }
+    if (h->p.list_skin > 0 && s.B == 1 && n > 0) TRY(list_setup<T>(h, s, !(s.f && s.f_valid), st));
     if (uk) {
         CUDA_TRY(cudaMemsetAsync(h->ctr.p, 0, sizeof(int), st));
         TRY(record_uk(h, s, uk, uk_stride, st));
@@ -1614,7 +1615,7 @@ extern "C" int msm_stage_atoms(msm_handle *h, int32_t which, double *out, int64_
 extern "C" int msm_list_stats(msm_handle *h, int64_t *out, int32_t max)
 {
     if (!h || !out) return fail_msg(MSM_EINVAL, "NULL argument");
-    const int64_t v[8] = {h->vl_builds, h->vl_overflows, h->vl_cap, h->vl_jcap, h->vl_rows,
+    const int64_t v[8] = {h->vl_builds, h->vl_overflows, h->vl_cap, h->vl_cap_lj, VL_ROWS,
                           h->vl_seen[0], h->vl_seen[1], h->vl_seen[2]};
     for (int k = 0; k < 8 && k < max; k++) out[k] = v[k];
     return MSM_OK;
