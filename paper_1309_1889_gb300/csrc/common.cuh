@@ -61,6 +61,7 @@ struct SysDesc {
     int n_mol;          // leading rigid (O, H, H) triples of the system
     int cell_off;       // global id of its first cell (cell_start index)
     int bd[3], nb[3], nbricks;   // short-range bricks: edge in cells, count per axis
+    int lj_bd[3], lj_nb[3], lj_nbricks;   // bricks of the LJ-site pass (water completion)
     int grid_off;       // first point of its grids in the concatenated grid buffers
     int top_off;        // first point of its top level in the FP64 top buffer
     int ttab_off;       // first entry of its top-level Toeplitz table

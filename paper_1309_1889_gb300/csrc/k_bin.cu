@@ -170,6 +170,19 @@ __global__ void k_gather(const Batch bt, const int *__restrict__ perm, const int
 
 int scan_scratch_ints() { return SCAN_B + 1; }
 
+// start[0..m] = exclusive prefix sums of count[0..m-1] (start[m] = total).
+int launch_scan(int m, const int *count, int *start, int *bsum, const int *status, cudaStream_t st)
+{
+    const int nb = (m + SCAN_B - 1) / SCAN_B;
+    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
+    k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, count, start, bsum, status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + SCAN_B, status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + SCAN_B, status);
+    count_launch(3);
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
 // Scan, scatter and per-cell sort of precomputed keys whose histogram is
 // already in count[0..m-1]: the second half of launch_bin, for callers that
 // compute the keys themselves.

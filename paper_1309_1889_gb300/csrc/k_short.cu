@@ -71,22 +71,27 @@ template <typename T> struct ShortSmem {
 };
 
 // MODEL: rigid-water completion -- pairs inside one molecule are skipped (the
-// exclusion kernel removes their smooth part), LJ between flagged sites.
+// exclusion kernel removes their smooth part); atoms that are not LJ sites get
+// a zero LJ output.
 // COUNT: diagnostics only -- count the pairs inside the cutoff instead of summing.
-template <typename T, bool MODEL, bool COUNT>
+// LJP: the O-O Lennard-Jones pass of the water completion, over the LJ-site
+// cell list (i and j both LJ sites, other molecules, r < a): the same terms, in
+// the same ascending slot order, as summing them inside the Coulomb loop.
+template <typename T, bool MODEL, bool COUNT, bool LJP>
 __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const SysDesc &D = A.bt.sd[blockIdx.y];
+    const int *BD = LJP ? D.lj_bd : D.bd, *NB = LJP ? D.lj_nb : D.nb;
     const int brick = blockIdx.x * SR_WARPS + wid;
-    if (brick >= D.nbricks || failed(A.status)) return;
+    if (brick >= (LJP ? D.lj_nbricks : D.nbricks) || failed(A.status)) return;
     if (A.vl_ctl && A.vl_ctl[1] == 0 && A.vl_ctl[2] == 0) return;     // the Verlet-list path ran
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
-    const int bx = brick % D.nb[0], by = (brick / D.nb[0]) % D.nb[1], bz = brick / (D.nb[0] * D.nb[1]);
-    const int cx0 = bx * D.bd[0], cx1 = min(cx0 + D.bd[0], nx);
-    const int cy0 = by * D.bd[1], cy1 = min(cy0 + D.bd[1], ny);
-    const int cz0 = bz * D.bd[2], cz1 = min(cz0 + D.bd[2], nz);
+    const int bx = brick % NB[0], by = (brick / NB[0]) % NB[1], bz = brick / (NB[0] * NB[1]);
+    const int cx0 = bx * BD[0], cx1 = min(cx0 + BD[0], nx);
+    const int cy0 = by * BD[1], cy1 = min(cy0 + BD[1], ny);
+    const int cz0 = bz * BD[2], cz1 = min(cz0 + BD[2], nz);
     const int *__restrict__ start = A.start + D.cell_off;
     const unsigned lt = (1u << lane) - 1u;
 
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         }
         const bool valid = slot >= 0;
         const vec4<T> pi = valid ? A.apos[slot] : vec4<T>{big_t<T>(), big_t<T>(), big_t<T>(), T(0)};
-        const int fi = (MODEL && valid) ? A.aflag[slot] : -2;
+        const int fi = ((MODEL || LJP) && valid) ? A.aflag[slot] : -2;
 
         // ---- bounding box of the valid i atoms
         T lo[3], hi[3];
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                     }
                     const int js = S.rs0[wid][lo_r] + (want - (lo_r ? S.rend[wid][lo_r - 1] : 0));
                     S.sj[wid][lane] = A.apos[js];
-                    if (MODEL) S.sf[wid][lane] = A.aflag[js];
+                    if (MODEL || LJP) S.sf[wid][lane] = A.aflag[js];
                 }
                 __syncwarp();
 #pragma unroll 4
@@ -193,31 +198,28 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                     const T dx = pj.x - pi.x, dyy = pj.y - pi.y, dzz = pj.z - pi.z;
                     const T r2s = fma(dx, dx, fma(dyy, dyy, fma(dzz, dzz, r2_eps<T>())));
                     bool in = r2s < A.a2;
-                    int fj = 0;
                     // j = i: the water model's molecule test excludes it (an atom is in its own
                     // molecule); bare charges test the distance
-                    if (MODEL) { fj = S.sf[wid][k]; in = in & ((unsigned)(fi ^ fj) >= 2u); }
+                    if (MODEL || LJP) in = in & ((unsigned)(fi ^ S.sf[wid][k]) >= 2u);
                     else in = in & (r2s > T(2) * r2_eps<T>());
                     if (COUNT) { npair += in ? 1 : 0; continue; }
-                    const T qj = in ? pj.w : T(0);
                     const T ri = rsqrt_t<T>(r2s);
                     const T ri2 = ri * ri;
+                    if (LJP) {
+                        const T m = in ? T(1) : T(0);
+                        const T sr2 = A.lj_s2 * (in ? ri2 : T(0));   // masked pairs (j = i: r^2 = eps) stay finite
+                        const T sr6 = sr2 * sr2 * sr2;
+                        le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
+                        const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
+                        lx = fma(-fl, dx, lx); ly = fma(-fl, dyy, ly); lz = fma(-fl, dzz, lz);
+                        continue;
+                    }
+                    const T qj = in ? pj.w : T(0);
                     const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
                     phi = fma(qj, ri - poly, phi);
                     const T fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
                     const T sc = qj * fs;
                     ax = fma(sc, dx, ax); ay = fma(sc, dyy, ay); az = fma(sc, dzz, az);
-                    if (MODEL) {
-                        if (fj & 1) {                           // uniform: j is broadcast
-                            const bool on = (fi & 1) && in;
-                            const T m = on ? T(1) : T(0);
-                            const T sr2 = A.lj_s2 * (on ? ri2 : T(0));  // masked pairs (j = i: r^2 = eps) stay finite
-                            const T sr6 = sr2 * sr2 * sr2;
-                            le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
-                            const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
-                            lx = fma(-fl, dx, lx); ly = fma(-fl, dyy, ly); lz = fma(-fl, dzz, lz);
-                        }
-                    }
                 }
                 __syncwarp();
             }
@@ -225,8 +227,9 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         if (valid) {
             if (COUNT) { A.cnt[slot] = (double)npair; continue; }
             const int atom = A.perm[slot];
+            if (LJP) { A.lj[atom] = vec4<T>{lx, ly, lz, le}; continue; }
             A.sr[atom] = vec4<T>{-pi.w * ax, -pi.w * ay, -pi.w * az, phi};
-            if (MODEL) A.lj[atom] = vec4<T>{lx, ly, lz, le};
+            if (MODEL && !(fi & 1)) A.lj[atom] = vec4<T>{T(0), T(0), T(0), T(0)};
         }
     }
 }
@@ -243,8 +246,19 @@ int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    if (model) k_short<T, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
-    else k_short<T, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    if (model) k_short<T, true, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    else k_short<T, false, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+template <typename T>
+int launch_short_lj(const ShortArgs<T> &a, cudaStream_t st)
+{
+    if (a.max_bricks <= 0) return MSM_OK;
+    const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
+    k_short<T, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -255,7 +269,62 @@ int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    k_short<T, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    k_short<T, false, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// ------------------------------------------------------ LJ-site cell list
+
+__global__ void k_lj_count(int m, const int *__restrict__ start, const int *__restrict__ aflag,
+                           int *__restrict__ lj_count, const int *__restrict__ status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m || failed(status)) return;
+    int k = 0;
+    for (int s = start[c]; s < start[c + 1]; s++) k += aflag[s] & 1;
+    lj_count[c] = k;
+}
+
+template <typename T>
+__global__ void k_lj_compact(int m, const int *__restrict__ start, const int *__restrict__ lj_start,
+                             const vec4<T> *__restrict__ apos, const int *__restrict__ aflag,
+                             const int *__restrict__ perm, vec4<T> *__restrict__ lj_apos, int *__restrict__ lj_flag,
+                             int *__restrict__ lj_perm, const int *__restrict__ status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m || failed(status)) return;
+    int k = lj_start[c];
+    for (int s = start[c]; s < start[c + 1]; s++) {
+        const int f = aflag[s];
+        if (!(f & 1)) continue;
+        lj_apos[k] = apos[s];
+        lj_flag[k] = f;
+        lj_perm[k] = perm[s];
+        k++;
+    }
+}
+
+template <typename T>
+int launch_lj_count(int m_total, const int *start, const int *aflag, int *lj_count, const int *status,
+                    cudaStream_t st)
+{
+    if (m_total <= 0) return MSM_OK;
+    k_lj_count<<<(m_total + 255) / 256, 256, 0, st>>>(m_total, start, aflag, lj_count, status);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+template <typename T>
+int launch_lj_compact(int m_total, const int *start, const int *lj_start, const vec4<T> *apos, const int *aflag,
+                      const int *perm, vec4<T> *lj_apos, int *lj_flag, int *lj_perm, const int *status,
+                      cudaStream_t st)
+{
+    if (m_total <= 0) return MSM_OK;
+    k_lj_compact<T><<<(m_total + 255) / 256, 256, 0, st>>>(m_total, start, lj_start, apos, aflag, perm, lj_apos,
+                                                           lj_flag, lj_perm, status);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -265,5 +334,13 @@ template int launch_short<float>(const ShortArgs<float> &, bool, cudaStream_t);
 template int launch_short<double>(const ShortArgs<double> &, bool, cudaStream_t);
 template int launch_count_pairs<float>(const ShortArgs<float> &, cudaStream_t);
 template int launch_count_pairs<double>(const ShortArgs<double> &, cudaStream_t);
+template int launch_short_lj<float>(const ShortArgs<float> &, cudaStream_t);
+template int launch_short_lj<double>(const ShortArgs<double> &, cudaStream_t);
+template int launch_lj_count<float>(int, const int *, const int *, int *, const int *, cudaStream_t);
+template int launch_lj_count<double>(int, const int *, const int *, int *, const int *, cudaStream_t);
+template int launch_lj_compact<float>(int, const int *, const int *, const vec4<float> *, const int *, const int *,
+                                      vec4<float> *, int *, int *, const int *, cudaStream_t);
+template int launch_lj_compact<double>(int, const int *, const int *, const vec4<double> *, const int *, const int *,
+                                       vec4<double> *, int *, int *, const int *, cudaStream_t);
 
 }  // namespace msm

@@ -40,13 +40,14 @@ template <typename T> struct BinArgs {
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
 int scan_scratch_ints();
+int launch_scan(int m, const int *count, int *start, int *bsum, const int *status, cudaStream_t st);
 int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int *perm, int *bsum, int *status,
                        cudaStream_t st);
 
 // ---- short range (k_short.cu) ----------------------------------------------
 template <typename T> struct ShortArgs {
     Batch bt;
-    int max_bricks;        // bricks of the largest system
+    int max_bricks;        // bricks of the largest system (of its LJ pass for launch_short_lj)
     const int *start;      // global cell_start
     const vec4<T> *apos;
     const int *aflag;
@@ -62,8 +63,20 @@ template <typename T> struct ShortArgs {
     const int *status;
 };
 // model = true: skip pairs of the same molecule (their smooth part is removed by
-// the exclusion kernel) and add the LJ term between flagged sites.
+// the exclusion kernel) and write a zero LJ output for atoms that are not LJ
+// sites; the LJ term itself is the separate pass below.
 template <typename T> int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st);
+// O-O Lennard-Jones of the water completion over the LJ sites only: a the
+// ShortArgs of the LJ-site cell list (start, apos, aflag, perm of the subset),
+// bricks from SysDesc::lj_*; writes lj[atom] of every LJ site.
+template <typename T> int launch_short_lj(const ShortArgs<T> &a, cudaStream_t st);
+// The LJ-site cell list: per global cell the LJ sites among its sorted slots,
+// compacted in slot order (count -> lj_start by launch_scan -> copies).
+template <typename T> int launch_lj_count(int m_total, const int *start, const int *aflag, int *lj_count,
+                                          const int *status, cudaStream_t st);
+template <typename T> int launch_lj_compact(int m_total, const int *start, const int *lj_start, const vec4<T> *apos,
+                                            const int *aflag, const int *perm, vec4<T> *lj_apos, int *lj_flag,
+                                            int *lj_perm, const int *status, cudaStream_t st);
 template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st);
 // Largest brick (cells per axis) whose candidate rows fit the kernel's row list
 // for cutoff a_sel and cell edge h.

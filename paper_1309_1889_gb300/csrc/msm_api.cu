@@ -104,11 +104,12 @@ static bool on_device(const void *p)
 
 // Stages timed by the profiler (CUDA events around each stage's launches).
 enum Stage { ST_BIN, ST_SHORT, ST_ANTERP, ST_RESTRICT, ST_STENCIL, ST_TOP, ST_PROLONG, ST_INTERP, ST_SUMS,
-             ST_VV1, ST_VV2, ST_LIST, N_STAGES };
+             ST_VV1, ST_VV2, ST_LIST, ST_LJ, N_STAGES };
 static const char *kStageNames[N_STAGES] = {"bin_sort",      "short_range", "anterpolation",
                                             "restriction",   "lattice_cutoff", "top_level",
                                             "prolongation",  "interpolation", "exclusions_sums",
-                                            "vv_first_shake", "vv_second_rattle", "verlet_list_maintenance"};
+                                            "vv_first_shake", "vv_second_rattle", "verlet_list_maintenance",
+                                            "lennard_jones"};
 
 struct Profiler {
     bool on = false;
@@ -153,7 +154,7 @@ struct msm_handle {
     std::vector<int> h_blk;
     long long geom_gen = 0;
     int N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, stiles = 0;
-    int max_n = 0, max_mol = 0, max_units = 0, max_bricks = 0, max_atiles = 0, max_top = 0;
+    int max_n = 0, max_mol = 0, max_units = 0, max_bricks = 0, max_atiles = 0, max_top = 0, max_lj_bricks = 0;
     int max_lev[MSM_MAX_LEVELS] = {0};
     DevBuf sd_buf, blk_buf;
     // system 0 of the batch (inspection and Verlet lists)
@@ -171,6 +172,7 @@ struct msm_handle {
     StencilGeom sg;
     // scratch
     DevBuf key, count, start, perm, bsum, rel, frac, apos, afrac, akey, aflag, sr, lj;
+    DevBuf lj_count, lj_start, lj_apos, lj_flag, lj_perm;      // LJ-site cell list (water completion)
     DevBuf qgrid, ucut, ugrid, utop, ttop, wst_d, wst_t, rows;
     DevBuf eatom, vatom, kin, partials, sums, kin_s, status, ctr;
     DevBuf in_pos, in_q, in_lj, out_f, out_p;          // staging of host arrays
@@ -310,7 +312,8 @@ extern "C" void msm_destroy(msm_handle *h)
 {
     if (!h) return;
     DevBuf *all[] = {&h->key, &h->count, &h->start, &h->perm, &h->bsum, &h->rel, &h->frac, &h->apos, &h->afrac,
-                     &h->akey, &h->aflag, &h->sr, &h->lj, &h->qgrid, &h->ucut, &h->ugrid, &h->utop, &h->ttop,
+                     &h->akey, &h->aflag, &h->sr, &h->lj, &h->lj_count, &h->lj_start, &h->lj_apos, &h->lj_flag,
+                     &h->lj_perm, &h->qgrid, &h->ucut, &h->ugrid, &h->utop, &h->ttop,
                      &h->wst_d, &h->wst_t, &h->rows, &h->eatom, &h->vatom, &h->kin, &h->partials, &h->sums,
                      &h->kin_s, &h->status, &h->ctr, &h->sd_buf, &h->blk_buf,
                      &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
@@ -351,9 +354,9 @@ static int ensure_host_e(msm_handle *h, int B)
 // system's mean density (one i atom per lane), unless the autotuner timed
 // this geometry.  The shape changes only the speed, never the results: each
 // i atom sums its j's in ascending slot order whatever the brick.
-static const int kNumShapes = 11;
+static const int kNumShapes = 12;
 static const int kBrickShapes[kNumShapes][3] = {{1, 1, 1}, {2, 1, 1}, {2, 2, 1}, {2, 2, 2}, {3, 2, 2}, {4, 2, 2},
-                                                {3, 3, 2}, {5, 2, 2}, {4, 3, 2}, {4, 4, 2}, {4, 4, 4}};
+                                                {3, 3, 2}, {5, 2, 2}, {4, 3, 2}, {4, 4, 2}, {4, 4, 3}, {4, 4, 4}};
 
 // The largest shape (by volume) that holds at most ~28 atoms at the mean density.
 static int brick_heuristic(int64_t n, const CellGeom &g)
@@ -464,6 +467,15 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             set_bricks(D, kBrickShapes[brick_heuristic(S.n, D.g)]);
             if ((h->p.flags & MSM_FLAG_AUTOTUNE) && B == 1 && S.n > 0) pending = true;
         }
+        if (h->p.model == MSM_MODEL_WATER) {
+            // LJ pass: the O sites and single sites of the water completion
+            const int *lb = kBrickShapes[brick_heuristic(S.n_mol + (S.n - 3 * S.n_mol), D.g)];
+            for (int k = 0; k < 3; k++) {
+                D.lj_bd[k] = lb[k];
+                D.lj_nb[k] = (D.g.nc[k] + lb[k] - 1) / lb[k];
+            }
+            D.lj_nbricks = D.lj_nb[0] * D.lj_nb[1] * D.lj_nb[2];
+        }
         D.grid_off = (int)G;
         G += tot;
         const LevelGeom &Lt = D.gg.L[l - 1];
@@ -493,6 +505,10 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     const size_t ts = h->precision == MSM_FP32 ? sizeof(float) : sizeof(double);
     TRY(ensure(h->count, sizeof(int) * (size_t)(M + 1)));
     TRY(ensure(h->start, sizeof(int) * (size_t)(M + 1)));
+    if (h->p.model == MSM_MODEL_WATER) {
+        TRY(ensure(h->lj_count, sizeof(int) * (size_t)(M + 1)));
+        TRY(ensure(h->lj_start, sizeof(int) * (size_t)(M + 1)));
+    }
     TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints()));
     TRY(ensure(h->qgrid, ts * (size_t)G));
     TRY(ensure(h->ucut, ts * (size_t)G));
@@ -551,13 +567,14 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     h->B = B;
     h->N = (int)N; h->M = (int)M; h->G = (int)G; h->UT = (int)UT; h->TT = (int)TT; h->PB = (int)PB;
     h->stiles = (int)ST;
-    h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = 0;
+    h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = h->max_lj_bricks = 0;
     for (int k = 0; k < MSM_MAX_LEVELS; k++) h->max_lev[k] = 0;
     for (const SysDesc &D : h->hsd) {
         h->max_n = std::max(h->max_n, D.n);
         h->max_mol = std::max(h->max_mol, D.n_mol);
         h->max_units = std::max(h->max_units, D.n_mol + (D.n - 3 * D.n_mol));
         h->max_bricks = std::max(h->max_bricks, D.nbricks);
+        h->max_lj_bricks = std::max(h->max_lj_bricks, D.lj_nbricks);
         h->max_atiles = std::max(h->max_atiles, anterp_tiles(D.gg.L[0]));
         for (int k = 0; k < l; k++) h->max_lev[k] = std::max(h->max_lev[k], D.gg.L[k].n[0] * D.gg.L[k].n[1] * D.gg.L[k].n[2]);
     }
@@ -590,7 +607,12 @@ static int ensure_atoms(msm_handle *h, int64_t n)
     TRY(ensure(h->apos, 4 * ts * nn));
     TRY(ensure(h->afrac, 4 * ts * nn));
     TRY(ensure(h->sr, 4 * ts * nn));
-    if (h->p.model == MSM_MODEL_WATER) TRY(ensure(h->lj, 4 * ts * nn));
+    if (h->p.model == MSM_MODEL_WATER) {
+        TRY(ensure(h->lj, 4 * ts * nn));
+        TRY(ensure(h->lj_apos, 4 * ts * nn));
+        TRY(ensure(h->lj_flag, sizeof(int) * nn));
+        TRY(ensure(h->lj_perm, sizeof(int) * nn));
+    }
     TRY(ensure(h->eatom, sizeof(double) * nn));
     TRY(ensure(h->vatom, sizeof(double) * nn));
     TRY(ensure(h->kin, sizeof(double) * nn));
@@ -726,9 +748,25 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             PROF(ST_LIST);
             TRY(launch_list_maintain<T>(la, st));
         }
-        PROF(ST_SHORT);
-        if (h->list_on) TRY(launch_list_force<T>(la, st));
-        TRY(launch_short<T>(s, model, st));
+        {
+            PROF(ST_SHORT);
+            if (h->list_on) TRY(launch_list_force<T>(la, st));
+            TRY(launch_short<T>(s, model, st));
+        }
+        if (model) {
+            PROF(ST_LJ);
+            // O-O Lennard-Jones over the LJ sites alone
+            TRY(launch_lj_count<T>(h->M, h->start.as<int>(), h->aflag.as<int>(), h->lj_count.as<int>(), status, st));
+            TRY(launch_scan(h->M, h->lj_count.as<int>(), h->lj_start.as<int>(), h->bsum.as<int>(), status, st));
+            TRY(launch_lj_compact<T>(h->M, h->start.as<int>(), h->lj_start.as<int>(), h->apos.as<vec4<T>>(),
+                                     h->aflag.as<int>(), h->perm.as<int>(), h->lj_apos.as<vec4<T>>(),
+                                     h->lj_flag.as<int>(), h->lj_perm.as<int>(), status, st));
+            ShortArgs<T> sl = s;
+            sl.max_bricks = h->max_lj_bricks;
+            sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
+            sl.perm = h->lj_perm.as<int>();
+            TRY(launch_short_lj<T>(sl, st));
+        }
     }
 
     // step 2: anterpolation
