@@ -234,13 +234,6 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
     }
 }
 
-bool short_rows_fit(const int bd[3], double a_sel, double h)
-{
-    // rows per axis: brick extent + 2 a_sel / h + 1, plus float rounding slack
-    const int pad = (int)ceil(2.0 * a_sel / h) + 3;
-    return (bd[1] + pad) * (bd[2] + pad) <= SR_MAXROWS;
-}
-
 template <typename T>
 int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st)
 {

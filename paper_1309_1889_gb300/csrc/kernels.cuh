@@ -78,9 +78,6 @@ template <typename T> int launch_lj_compact(int m_total, const int *start, const
                                             const int *aflag, const int *perm, vec4<T> *lj_apos, int *lj_flag,
                                             int *lj_perm, const int *status, cudaStream_t st);
 template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st);
-// Largest brick (cells per axis) whose candidate rows fit the kernel's row list
-// for cutoff a_sel and cell edge h.
-bool short_rows_fit(const int bd[3], double a_sel, double h);
 
 // ---- Verlet lists (k_list.cu, single systems) -----------------------------
 constexpr int VL_ROWS = 512;       // candidate rows per brick (9 bits of an entry)
