@@ -12,13 +12,21 @@
 //
 // The warp finds its rows in parallel (one candidate row per lane, kept rows
 // compacted by ballot into a shared list with running end offsets), then
-// streams the concatenation of the rows through shared memory 32 atoms at a
-// time, so every chunk but the last is full; a lane finds the row of the atom
-// it stages by binary search over the offsets.  All lanes then read each
-// staged j by broadcast.  Per candidate a lane evaluates one rsqrt and ~20
-// FP32 FMA-pipe instructions; pairs beyond a, the pair j = i and pairs inside
-// one rigid molecule get charge zero (exact zero contributions), never a
-// branch.  More rows than the list holds are taken in segments.
+// walks the concatenation of the rows 32 atoms at a time; a lane finds the
+// row of the atom it fetches by binary search over the offsets.  A fetched j
+// whose distance to the bounding box of the warp's i atoms is not below a
+// (cell rows overhang the cutoff sphere by up to a cell) is dropped there;
+// the rest enter a 64-entry FIFO in shared memory, which is drained 32 at a
+// time, so the pair loop runs full.  All lanes read each queued j by
+// broadcast.  Per candidate a lane evaluates one rsqrt and ~20 FP32 FMA-pipe
+// instructions; pairs beyond a, the pair j = i and pairs inside one rigid
+// molecule get charge zero (exact zero contributions), never a branch.  More
+// rows than the list holds are taken in segments.
+//
+// The box test computes, in the pair test's own rounding order, a lower bound
+// of every r^2 the j would meet (rounding is monotone), so a dropped j is one
+// that every lane would have tested out: dropping it removes exact zero
+// contributions only.
 //
 // Each i adds its in-range j's in ascending slot order into one accumulator,
 // whatever the brick shape or chunking: results are bitwise reproducible and
@@ -66,8 +74,8 @@ template <> __device__ __forceinline__ double r2_eps<double>() { return 1e-30; }
 template <typename T> struct ShortSmem {
     int rs0[SR_WARPS][SR_MAXROWS];      // first slot of each kept row
     int rend[SR_WARPS][SR_MAXROWS];     // running end of each row in the concatenation
-    vec4<T> sj[SR_WARPS][32];           // staged chunk
-    int sf[SR_WARPS][32];               // staged (molecule << 1 | LJ) flags
+    vec4<T> sj[SR_WARPS][64];           // FIFO of queued j atoms
+    int sf[SR_WARPS][64];               // their (molecule << 1 | LJ) flags
 };
 
 // MODEL: rigid-water completion -- pairs inside one molecule are skipped (the
@@ -130,6 +138,40 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         T phi = 0, ax = 0, ay = 0, az = 0;
         T lx = 0, ly = 0, lz = 0, le = 0;
         int npair = 0;
+        int head = 0, npend = 0;        // FIFO: queued j's at [head, head + npend) mod 64, head in {0, 32}
+
+        // sum the cnt queued j's from FIFO position q0 (no wrap: q0 + cnt <= 64)
+        auto pairs = [&](const int q0, const int cnt) {
+#pragma unroll 4
+            for (int k = 0; k < cnt; k++) {
+                const vec4<T> pj = S.sj[wid][q0 + k];
+                const T dx = pj.x - pi.x, dyy = pj.y - pi.y, dzz = pj.z - pi.z;
+                const T r2s = fma(dx, dx, fma(dyy, dyy, fma(dzz, dzz, r2_eps<T>())));
+                bool in = r2s < A.a2;
+                // j = i: the water model's molecule test excludes it (an atom is in its own
+                // molecule); bare charges test the distance
+                if (MODEL || LJP) in = in & ((unsigned)(fi ^ S.sf[wid][q0 + k]) >= 2u);
+                else in = in & (r2s > T(2) * r2_eps<T>());
+                if (COUNT) { npair += in ? 1 : 0; continue; }
+                const T ri = rsqrt_t<T>(r2s);
+                const T ri2 = ri * ri;
+                if (LJP) {
+                    const T m = in ? T(1) : T(0);
+                    const T sr2 = A.lj_s2 * (in ? ri2 : T(0));   // masked pairs (j = i: r^2 = eps) stay finite
+                    const T sr6 = sr2 * sr2 * sr2;
+                    le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
+                    const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
+                    lx = fma(-fl, dx, lx); ly = fma(-fl, dyy, ly); lz = fma(-fl, dzz, lz);
+                    continue;
+                }
+                const T qj = in ? pj.w : T(0);
+                const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
+                phi = fma(qj, ri - poly, phi);
+                const T fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
+                const T sc = qj * fs;
+                ax = fma(sc, dx, ax); ay = fma(sc, dyy, ay); az = fma(sc, dzz, az);
+            }
+        };
 
         const int zlo = max(0, (int)floor((lo[2] - A.a_sel) * inv_h));
         const int zhi = min(nz - 1, (int)floor((hi[2] + A.a_sel) * inv_h));
@@ -177,9 +219,12 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                 r_next += 32;
             }
             __syncwarp();
-            // ---- stream the segment's atoms, 32 per chunk
+            // ---- fetch the segment's atoms 32 at a time, queue those near the box
             for (int cb = 0; cb < total; cb += 32) {
                 const int cnt = min(32, total - cb);
+                bool keep = false;
+                vec4<T> pj{T(0), T(0), T(0), T(0)};
+                int fj = 0;
                 if (lane < cnt) {
                     const int want = cb + lane;
                     int lo_r = 0, hi_r = nrows - 1;
@@ -188,41 +233,32 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                         if (S.rend[wid][mid] > want) hi_r = mid; else lo_r = mid + 1;
                     }
                     const int js = S.rs0[wid][lo_r] + (want - (lo_r ? S.rend[wid][lo_r - 1] : 0));
-                    S.sj[wid][lane] = A.apos[js];
-                    if (MODEL || LJP) S.sf[wid][lane] = A.aflag[js];
+                    pj = A.apos[js];
+                    if (MODEL || LJP) fj = A.aflag[js];
+                    const T ex = max(T(0), max(lo[0] - pj.x, pj.x - hi[0]));
+                    const T ey = max(T(0), max(lo[1] - pj.y, pj.y - hi[1]));
+                    const T ez = max(T(0), max(lo[2] - pj.z, pj.z - hi[2]));
+                    keep = fma(ex, ex, fma(ey, ey, fma(ez, ez, r2_eps<T>()))) < A.a2;
                 }
-                __syncwarp();
-#pragma unroll 4
-                for (int k = 0; k < cnt; k++) {
-                    const vec4<T> pj = S.sj[wid][k];
-                    const T dx = pj.x - pi.x, dyy = pj.y - pi.y, dzz = pj.z - pi.z;
-                    const T r2s = fma(dx, dx, fma(dyy, dyy, fma(dzz, dzz, r2_eps<T>())));
-                    bool in = r2s < A.a2;
-                    // j = i: the water model's molecule test excludes it (an atom is in its own
-                    // molecule); bare charges test the distance
-                    if (MODEL || LJP) in = in & ((unsigned)(fi ^ S.sf[wid][k]) >= 2u);
-                    else in = in & (r2s > T(2) * r2_eps<T>());
-                    if (COUNT) { npair += in ? 1 : 0; continue; }
-                    const T ri = rsqrt_t<T>(r2s);
-                    const T ri2 = ri * ri;
-                    if (LJP) {
-                        const T m = in ? T(1) : T(0);
-                        const T sr2 = A.lj_s2 * (in ? ri2 : T(0));   // masked pairs (j = i: r^2 = eps) stay finite
-                        const T sr6 = sr2 * sr2 * sr2;
-                        le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
-                        const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
-                        lx = fma(-fl, dx, lx); ly = fma(-fl, dyy, ly); lz = fma(-fl, dzz, lz);
-                        continue;
-                    }
-                    const T qj = in ? pj.w : T(0);
-                    const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
-                    phi = fma(qj, ri - poly, phi);
-                    const T fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
-                    const T sc = qj * fs;
-                    ax = fma(sc, dx, ax); ay = fma(sc, dyy, ay); az = fma(sc, dzz, az);
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int q = (head + npend + __popc(m & lt)) & 63;
+                    S.sj[wid][q] = pj;
+                    if (MODEL || LJP) S.sf[wid][q] = fj;
                 }
+                npend += __popc(m);
                 __syncwarp();
+                if (npend >= 32) {
+                    pairs(head, 32);
+                    head ^= 32;
+                    npend -= 32;
+                    __syncwarp();
+                }
             }
+        }
+        if (npend > 0) {
+            pairs(head, npend);
+            __syncwarp();
         }
         if (valid) {
             if (COUNT) { A.cnt[slot] = (double)npair; continue; }
