@@ -287,6 +287,18 @@ MSM_API int  msm_cell_list_noalloc(int64_t n, const double *pos, const double bo
  * build. */
 MSM_API int  msm_list_stats(msm_handle *h, int64_t *out, int32_t max);
 
+/* Diagnostic: the binary64 <-> binary32 conversions the FP32 kernels use
+ * between the FP64 state and FP32 arithmetic, computed (like there) with
+ * integer operations on the IEEE 754 bit fields.  x32[i] = x[i] rounded to
+ * binary32 (to nearest, ties to even); y64[i] = y[i] as binary64.  Both agree
+ * with the hardware conversions except that magnitudes below 2^-126 become
+ * signed zero; NaN stays NaN.  x, x32, y, y64 are device arrays of n elements
+ * owned by the caller; stream is a cudaStream_t (NULL: the legacy default
+ * stream).  Synchronises the stream.  Errors: MSM_EINVAL (n < 0, NULL or host
+ * arrays), MSM_ECUDA. */
+MSM_API int  msm_diag_convert(int64_t n, const double *x, float *x32, const float *y, double *y64,
+                              void *stream);
+
 /* Number of kernels this library launched since load (all handles). */
 MSM_API int64_t msm_kernel_launches(void);
 

@@ -51,7 +51,7 @@ EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
            "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats",
-           "msm_system_forces_batched", "md_run_batched")
+           "msm_system_forces_batched", "md_run_batched", "msm_diag_convert")
 
 
 def lib():
@@ -89,6 +89,7 @@ def lib():
         L.msm_list_stats.argtypes = [p, p, i32]; L.msm_list_stats.restype = C.c_int
         L.msm_cell_list_noalloc.argtypes = [i64, p, P(d), d, p, p, i64, p]
         L.msm_cell_list_noalloc.restype = C.c_int
+        L.msm_diag_convert.argtypes = [i64, p, p, p, p, p]; L.msm_diag_convert.restype = C.c_int
         L.msm_last_error.argtypes = []; L.msm_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -101,6 +102,19 @@ def _check(rc: int):
 
 def kernel_launches() -> int:
     return int(lib().msm_kernel_launches())
+
+
+def diag_convert(x, y):
+    """The library's integer-pipe conversions on CUDA tensors: (binary32 of the
+    float64 tensor x, binary64 of the float32 tensor y)."""
+    t = _torch()
+    if x.dtype != t.float64 or y.dtype != t.float32 or not x.is_cuda or not y.is_cuda or x.numel() != y.numel():
+        raise ValueError("x: float64 CUDA tensor, y: float32 CUDA tensor of the same size")
+    x = x.contiguous(); y = y.contiguous()
+    x32 = t.empty_like(x, dtype=t.float32); y64 = t.empty_like(y, dtype=t.float64)
+    _check(lib().msm_diag_convert(x.numel(), x.data_ptr(), x32.data_ptr(), y.data_ptr(), y64.data_ptr(),
+                                  t.cuda.current_stream().cuda_stream))
+    return x32, y64
 
 
 # --------------------------------------------------------------- marshalling

@@ -23,6 +23,45 @@ template <typename T> struct alignas(4 * sizeof(T)) vec4 { T x, y, z, w; };
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 __device__ __forceinline__ bool failed(const int *status) { return *(volatile const int *)status != 0; }
 
+// binary64 <-> binary32 conversions on the integer pipe, from the IEEE 754
+// bit layouts (sign | exponent | fraction: 1|11|52 and 1|8|23, biases 1023
+// and 127).  GB300 issues FP64 instructions, conversions included, at 1/64 of
+// the FP32 rate, so kernels that move values between the FP64 state and FP32
+// arithmetic convert with integer operations instead.  Results equal the
+// hardware conversions (round to nearest, ties to even) wherever the binary32
+// value is normal, zero or infinite; NaN stays NaN; magnitudes below the
+// binary32 normal range (2^-126) become signed zero in both directions.
+__device__ __forceinline__ float f32_of(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7ffu);                  // binary64 biased exponent
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);    // leading 23 fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                     // the 29 bits dropped
+    unsigned r = ((unsigned)(e - 896) << 23) + m;               // rebias: 1023 - 127 = 896
+    // ties to even; a carry out of the fraction steps the exponent (to infinity at the top)
+    r += (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
+    if (e <= 896) r = 0u;
+    if (e >= 1151) r = (e == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(r | (hi & 0x80000000u));
+}
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    unsigned hi = ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3), lo = u << 29;
+    if (e == 0u) hi = lo = 0u;
+    if (e == 255u) hi |= 0x7ff00000u;
+    return __longlong_as_double((long long)(((unsigned long long)(hi | (u & 0x80000000u)) << 32) | lo));
+}
+// T from / to the FP64 state: the integer-pipe conversions for T = float, the
+// identity for T = double.
+template <typename T> __device__ __forceinline__ T to_t(double x);
+template <> __device__ __forceinline__ float to_t<float>(double x) { return f32_of(x); }
+template <> __device__ __forceinline__ double to_t<double>(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return f64_of(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+
 // Geometry of one system's finest-grid cells and grid levels.
 struct CellGeom {
     double origin[3];   // box origin x0
@@ -66,6 +105,8 @@ struct SysDesc {
     int top_off;        // first point of its top level in the FP64 top buffer
     int ttab_off;       // first entry of its top-level Toeplitz table
     int part_off;       // first block of its FP64 sum partials
+    int wall_lo[3], wall_hi[3];   // only atoms in cells c < wall_lo[d] or c > wall_hi[d] can
+                                  // reach the flat-bottom wall (one cell of margin)
 };
 
 // 1-D cubic C1 numerical-Hermite weights of an atom whose fractional

@@ -35,24 +35,39 @@ __global__ void k_bin_keys(const Batch bt, const double *__restrict__ pos, const
     const CellGeom &g = D.g;
     int c[3];
     double r[3], f[3];
+    // FP64 arithmetic only where the binning contract needs it (the subtract and
+    // the multiply, and t - floor(t)); the finiteness and range tests, the floor
+    // and the conversions to T act on the IEEE 754 bit fields (GB300 runs FP64
+    // instructions at 1/64 of the FP32 rate).
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        double x = pos[3 * i + d];
-        if (!isfinite(x)) { set_status(status, MSM_EINVAL); key[i] = -1; return; }
-        double rl = __dsub_rn(x, g.origin[d]);
-        double t = __dmul_rn(rl, D.inv_h);
-        double fl = floor(t);
-        if (!(t >= 0.0) || fl > (double)(g.nc[d] - 1)) { set_status(status, MSM_ERANGE); key[i] = -1; return; }
-        c[d] = (int)fl;
+        const double x = pos[3 * i + d];
+        if (((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff) { set_status(status, MSM_EINVAL); key[i] = -1; return; }
+        const double rl = __dsub_rn(x, g.origin[d]);
+        const double t = __dmul_rn(rl, D.inv_h);
+        // floor(t) for 0 <= t < 2^31: clear the fraction bits below the binary point
+        const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+        const int e = (int)((b >> 52) & 0x7ff) - 1023;                 // unbiased exponent
+        if ((b >> 63) && t != 0.0) { set_status(status, MSM_ERANGE); key[i] = -1; return; }   // t < 0
+        if (e >= 31) { set_status(status, MSM_ERANGE); key[i] = -1; return; }
+        int ci = 0;
+        double fl = __longlong_as_double((long long)(b & 0x8000000000000000ull));   // floor of [+-0, 1): signed 0
+        if (e >= 0) {
+            const int sh = 52 - e;                                      // fraction bits below the point
+            ci = (int)((((b & 0xfffffffffffffull) | (1ull << 52))) >> sh);
+            fl = __longlong_as_double((long long)(b & ~((1ull << sh) - 1ull)));
+        }
+        if (ci > g.nc[d] - 1) { set_status(status, MSM_ERANGE); key[i] = -1; return; }
+        c[d] = ci;
         r[d] = rl;
         f[d] = __dsub_rn(t, fl);
     }
     int k = D.cell_off + (c[2] * g.nc[1] + c[1]) * g.nc[0] + c[0];
     key[i] = k;
     atomicAdd(&count[k], 1);
-    T qi = (T)q[i];
-    rel[i] = vec4<T>{(T)r[0], (T)r[1], (T)r[2], qi};
-    frac[i] = vec4<T>{(T)f[0], (T)f[1], (T)f[2], qi};
+    T qi = to_t<T>(q[i]);
+    rel[i] = vec4<T>{to_t<T>(r[0]), to_t<T>(r[1]), to_t<T>(r[2]), qi};
+    frac[i] = vec4<T>{to_t<T>(f[0]), to_t<T>(f[1]), to_t<T>(f[2]), qi};
 }
 
 // Exclusive scan in three passes: per-block sums, scan of block sums, add.
@@ -166,6 +181,27 @@ __global__ void k_gather(const Batch bt, const int *__restrict__ perm, const int
     const int li = i - D.atom_off;
     const int mol = li < 3 * D.n_mol ? i - li % 3 : i;       // first atom of the molecule; single sites: own
     aflag[s] = (mol << 1) | ((lj && lj[i]) ? 1 : 0);
+}
+
+// The integer-pipe binary64 <-> binary32 conversions of the FP32 kernels, on
+// device arrays (a diagnostic entry point checks them against the hardware's).
+__global__ void k_diag_convert(int64_t n, const double *__restrict__ x, float *__restrict__ x32,
+                               const float *__restrict__ y, double *__restrict__ y64)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x32[i] = f32_of(x[i]);
+    y64[i] = f64_of(y[i]);
+}
+
+int launch_diag_convert(int64_t n, const double *x, float *x32, const float *y, double *y64, cudaStream_t st)
+{
+    if (n <= 0) return MSM_OK;
+    if (n > ((int64_t)1 << 40)) return fail_msg(MSM_EINVAL, "n too large");
+    k_diag_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, x32, y, y64);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
 }
 
 int scan_scratch_ints() { return SCAN_B + 1; }

@@ -691,32 +691,37 @@ __global__ void k_interp(const InterpArgs<T> A)
             gz = fma(dz[oz] * wy[oy], rp, gz);
         }
     }
+    // Per-atom combination in T, then one conversion to the FP64 outputs (on the
+    // integer pipe: GB300 runs FP64 instructions at 1/64 of the FP32 rate).
     const int i = A.perm[s];
     const vec4<T> sr = A.sr[i];
-    const double q = A.q[i];
-    const double ke = A.ke, ih = D.inv_h;
-    const double phi = ke * ((double)sr.w + (double)p - q * A.self);
-    double F[3] = {ke * ((double)sr.x - q * (double)gx * ih), ke * ((double)sr.y - q * (double)gy * ih),
-                   ke * ((double)sr.z - q * (double)gz * ih)};
-    double e = 0.5 * q * phi;
+    const T q = to_t<T>(A.q[i]);
+    const T ke = to_t<T>(A.ke), ih = to_t<T>(D.inv_h);
+    const T phi = ke * (sr.w + p - q * to_t<T>(A.self));
+    T F[3] = {ke * (sr.x - q * gx * ih), ke * (sr.y - q * gy * ih), ke * (sr.z - q * gz * ih)};
+    T e = T(0.5) * q * phi;
     if (A.lj) {
         const vec4<T> lj = A.lj[i];
-        F[0] += (double)lj.x; F[1] += (double)lj.y; F[2] += (double)lj.z;
-        e += 0.5 * (double)lj.w;
+        F[0] += lj.x; F[1] += lj.y; F[2] += lj.z;
+        e += T(0.5) * lj.w;
     }
-    if (A.wall_k > 0.0) {                          // flat-bottom wall of the water completion
+    double Fd[3] = {to_d(F[0]), to_d(F[1]), to_d(F[2])}, ed = to_d(e);
+    const double x[3] = {A.pos[3 * i], A.pos[3 * i + 1], A.pos[3 * i + 2]};
+    const int c[3] = {cx, cy, cz};
+    if (A.wall_k > 0.0 && (c[0] < D.wall_lo[0] || c[0] > D.wall_hi[0] || c[1] < D.wall_lo[1] ||
+                           c[1] > D.wall_hi[1] || c[2] < D.wall_lo[2] || c[2] > D.wall_hi[2])) {
+        // flat-bottom wall of the water completion (FP64; only cells near a face can reach it)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double x = A.pos[3 * i + d];
-            const double lo = A.wall_w - (x - D.box_lo[d]), hi = A.wall_w - (D.box_hi[d] - x);
-            if (lo > 0.0) { F[d] += A.wall_k * lo; e += 0.5 * A.wall_k * lo * lo; }
-            if (hi > 0.0) { F[d] -= A.wall_k * hi; e += 0.5 * A.wall_k * hi * hi; }
+            const double lo = A.wall_w - (x[d] - D.box_lo[d]), hi = A.wall_w - (D.box_hi[d] - x[d]);
+            if (lo > 0.0) { Fd[d] += A.wall_k * lo; ed += 0.5 * A.wall_k * lo * lo; }
+            if (hi > 0.0) { Fd[d] -= A.wall_k * hi; ed += 0.5 * A.wall_k * hi * hi; }
         }
     }
-    if (A.forces) { A.forces[3 * i] = F[0]; A.forces[3 * i + 1] = F[1]; A.forces[3 * i + 2] = F[2]; }
-    if (A.pot) A.pot[i] = phi;
-    A.eatom[i] = e;
-    A.vatom[i] = A.pos[3 * i] * F[0] + A.pos[3 * i + 1] * F[1] + A.pos[3 * i + 2] * F[2];
+    if (A.forces) { A.forces[3 * i] = Fd[0]; A.forces[3 * i + 1] = Fd[1]; A.forces[3 * i + 2] = Fd[2]; }
+    if (A.pot) A.pot[i] = to_d(phi);
+    A.eatom[i] = ed;
+    A.vatom[i] = x[0] * Fd[0] + x[1] * Fd[1] + x[2] * Fd[2];
 }
 
 template <typename T>

@@ -2,8 +2,9 @@
 //   k_exclusions   rigid-water completion: the short-range kernel skipped the
 //                  three intramolecular pairs of each (O, H, H) triple, so only
 //                  their smooth part k_e q_i q_j gamma(r/a)/a, which the grids
-//                  carry, is subtracted here (FP64); together this removes the
-//                  full 1/r = g* + gamma(r/a)/a of every excluded pair
+//                  carry, is subtracted here (in T, accumulated into the FP64
+//                  outputs); together this removes the full 1/r = g* +
+//                  gamma(r/a)/a of every excluded pair
 //   k_sum_*        deterministic FP64 sums (fixed partition, fixed tree) for
 //                  the energy, the virial and the kinetic energy
 //   k_vv_first     velocity Verlet (Sec. 2): half kick, drift, then SHAKE
@@ -29,20 +30,23 @@ __global__ void k_exclusions(const ExclArgs A)
     const int mo = blockIdx.x * blockDim.x + threadIdx.x;
     if (mo >= D.n_mol || failed(A.status)) return;
     const int i0 = D.atom_off + 3 * mo;
-    double x[3][3];
-    T q[3], F[3][3], dphi[3], de[3];
+    // bond vectors from two FP64 differences against the O atom, then T
+    T rel[3][3], q[3], F[3][3], dphi[3], de[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        q[a] = (T)A.q[i0 + a];
+        q[a] = to_t<T>(A.q[i0 + a]);
         dphi[a] = de[a] = 0;
 #pragma unroll
-        for (int d = 0; d < 3; d++) { x[a][d] = A.x[3 * (i0 + a) + d]; F[a][d] = 0; }
+        for (int d = 0; d < 3; d++) {
+            rel[a][d] = a ? to_t<T>(A.x[3 * (i0 + a) + d] - A.x[3 * i0 + d]) : T(0);
+            F[a][d] = 0;
+        }
     }
-    const T ke = (T)A.ke, ia = T(1) / (T)A.a;
+    const T ke = to_t<T>(A.ke), ia = T(1) / to_t<T>(A.a);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const int a = c == 2 ? 1 : 0, b = c == 0 ? 1 : 2;
-        const T dx = (T)(x[a][0] - x[b][0]), dy = (T)(x[a][1] - x[b][1]), dz = (T)(x[a][2] - x[b][2]);
+        const T dx = rel[a][0] - rel[b][0], dy = rel[a][1] - rel[b][1], dz = rel[a][2] - rel[b][2];
         const T r = sqrt(dx * dx + dy * dy + dz * dz);
         const T rho = r * ia;
         T gam, dgam;                                   // gamma(rho), gamma'(rho)
@@ -71,11 +75,12 @@ __global__ void k_exclusions(const ExclArgs A)
         double v = 0;
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            if (A.forces) A.forces[3 * i + d] += (double)F[a][d];
-            v += x[a][d] * (double)F[a][d];
+            const double fd = to_d(F[a][d]);
+            if (A.forces) A.forces[3 * i + d] += fd;
+            v += A.x[3 * i + d] * fd;
         }
-        if (A.pot) A.pot[i] += (double)dphi[a];
-        A.eatom[i] += (double)de[a];
+        if (A.pot) A.pot[i] += to_d(dphi[a]);
+        A.eatom[i] += to_d(de[a]);
         A.vatom[i] += v;
     }
 }
@@ -188,32 +193,37 @@ __global__ void k_vv_first(const VVArgs A)
         }
         return;
     }
+    // The state stays FP64; what a step adds to it (half kick, drift, SHAKE
+    // correction) is formed in T in molecule-local coordinates (relative to the
+    // old O position), so x and v take one FP64 add per component.  GB300 runs
+    // FP64 instructions at 1/64 of the FP32 rate: the conversions use the
+    // integer pipe, and no FP64 value is kept live across the SHAKE loop (the
+    // state is read again after it; holding 18 doubles through the loop cost
+    // ~11 FP64-pipe instructions per iteration).
     const int i0 = D.atom_off + 3 * u;
-    double xo[3][3], xn[3][3], v[3][3], im[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        im[a] = A.im[i0 + a];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            xo[a][d] = A.x[3 * (i0 + a) + d];
-            v[a][d] = A.v[3 * (i0 + a) + d] + 0.5 * dt * A.f[3 * (i0 + a) + d] * im[a];   // half kick
-            xn[a][d] = xo[a][d] + dt * v[a][d];                                         // drift
-        }
-    }
-    // SHAKE in local coordinates (relative to the old O position), compute type T
+    const T tdt = (T)dt, hk = (T)(0.5 * dt), inv_dt = T(1) / tdt;
     T p[3][3], p0[3][3], ro[3][3], w[3], d2[3];
+    {
+        T rel[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            w[a] = to_t<T>(A.im[i0 + a]);
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double x = A.x[3 * (i0 + a) + d];
+                rel[a][d] = a ? to_t<T>(x - A.x[3 * i0 + d]) : T(0);
+                const T dv = hk * to_t<T>(A.f[3 * (i0 + a) + d]) * w[a];          // half kick
+                p0[a][d] = p[a][d] = rel[a][d] + tdt * (to_t<T>(A.v[3 * (i0 + a) + d]) + dv);   // drift
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) ro[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
+    }
+    // SHAKE on the drifted local positions p; the old bond vectors ro give the directions
     d2[0] = d2[1] = (T)A.d_oh2;
     d2[2] = (T)A.d_hh2;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        w[a] = (T)im[a];
-#pragma unroll
-        for (int d = 0; d < 3; d++) p0[a][d] = p[a][d] = (T)(xn[a][d] - xo[0][d]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) ro[c][d] = (T)(xo[bond_i(c)][d] - xo[bond_j(c)][d]);
     const T tol = (T)A.tol;
     bool ok = false;
     for (int it = 0; it < A.max_iter && !ok; it++) {
@@ -225,7 +235,7 @@ __global__ void k_vv_first(const VVArgs A)
 #pragma unroll
             for (int d = 0; d < 3; d++) { rn[d] = p[a][d] - p[b][d]; rn2 += rn[d] * rn[d]; }
             const T diff = d2[c] - rn2;
-            if (fabs(diff) > tol * d2[c]) {
+            if ((diff < T(0) ? -diff : diff) > tol * d2[c]) {
                 ok = false;
 #pragma unroll
                 for (int d = 0; d < 3; d++) dot += ro[c][d] * rn[d];
@@ -236,16 +246,20 @@ __global__ void k_vv_first(const VVArgs A)
         }
     }
     if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 1); atomicCAS(A.status + 3, 0, i0 + 1); }
-    const double inv_dt = 1.0 / dt;
+    // x = x_old + (drift + dp), v = v_old + (kick + dp / dt): the same kick and drift
+    // arithmetic as above, on the state read again
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double dp = (double)(p[a][d] - p0[a][d]);
-            const int i = i0 + a;
-            A.xo[3 * i + d] = xo[a][d];
-            A.x[3 * i + d] = xn[a][d] + dp;
-            A.v[3 * i + d] = v[a][d] + dp * inv_dt;
+            const int k = 3 * (i0 + a) + d;
+            const double x = A.x[k], v = A.v[k];
+            const T dv = hk * to_t<T>(A.f[k]) * w[a];
+            const T sd = tdt * (to_t<T>(v) + dv);
+            const T dp = p[a][d] - p0[a][d];
+            A.xo[k] = x;
+            A.x[k] = x + to_d(sd + dp);
+            A.v[k] = v + to_d(dv + dp * inv_dt);
         }
 }
 
@@ -270,31 +284,32 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
         if (kin) kin[i] = 0.5 * m * k2;
         return;
     }
+    // as in k_vv_first: the kick and the RATTLE correction form one increment in
+    // T, integer-pipe conversions, and no FP64 value lives across the loop
     const int i0 = D.atom_off + 3 * u;
-    double v[3][3], m[3];
+    const T hk = (T)hdt;
+    T r[3][3], r2[3], wv[3][3], wm[3];
+    {
+        T rel[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        m[a] = A.m[i0 + a];
-        const double im = A.im[i0 + a];
+        for (int a = 0; a < 3; a++) {
+            wm[a] = to_t<T>(A.im[i0 + a]);
 #pragma unroll
-        for (int d = 0; d < 3; d++) v[a][d] = A.v[3 * (i0 + a) + d] + hdt * A.f[3 * (i0 + a) + d] * im;
-    }
-    // RATTLE velocity stage: zero the bond-parallel relative velocities
-    T r[3][3], r2[3], wv[3][3], w0[3][3], wm[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        r2[c] = 0;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            r[c][d] = (T)(A.x[3 * (i0 + bond_i(c)) + d] - A.x[3 * (i0 + bond_j(c)) + d]);
-            r2[c] += r[c][d] * r[c][d];
+            for (int d = 0; d < 3; d++) {
+                wv[a][d] = to_t<T>(A.v[3 * (i0 + a) + d]) + hk * to_t<T>(A.f[3 * (i0 + a) + d]) * wm[a];
+                rel[a][d] = a ? to_t<T>(A.x[3 * (i0 + a) + d] - A.x[3 * i0 + d]) : T(0);
+            }
         }
-    }
+        // RATTLE velocity stage: zero the bond-parallel relative velocities
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        wm[a] = (T)A.im[i0 + a];
+        for (int c = 0; c < 3; c++) {
+            r2[c] = 0;
 #pragma unroll
-        for (int d = 0; d < 3; d++) w0[a][d] = wv[a][d] = (T)v[a][d];
+            for (int d = 0; d < 3; d++) {
+                r[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
+                r2[c] += r[c][d] * r[c][d];
+            }
+        }
     }
     const T tol = (T)A.tol_v;
     bool ok = false;
@@ -314,7 +329,7 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
 #pragma unroll
             for (int d = 0; d < 3; d++) rv += r[c][d] * (wv[a][d] - wv[b][d]);
             const T lim = sizeof(T) == 4 ? tol * sqrt(r2[c]) * (spd[a] + spd[b]) : tol;
-            if (fabs(rv) > lim) {
+            if ((rv < T(0) ? -rv : rv) > lim) {
                 ok = false;
                 const T k = rv / (r2[c] * (wm[a] + wm[b]));
 #pragma unroll
@@ -329,11 +344,12 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
         double k2 = 0;
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double vv = v[a][d] + (double)(wv[a][d] - w0[a][d]);
+            const double v = A.v[3 * i + d];
+            const double vv = v + to_d(wv[a][d] - to_t<T>(v));
             A.v[3 * i + d] = vv;
             k2 += vv * vv;
         }
-        if (kin) kin[i] = 0.5 * m[a] * k2;
+        if (kin) kin[i] = 0.5 * A.m[i] * k2;
     }
 }
 

@@ -40,6 +40,7 @@ template <typename T> struct BinArgs {
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
 int scan_scratch_ints();
+int launch_diag_convert(int64_t n, const double *x, float *x32, const float *y, double *y64, cudaStream_t st);
 int launch_scan(int m, const int *count, int *start, int *bsum, const int *status, cudaStream_t st);
 int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int *perm, int *bsum, int *status,
                        cudaStream_t st);

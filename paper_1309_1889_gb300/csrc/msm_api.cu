@@ -439,6 +439,10 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         D.g.h = hh;
         D.g.ncells = (int)ncells;
         D.inv_h = 1.0 / hh;
+        for (int k = 0; k < 3; k++) {
+            D.wall_lo[k] = (int)floor(h->p.wall_width * D.inv_h) + 2;
+            D.wall_hi[k] = (int)floor((S.box[3 + k] - h->p.wall_width) * D.inv_h) - 2;
+        }
         D.gg.levels = l;
         int64_t lo[3], hi[3], tot = 0;
         for (int k = 0; k < 3; k++) { lo[k] = -1; hi[k] = (int64_t)floor(S.box[3 + k] / hh) + 2; }
@@ -1661,6 +1665,18 @@ extern "C" int msm_list_stats(msm_handle *h, int64_t *out, int32_t max)
     const int64_t v[8] = {h->vl_builds, h->vl_overflows, h->vl_cap, h->vl_cap_lj, VL_ROWS,
                           h->vl_seen[0], h->vl_seen[1], h->vl_seen[2]};
     for (int k = 0; k < 8 && k < max; k++) out[k] = v[k];
+    return MSM_OK;
+}
+
+extern "C" int msm_diag_convert(int64_t n, const double *x, float *x32, const float *y, double *y64, void *stream)
+{
+    if (n < 0) return fail_msg(MSM_EINVAL, "n < 0");
+    if (n == 0) return MSM_OK;
+    if (!on_device(x) || !on_device(x32) || !on_device(y) || !on_device(y64))
+        return fail_msg(MSM_EINVAL, "msm_diag_convert takes device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(launch_diag_convert(n, x, x32, y, y64, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
     return MSM_OK;
 }
 
