@@ -13,7 +13,8 @@
 //   k_scatter      atom -> a slot of its cell (order inside a cell arbitrary)
 //   k_sort_cells   each cell's slots reordered by atom index: the result is the
 //                  unique stable order (key, index), whatever the atomics did
-//   k_gather       sorted copies of position, fraction, key and (molecule, LJ) flag
+//   k_gather       sorted copies of position, fraction, key and (molecule, LJ)
+//                  flag, and each atom's anterpolation weights
 //
 // A batch of systems is binned by one pass of each kernel: a system's cell ids
 // are offset by the cells of the systems before it, so the one global stable
@@ -163,11 +164,11 @@ __global__ void k_sort_cells(int ncells, const int *__restrict__ start, int *__r
 // Sorted slots of system s are [atom_off, atom_off + n): its cells come before
 // the next system's and every atom lands in a cell of its own system.
 template <typename T>
-__global__ void k_gather(const Batch bt, const int *__restrict__ perm, const int *__restrict__ key,
+__global__ void k_gather(const Batch bt, int n_total, const int *__restrict__ perm, const int *__restrict__ key,
                          const vec4<T> *__restrict__ rel, const vec4<T> *__restrict__ frac,
                          const uint8_t *__restrict__ lj, vec4<T> *__restrict__ apos,
                          vec4<T> *__restrict__ afrac, int *__restrict__ akey, int *__restrict__ aflag,
-                         const int *__restrict__ status)
+                         vec4<T> *__restrict__ aw, const int *__restrict__ status)
 {
     if (failed(status)) return;
     const SysDesc &D = bt.sd[blockIdx.y];
@@ -176,8 +177,18 @@ __global__ void k_gather(const Batch bt, const int *__restrict__ perm, const int
     const int s = D.atom_off + ls;
     const int i = perm[s];
     apos[s] = rel[i];
-    afrac[s] = frac[i];
+    const vec4<T> f = frac[i];
+    afrac[s] = f;
     akey[s] = key[i];
+    if (aw) {                      // the atom's anterpolation weights (Sec. 3, p = 3), x scaled by q
+        T wx[4], wy[4], wz[4];
+        phi_weights(f.x, wx);
+        phi_weights(f.y, wy);
+        phi_weights(f.z, wz);
+        aw[s] = vec4<T>{wx[0] * f.w, wx[1] * f.w, wx[2] * f.w, wx[3] * f.w};
+        aw[n_total + s] = vec4<T>{wy[0], wy[1], wy[2], wy[3]};
+        aw[2 * n_total + s] = vec4<T>{wz[0], wz[1], wz[2], wz[3]};
+    }
     const int li = i - D.atom_off;
     const int mol = li < 3 * D.n_mol ? i - li % 3 : i;       // first atom of the molecule; single sites: own
     aflag[s] = (mol << 1) | ((lj && lj[i]) ? 1 : 0);
@@ -259,8 +270,8 @@ int launch_bin(const BinArgs<T> &a, cudaStream_t st)
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, a.key, a.start, a.count, a.perm, a.status);
         k_sort_cells<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.perm, a.status);
-        k_gather<T><<<ga, 256, 0, st>>>(a.bt, a.perm, a.key, a.rel, a.frac, a.lj, a.apos, a.afrac, a.akey,
-                                        a.aflag, a.status);
+        k_gather<T><<<ga, 256, 0, st>>>(a.bt, n, a.perm, a.key, a.rel, a.frac, a.lj, a.apos, a.afrac, a.akey,
+                                        a.aflag, a.aw, a.status);
         count_launch(3);
     }
     CUDA_TRY(cudaGetLastError());

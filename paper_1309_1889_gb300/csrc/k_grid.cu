@@ -1,7 +1,7 @@
 // k_grid.cu -- the long-range steps of the MSM (Sec. 3):
-//   k_anterp       q^0_mu = sum_j phi^0_mu(r_j) q_j, one thread per grid point
-//                  gathering the atoms of the 4^3 cells its basis function
-//                  touches (cells mu-2 .. mu+1 per axis): no atomics
+//   k_anterp       q^0_mu = sum_j phi^0_mu(r_j) q_j, one thread per column of
+//                  8 grid points gathering the atoms of the cells their basis
+//                  functions touch (cells mu-2 .. mu+1 per axis): no atomics
 //   k_restrict     q^{k+1}_mu = sum_nu Phi(nu/2 - mu)^{x3} q^k_nu: taps at
 //                  nu - 2mu in {-3,-1,0,1,3} with weights {-1,9,16,9,-1}/16
 //   k_stencil      u^{k,cut}_mu = sum_n 2^{-k} W[n] q^k_{mu+n}, W[n] = g^0(|n| h)
@@ -29,168 +29,84 @@ namespace msm {
 // ---------------------------------------------------------------- anterpolation
 
 
-// A CTA owns a tile of AT_X x AT_Y x AT_Z level-0 points.  The cells whose atoms
-// touch the tile (tile - 2 .. tile + 1 per axis) are staged in shared memory:
-// per atom the 4 weights along each axis (x weights pre-multiplied by q), one
-// float per weight, structure-of-arrays.  Each thread then gathers its point's
-// 4^3 cells in a fixed order (cells by oz, oy, ox, atoms by slot).  A block with
-// more atoms than the staging capacity (very dense input) takes the same loop
-// over global memory with the same arithmetic, so results do not depend on
-// which path ran.
-constexpr int AT_X = 8, AT_Y = 8, AT_Z = 4, AT_THREADS = AT_X * AT_Y * AT_Z;
-constexpr int AC_X = AT_X + 3, AC_Y = AT_Y + 3, AC_Z = AT_Z + 3, AC_N = AC_X * AC_Y * AC_Z;
-constexpr int AT_CAP = 1792;
-
-template <typename T> struct AnterpSmem {
-    int cell_off[AC_N + 1];
-    T w[12][AT_CAP];        // [0..3] x weights * q, [4..7] y weights, [8..11] z weights
-};
-template <typename T> size_t anterp_smem_bytes() { return sizeof(AnterpSmem<T>); }
+// A thread owns AN_Z consecutive level-0 points along z at one (x, y); a CTA
+// is an AN_X x AN_Y patch of such columns.  Point mu receives, from an atom in
+// cell c, the weight with index O = mu - c + 1 per axis (cells mu - 2 .. mu + 1).
+// For each of the 4 cell rows in y and the AN_Z + 3 rows in z that reach the
+// column, the 4 cells mu_x - 2 .. mu_x + 1 of the row are one contiguous range
+// of sorted slots; every atom of it adds (q wx[Ox] wy[Oy]) wz[Oz] to the up to
+// 4 points of the column it reaches (Oz fixed by the row, so the accumulator
+// of each term is known at compile time).  Weights come precomputed per
+// sorted atom (BinArgs::aw).  Each point sums its atoms in a fixed order
+// (y rows, then z rows, then slots) whatever the launch shape: no atomics.
+constexpr int AN_X = 16, AN_Y = 8, AN_Z = 8;
 
 template <typename T>
-__device__ __forceinline__ void anterp_weights(const vec4<T> f, T wx[4], T wy[4], T wz[4])
+__global__ void __launch_bounds__(AN_X * AN_Y) k_anterp(const AnterpArgs<T> A)
 {
-    phi_weights(f.x, wx);
-    phi_weights(f.y, wy);
-    phi_weights(f.z, wz);
-#pragma unroll
-    for (int o = 0; o < 4; o++) wx[o] *= f.w;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(AT_THREADS) k_anterp(const AnterpArgs<T> A)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AnterpSmem<T> &S = *reinterpret_cast<AnterpSmem<T> *>(smem_raw);
-    __shared__ int s_total;
     if (failed(A.status)) return;
     const SysDesc &D = A.bt.sd[blockIdx.y];
     const LevelGeom &L = D.gg.L[0];
-    const int ntx = (L.n[0] + AT_X - 1) / AT_X, nty = (L.n[1] + AT_Y - 1) / AT_Y, ntz = (L.n[2] + AT_Z - 1) / AT_Z;
+    const int ntx = (L.n[0] + AN_X - 1) / AN_X, nty = (L.n[1] + AN_Y - 1) / AN_Y, ntz = (L.n[2] + AN_Z - 1) / AN_Z;
     if ((int)blockIdx.x >= ntx * nty * ntz) return;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
+    const int ix = bx * AN_X + threadIdx.x % AN_X, iy = by * AN_Y + threadIdx.x / AN_X, iz0 = bz * AN_Z;
+    if (ix >= L.n[0] || iy >= L.n[1]) return;
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
+    const int mx = L.lo[0] + ix, my = L.lo[1] + iy, mz0 = L.lo[2] + iz0;
     const int *__restrict__ start = A.start + D.cell_off;
-    // absolute index of the tile's first point; cell block origin = that - 2
-    const int m0x = L.lo[0] + bx * AT_X, m0y = L.lo[1] + by * AT_Y, m0z = L.lo[2] + bz * AT_Z;
-    const int c0x = m0x - 2, c0y = m0y - 2, c0z = m0z - 2;
-    const int t = threadIdx.x;
-
-    // cell counts of the block (cells outside the grid count 0), exclusive scan
-    for (int e = t; e < AC_N; e += AT_THREADS) {
-        const int lx = e % AC_X, ly = (e / AC_X) % AC_Y, lz = e / (AC_X * AC_Y);
-        const int cx = c0x + lx, cy = c0y + ly, cz = c0z + lz;
-        int c = 0;
-        if (cx >= 0 && cx < nx && cy >= 0 && cy < ny && cz >= 0 && cz < nz) {
-            const int cell = (cz * ny + cy) * nx + cx;
-            c = start[cell + 1] - start[cell];
-        }
-        S.cell_off[e + 1] = c;
-    }
-    __syncthreads();
-    {
-        // inclusive prefix sum of the counts in place (cell_off[e] becomes the first
-        // staged atom of cell e): AT_PER consecutive cells per thread, then a block scan
-        constexpr int AT_PER = (AC_N + AT_THREADS - 1) / AT_THREADS;
-        __shared__ int ws[AT_THREADS / 32];
-        int loc[AT_PER], sum = 0;
+    const vec4<T> *__restrict__ wxq = A.aw;
+    const T *__restrict__ wy = &A.aw[A.n_total].x;
+    const vec4<T> *__restrict__ wz = A.aw + 2 * (size_t)A.n_total;
+    int xc[5];                                    // cells mu_x - 2 .. mu_x + 2 clamped to [0, nx]
 #pragma unroll
-        for (int k = 0; k < AT_PER; k++) {
-            const int e = t * AT_PER + k;
-            loc[k] = e < AC_N ? S.cell_off[e + 1] : 0;
-            sum += loc[k];
-        }
-        const int lane = t & 31, w = t >> 5;
-        int inc = sum;
+    for (int k = 0; k < 5; k++) xc[k] = min(max(mx - 2 + k, 0), nx);
+    T acc[AN_Z];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) ws[w] = inc;
-        __syncthreads();
-        int wbase = 0;
-        for (int k = 0; k < w; k++) wbase += ws[k];
-        int run = wbase + inc - sum;                       // exclusive prefix of this thread's cells
+    for (int p = 0; p < AN_Z; p++) acc[p] = T(0);
+#pragma unroll 1
+    for (int oy = 0; oy < 4; oy++) {
+        const int cy = my + 1 - oy;
+        if (cy < 0 || cy >= ny) continue;
 #pragma unroll
-        for (int k = 0; k < AT_PER; k++) {
-            const int e = t * AT_PER + k;
-            run += loc[k];
-            if (e < AC_N) S.cell_off[e + 1] = run;
-        }
-        if (t == 0) S.cell_off[0] = 0;
-        if (t == AT_THREADS - 1) s_total = run;
-    }
-    __syncthreads();
-    const bool staged = s_total <= AT_CAP;
-    if (staged) {
-        for (int e = t; e < AC_N; e += AT_THREADS) {
-            const int lx = e % AC_X, ly = (e / AC_X) % AC_Y, lz = e / (AC_X * AC_Y);
-            const int cx = c0x + lx, cy = c0y + ly, cz = c0z + lz;
-            if (cx < 0 || cx >= nx || cy < 0 || cy >= ny || cz < 0 || cz >= nz) continue;
-            const int cell = (cz * ny + cy) * nx + cx;
-            const int g0 = start[cell], g1 = start[cell + 1];
-            for (int g = g0, k = S.cell_off[e]; g < g1; g++, k++) {
-                T wx[4], wy[4], wz[4];
-                anterp_weights(A.afrac[g], wx, wy, wz);
-#pragma unroll
-                for (int o = 0; o < 4; o++) { S.w[o][k] = wx[o]; S.w[4 + o][k] = wy[o]; S.w[8 + o][k] = wz[o]; }
+        for (int rz = 0; rz < AN_Z + 3; rz++) {
+            const int cz = mz0 - 2 + rz;
+            if (cz < 0 || cz >= nz) continue;
+            const int rb = (cz * ny + cy) * nx;
+            const int b0 = start[rb + xc[0]], b1 = start[rb + xc[1]], b2 = start[rb + xc[2]];
+            const int b3 = start[rb + xc[3]], b4 = start[rb + xc[4]];
+            for (int s = b0; s < b4; s++) {
+                const int ox = 3 - (s >= b1) - (s >= b2) - (s >= b3);
+                const T t = (&wxq[s].x)[ox] * wy[4 * (size_t)s + oy];
+                const vec4<T> z = wz[s];
+                // the point rz - 3 + Oz takes weight wz[Oz]
+                if (rz - 3 >= 0 && rz - 3 < AN_Z) acc[rz - 3 >= 0 ? rz - 3 : 0] += t * z.x;
+                if (rz - 2 >= 0 && rz - 2 < AN_Z) acc[rz - 2 >= 0 ? rz - 2 : 0] += t * z.y;
+                if (rz - 1 >= 0 && rz - 1 < AN_Z) acc[rz - 1 >= 0 ? rz - 1 : 0] += t * z.z;
+                if (rz < AN_Z) acc[rz < AN_Z ? rz : 0] += t * z.w;
             }
         }
     }
-    __syncthreads();
-
-    const int ix = bx * AT_X + t % AT_X, iy = by * AT_Y + (t / AT_X) % AT_Y, iz = bz * AT_Z + t / (AT_X * AT_Y);
-    if (ix >= L.n[0] || iy >= L.n[1] || iz >= L.n[2]) return;
-    const int mx = L.lo[0] + ix, my = L.lo[1] + iy, mz = L.lo[2] + iz;
-    T acc = 0;
-    // point mu receives weight index O = mu - c + 1 from an atom in cell c
-    // runtime loops: the unrolled 64-cell body does not fit the instruction cache
-#pragma unroll 1
-    for (int oz = 0; oz < 4; oz++) {
-        const int cz = mz + 1 - oz;
-        if (cz < 0 || cz >= nz) continue;
-#pragma unroll 1
-        for (int oy = 0; oy < 4; oy++) {
-            const int cy = my + 1 - oy;
-            if (cy < 0 || cy >= ny) continue;
-#pragma unroll 1
-            for (int ox = 0; ox < 4; ox++) {
-                const int cx = mx + 1 - ox;
-                if (cx < 0 || cx >= nx) continue;
-                if (staged) {
-                    const int e = ((cz - c0z) * AC_Y + (cy - c0y)) * AC_X + (cx - c0x);
-                    for (int k = S.cell_off[e]; k < S.cell_off[e + 1]; k++)
-                        acc += (S.w[ox][k] * S.w[4 + oy][k]) * S.w[8 + oz][k];
-                } else {
-                    const int cell = (cz * ny + cy) * nx + cx;
-                    for (int g = start[cell]; g < start[cell + 1]; g++) {
-                        T wx[4], wy[4], wz[4];
-                        anterp_weights(A.afrac[g], wx, wy, wz);
-                        acc += (wx[ox] * wy[oy]) * wz[oz];
-                    }
-                }
-            }
-        }
-    }
-    A.q[D.grid_off + L.off + (iz * L.n[1] + iy) * L.n[0] + ix] = acc;
-}
-
-int anterp_tiles(const LevelGeom &L)
-{
-    return ((L.n[0] + AT_X - 1) / AT_X) * ((L.n[1] + AT_Y - 1) / AT_Y) * ((L.n[2] + AT_Z - 1) / AT_Z);
+    T *out = A.q + D.grid_off + L.off + ((size_t)iz0 * L.n[1] + iy) * L.n[0] + ix;
+    const size_t plane = (size_t)L.n[1] * L.n[0];
+#pragma unroll
+    for (int p = 0; p < AN_Z; p++)
+        if (iz0 + p < L.n[2]) out[p * plane] = acc[p];
 }
 
 template <typename T>
 int launch_anterp(const AnterpArgs<T> &a, cudaStream_t st)
 {
     if (a.max_tiles <= 0) return MSM_OK;
-    const size_t smem = anterp_smem_bytes<T>();
-    CUDA_TRY(cudaFuncSetAttribute(k_anterp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_anterp<T><<<dim3(a.max_tiles, a.bt.B), AT_THREADS, smem, st>>>(a);
+    k_anterp<T><<<dim3(a.max_tiles, a.bt.B), AN_X * AN_Y, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
+}
+
+int anterp_tiles(const LevelGeom &L)
+{
+    return ((L.n[0] + AN_X - 1) / AN_X) * ((L.n[1] + AN_Y - 1) / AN_Y) * ((L.n[2] + AN_Z - 1) / AN_Z);
 }
 
 // ------------------------------------------------------------------ restriction

@@ -36,6 +36,8 @@ template <typename T> struct BinArgs {
     int *akey;             // sorted global cell id
     int *aflag;            // sorted (molecule id << 1) | LJ flag; molecule id = global
                            // index of the molecule's first atom (single sites: own index)
+    vec4<T> *aw;           // sorted anterpolation weights, 3 n_total: [0, n) q wx[0..3],
+                           // [n, 2n) wy[0..3], [2n, 3n) wz[0..3]
     int *status;
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
@@ -114,8 +116,9 @@ template <typename T> int launch_list_force(const ListArgs<T> &a, cudaStream_t s
 template <typename T> struct AnterpArgs {
     Batch bt;
     int max_tiles;         // anterpolation tiles of the largest level-0 grid
+    int n_total;           // atoms over all systems (stride of the weight records)
     const int *start;      // global cell_start
-    const vec4<T> *afrac;
+    const vec4<T> *aw;     // sorted weight records (BinArgs::aw)
     T *q;                  // concatenated grids
     const int *status;
 };

@@ -171,7 +171,7 @@ struct msm_handle {
     bool stencil_ready = false;
     StencilGeom sg;
     // scratch
-    DevBuf key, count, start, perm, bsum, rel, frac, apos, afrac, akey, aflag, sr, lj;
+    DevBuf key, count, start, perm, bsum, rel, frac, apos, afrac, akey, aflag, aw, sr, lj;
     DevBuf lj_count, lj_start, lj_apos, lj_flag, lj_perm;      // LJ-site cell list (water completion)
     DevBuf qgrid, ucut, ugrid, utop, ttop, wst_d, wst_t, rows;
     DevBuf eatom, vatom, kin, partials, sums, kin_s, status, ctr;
@@ -312,7 +312,7 @@ extern "C" void msm_destroy(msm_handle *h)
 {
     if (!h) return;
     DevBuf *all[] = {&h->key, &h->count, &h->start, &h->perm, &h->bsum, &h->rel, &h->frac, &h->apos, &h->afrac,
-                     &h->akey, &h->aflag, &h->sr, &h->lj, &h->lj_count, &h->lj_start, &h->lj_apos, &h->lj_flag,
+                     &h->aw, &h->akey, &h->aflag, &h->sr, &h->lj, &h->lj_count, &h->lj_start, &h->lj_apos, &h->lj_flag,
                      &h->lj_perm, &h->qgrid, &h->ucut, &h->ugrid, &h->utop, &h->ttop,
                      &h->wst_d, &h->wst_t, &h->rows, &h->eatom, &h->vatom, &h->kin, &h->partials, &h->sums,
                      &h->kin_s, &h->status, &h->ctr, &h->sd_buf, &h->blk_buf,
@@ -611,6 +611,7 @@ static int ensure_atoms(msm_handle *h, int64_t n)
     TRY(ensure(h->frac, 4 * ts * nn));
     TRY(ensure(h->apos, 4 * ts * nn));
     TRY(ensure(h->afrac, 4 * ts * nn));
+    TRY(ensure(h->aw, 12 * ts * nn));
     TRY(ensure(h->sr, 4 * ts * nn));
     if (h->p.model == MSM_MODEL_WATER) {
         TRY(ensure(h->lj, 4 * ts * nn));
@@ -724,7 +725,7 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     b.key = h->key.as<int>(); b.count = h->count.as<int>(); b.start = h->start.as<int>(); b.perm = h->perm.as<int>();
     b.bsum = h->bsum.as<int>(); b.rel = h->rel.as<vec4<T>>(); b.frac = h->frac.as<vec4<T>>();
     b.apos = h->apos.as<vec4<T>>(); b.afrac = h->afrac.as<vec4<T>>(); b.akey = h->akey.as<int>();
-    b.aflag = h->aflag.as<int>(); b.status = status;
+    b.aflag = h->aflag.as<int>(); b.aw = h->aw.as<vec4<T>>(); b.status = status;
     { PROF(ST_BIN); TRY(launch_bin<T>(b, st)); }
     if (h->tune_pending) TRY(autotune_bricks<T>(h, st));
 
@@ -781,7 +782,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     // step 2: anterpolation
     T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
     AnterpArgs<T> an;
-    an.bt = bt; an.max_tiles = h->max_atiles; an.start = h->start.as<int>(); an.afrac = h->afrac.as<vec4<T>>();
+    an.bt = bt; an.max_tiles = h->max_atiles; an.n_total = (int)h->N; an.start = h->start.as<int>();
+    an.aw = h->aw.as<vec4<T>>();
     an.q = qg; an.status = status;
     { PROF(ST_ANTERP); TRY(launch_anterp<T>(an, st)); }
 
