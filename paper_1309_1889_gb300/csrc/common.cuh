@@ -54,6 +54,17 @@ __device__ __forceinline__ double f64_of(float f)
     if (e == 255u) hi |= 0x7ff00000u;
     return __longlong_as_double((long long)(((unsigned long long)(hi | (u & 0x80000000u)) << 32) | lo));
 }
+// 1/sqrt(x) from the hardware approximation (PTX rsqrt.approx.ftz.f32: relative
+// error below 2^-22.9), without the extra instructions the non-FTZ rsqrtf adds
+// for subnormal x.  The pair kernels call it only on r^2 + 1e-12, never below
+// the normal range.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // T from / to the FP64 state: the integer-pipe conversions for T = float, the
 // identity for T = double.
 template <typename T> __device__ __forceinline__ T to_t(double x);

@@ -44,7 +44,7 @@ __device__ __forceinline__ bool vl_rebuild(const int *ctl) { return ctl[3] != 0;
 __device__ __forceinline__ bool vl_usable(const int *ctl) { return ctl[1] == 0 && ctl[2] == 0; }
 
 template <typename T> __device__ __forceinline__ T vl_rsqrt(T x);
-template <> __device__ __forceinline__ float vl_rsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ float vl_rsqrt<float>(float x) { return rsqrt_ftz(x); }
 template <> __device__ __forceinline__ double vl_rsqrt<double>(double x) { return rsqrt(x); }
 // added to r^2 through the FMA chain: keeps rsqrt finite for masked entries
 template <typename T> __device__ __forceinline__ T vl_eps();

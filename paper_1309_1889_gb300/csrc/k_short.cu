@@ -40,7 +40,7 @@ constexpr int SR_WARPS = 4;
 constexpr int SR_MAXROWS = 320;     // row-list capacity per warp (a segment)
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrt_ftz(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 template <typename T> __device__ __forceinline__ T big_t();
 template <> __device__ __forceinline__ float big_t<float>() { return 1e30f; }
