@@ -1,6 +1,6 @@
 // k_grid.cu -- the long-range steps of the MSM (Sec. 3):
 //   k_anterp       q^0_mu = sum_j phi^0_mu(r_j) q_j, one thread per column of
-//                  8 grid points gathering the atoms of the cells their basis
+//                  4 grid points gathering the atoms of the cells their basis
 //                  functions touch (cells mu-2 .. mu+1 per axis): no atomics
 //   k_restrict     q^{k+1}_mu = sum_nu Phi(nu/2 - mu)^{x3} q^k_nu: taps at
 //                  nu - 2mu in {-3,-1,0,1,3} with weights {-1,9,16,9,-1}/16
@@ -39,7 +39,7 @@ namespace msm {
 // of each term is known at compile time).  Weights come precomputed per
 // sorted atom (BinArgs::aw).  Each point sums its atoms in a fixed order
 // (y rows, then z rows, then slots) whatever the launch shape: no atomics.
-constexpr int AN_X = 16, AN_Y = 8, AN_Z = 8;
+constexpr int AN_X = 16, AN_Y = 8, AN_Z = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(AN_X * AN_Y) k_anterp(const AnterpArgs<T> A)

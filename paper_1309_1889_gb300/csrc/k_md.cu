@@ -172,15 +172,107 @@ int launch_sum(const Batch &bt, int max_n, int total_blocks, int ncols, const do
 __device__ __forceinline__ constexpr int bond_i(int c) { return c == 2 ? 1 : 0; }
 __device__ __forceinline__ constexpr int bond_j(int c) { return c == 0 ? 1 : 2; }
 
+// One thread per molecule (or single site), VV_T per CTA.  The CTA's molecules
+// are 9 consecutive doubles each in x, v and f: they are staged through shared
+// memory with coalesced loads and stores (a thread reading its own 9 values
+// from global memory touches 18 cache lines per warp-wide load).
+constexpr int VV_T = 128;
+
 template <typename T>
-__global__ void k_vv_first(const VVArgs A)
+__global__ void __launch_bounds__(VV_T) k_vv_first(const VVArgs A)
 {
+    __shared__ double sx[VV_T * 9], sv[VV_T * 9], sf[VV_T * 9];
+    __shared__ int s_failed;
     const SysDesc &D = A.bt.sd[blockIdx.y];
     const int units = D.n_mol + (D.n - 3 * D.n_mol);
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= units || failed(A.status)) return;
+    const int u0 = blockIdx.x * VV_T;
+    if (u0 >= units) return;
+    if (threadIdx.x == 0) s_failed = failed(A.status);
+    __syncthreads();
+    if (s_failed) return;
+    const int u = u0 + threadIdx.x;
     const double dt = A.dt;
-    if (u >= D.n_mol) {                                 // single site: half kick, drift
+    const int nmb = max(0, min(VV_T, D.n_mol - u0));              // molecules of this CTA
+    const size_t g0 = 3 * ((size_t)D.atom_off + 3 * (size_t)u0);   // their first double
+    for (int e = threadIdx.x; e < 9 * nmb; e += VV_T) {
+        const double x = A.x[g0 + e];
+        sx[e] = x;
+        A.xo[g0 + e] = x;                                          // positions before the drift
+        sv[e] = A.v[g0 + e];
+        sf[e] = A.f[g0 + e];
+    }
+    __syncthreads();
+    if (u < D.n_mol) {
+        // The state stays FP64; what a step adds to it (half kick, drift, SHAKE
+        // correction) is formed in T in molecule-local coordinates (relative to
+        // the old O position), so x and v take one FP64 add per component.
+        // GB300 runs FP64 instructions at 1/64 of the FP32 rate: the conversions
+        // use the integer pipe, and no FP64 value is kept live across the SHAKE
+        // loop (holding 18 doubles through it cost ~11 FP64-pipe instructions per
+        // iteration); the state is read again from shared memory after it.
+        const int b = 9 * threadIdx.x, i0 = D.atom_off + 3 * u;
+        const T tdt = (T)dt, hk = (T)(0.5 * dt), inv_dt = T(1) / tdt;
+        T p[3][3], p0[3][3], ro[3][3], w[3], d2[3];
+        {
+            T rel[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                w[a] = to_t<T>(A.im[i0 + a]);
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const int k = b + 3 * a + d;
+                    rel[a][d] = a ? to_t<T>(sx[k] - sx[b + d]) : T(0);
+                    const T dv = hk * to_t<T>(sf[k]) * w[a];                          // half kick
+                    p0[a][d] = p[a][d] = rel[a][d] + tdt * (to_t<T>(sv[k]) + dv);    // drift
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int d = 0; d < 3; d++) ro[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
+        }
+        // SHAKE on the drifted local positions p; the old bond vectors ro give the directions
+        d2[0] = d2[1] = (T)A.d_oh2;
+        d2[2] = (T)A.d_hh2;
+        const T tol = (T)A.tol;
+        bool ok = false;
+        for (int it = 0; it < A.max_iter && !ok; it++) {
+            ok = true;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const int a = bond_i(c), bb = bond_j(c);
+                T rn[3], rn2 = 0, dot = 0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) { rn[d] = p[a][d] - p[bb][d]; rn2 += rn[d] * rn[d]; }
+                const T diff = d2[c] - rn2;
+                if ((diff < T(0) ? -diff : diff) > tol * d2[c]) {
+                    ok = false;
+#pragma unroll
+                    for (int d = 0; d < 3; d++) dot += ro[c][d] * rn[d];
+                    const T g = diff / (T(2) * dot * (w[a] + w[bb]));
+#pragma unroll
+                    for (int d = 0; d < 3; d++) { p[a][d] += g * w[a] * ro[c][d]; p[bb][d] -= g * w[bb] * ro[c][d]; }
+                }
+            }
+        }
+        if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 1); atomicCAS(A.status + 3, 0, i0 + 1); }
+        // x = x_old + (drift + dp), v = v_old + (kick + dp / dt): the same kick and
+        // drift arithmetic as above, on values read again (volatile: the compiler
+        // would otherwise keep the first reads live through the loop)
+        const volatile double *vx = sx, *vv = sv, *vf = sf;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const int k = b + 3 * a + d;
+                const double x = vx[k], v = vv[k];
+                const T dv = hk * to_t<T>(vf[k]) * w[a];
+                const T sd = tdt * (to_t<T>(v) + dv);
+                const T dp = p[a][d] - p0[a][d];
+                sx[k] = x + to_d(sd + dp);
+                sv[k] = v + to_d(dv + dp * inv_dt);
+            }
+    } else if (u < units) {                                        // single site: half kick, drift
         const int i = D.atom_off + 3 * D.n_mol + (u - D.n_mol);
         const double im = A.im[i];
 #pragma unroll
@@ -191,87 +283,107 @@ __global__ void k_vv_first(const VVArgs A)
             A.x[3 * i + d] = x + dt * v;
             A.v[3 * i + d] = v;
         }
-        return;
     }
-    // The state stays FP64; what a step adds to it (half kick, drift, SHAKE
-    // correction) is formed in T in molecule-local coordinates (relative to the
-    // old O position), so x and v take one FP64 add per component.  GB300 runs
-    // FP64 instructions at 1/64 of the FP32 rate: the conversions use the
-    // integer pipe, and no FP64 value is kept live across the SHAKE loop (the
-    // state is read again after it; holding 18 doubles through the loop cost
-    // ~11 FP64-pipe instructions per iteration).
-    const int i0 = D.atom_off + 3 * u;
-    const T tdt = (T)dt, hk = (T)(0.5 * dt), inv_dt = T(1) / tdt;
-    T p[3][3], p0[3][3], ro[3][3], w[3], d2[3];
-    {
-        T rel[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            w[a] = to_t<T>(A.im[i0 + a]);
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const double x = A.x[3 * (i0 + a) + d];
-                rel[a][d] = a ? to_t<T>(x - A.x[3 * i0 + d]) : T(0);
-                const T dv = hk * to_t<T>(A.f[3 * (i0 + a) + d]) * w[a];          // half kick
-                p0[a][d] = p[a][d] = rel[a][d] + tdt * (to_t<T>(A.v[3 * (i0 + a) + d]) + dv);   // drift
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-#pragma unroll
-            for (int d = 0; d < 3; d++) ro[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 9 * nmb; e += VV_T) {
+        A.x[g0 + e] = sx[e];
+        A.v[g0 + e] = sv[e];
     }
-    // SHAKE on the drifted local positions p; the old bond vectors ro give the directions
-    d2[0] = d2[1] = (T)A.d_oh2;
-    d2[2] = (T)A.d_hh2;
-    const T tol = (T)A.tol;
-    bool ok = false;
-    for (int it = 0; it < A.max_iter && !ok; it++) {
-        ok = true;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int a = bond_i(c), b = bond_j(c);
-            T rn[3], rn2 = 0, dot = 0;
-#pragma unroll
-            for (int d = 0; d < 3; d++) { rn[d] = p[a][d] - p[b][d]; rn2 += rn[d] * rn[d]; }
-            const T diff = d2[c] - rn2;
-            if ((diff < T(0) ? -diff : diff) > tol * d2[c]) {
-                ok = false;
-#pragma unroll
-                for (int d = 0; d < 3; d++) dot += ro[c][d] * rn[d];
-                const T g = diff / (T(2) * dot * (w[a] + w[b]));
-#pragma unroll
-                for (int d = 0; d < 3; d++) { p[a][d] += g * w[a] * ro[c][d]; p[b][d] -= g * w[b] * ro[c][d]; }
-            }
-        }
-    }
-    if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 1); atomicCAS(A.status + 3, 0, i0 + 1); }
-    // x = x_old + (drift + dp), v = v_old + (kick + dp / dt): the same kick and drift
-    // arithmetic as above, on the state read again
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const int k = 3 * (i0 + a) + d;
-            const double x = A.x[k], v = A.v[k];
-            const T dv = hk * to_t<T>(A.f[k]) * w[a];
-            const T sd = tdt * (to_t<T>(v) + dv);
-            const T dp = p[a][d] - p0[a][d];
-            A.xo[k] = x;
-            A.x[k] = x + to_d(sd + dp);
-            A.v[k] = v + to_d(dv + dp * inv_dt);
-        }
 }
 
 template <typename T>
-__global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
+__global__ void __launch_bounds__(VV_T) k_vv_second(const VVArgs A, double *__restrict__ kin)
 {
+    __shared__ double sx[VV_T * 9], sv[VV_T * 9], sf[VV_T * 9];
+    __shared__ int s_failed;
     const SysDesc &D = A.bt.sd[blockIdx.y];
     const int units = D.n_mol + (D.n - 3 * D.n_mol);
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= units || failed(A.status)) return;
+    const int u0 = blockIdx.x * VV_T;
+    if (u0 >= units) return;
+    if (threadIdx.x == 0) s_failed = failed(A.status);
+    __syncthreads();
+    if (s_failed) return;
+    const int u = u0 + threadIdx.x;
     const double hdt = 0.5 * A.dt;
-    if (u >= D.n_mol) {
+    const int nmb = max(0, min(VV_T, D.n_mol - u0));
+    const size_t g0 = 3 * ((size_t)D.atom_off + 3 * (size_t)u0);
+    for (int e = threadIdx.x; e < 9 * nmb; e += VV_T) {
+        sx[e] = A.x[g0 + e];
+        sv[e] = A.v[g0 + e];
+        sf[e] = A.f[g0 + e];
+    }
+    __syncthreads();
+    if (u < D.n_mol) {
+        // as in k_vv_first: the kick and the RATTLE correction form one increment
+        // in T, integer-pipe conversions, no FP64 value live across the loop
+        const int b = 9 * threadIdx.x, i0 = D.atom_off + 3 * u;
+        const T hk = (T)hdt;
+        T r[3][3], r2[3], wv[3][3], wm[3];
+        {
+            T rel[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                wm[a] = to_t<T>(A.im[i0 + a]);
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const int k = b + 3 * a + d;
+                    wv[a][d] = to_t<T>(sv[k]) + hk * to_t<T>(sf[k]) * wm[a];
+                    rel[a][d] = a ? to_t<T>(sx[k] - sx[b + d]) : T(0);
+                }
+            }
+            // RATTLE velocity stage: zero the bond-parallel relative velocities
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                r2[c] = 0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    r[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
+                    r2[c] += r[c][d] * r[c][d];
+                }
+            }
+        }
+        const T tol = (T)A.tol_v;
+        bool ok = false;
+        for (int it = 0; it < A.max_iter && !ok; it++) {
+            ok = true;
+            // FP64: |rv| <= tol (absolute, as the oracle).  FP32: |rv| <= tol |r| (|v_a| + |v_b|):
+            // the rounding of rv = r.(v_a - v_b) grows with the atoms' speeds (not with their
+            // difference, which can be tiny), so an absolute or |v_a - v_b|-relative test can stall
+            T spd[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                spd[a] = sizeof(T) == 4 ? sqrt(wv[a][0] * wv[a][0] + wv[a][1] * wv[a][1] + wv[a][2] * wv[a][2]) : T(0);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const int a = bond_i(c), bb = bond_j(c);
+                T rv = 0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) rv += r[c][d] * (wv[a][d] - wv[bb][d]);
+                const T lim = sizeof(T) == 4 ? tol * sqrt(r2[c]) * (spd[a] + spd[bb]) : tol;
+                if ((rv < T(0) ? -rv : rv) > lim) {
+                    ok = false;
+                    const T k = rv / (r2[c] * (wm[a] + wm[bb]));
+#pragma unroll
+                    for (int d = 0; d < 3; d++) { wv[a][d] -= k * wm[a] * r[c][d]; wv[bb][d] += k * wm[bb] * r[c][d]; }
+                }
+            }
+        }
+        if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 2); atomicCAS(A.status + 3, 0, i0 + 1); }
+        const volatile double *vv = sv;            // read again, not kept through the loop
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double k2 = 0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const int k = b + 3 * a + d;
+                const double v = vv[k];
+                const double vv = v + to_d(wv[a][d] - to_t<T>(v));
+                sv[k] = vv;
+                k2 += vv * vv;
+            }
+            if (kin) kin[i0 + a] = 0.5 * A.m[i0 + a] * k2;
+        }
+    } else if (u < units) {
         const int i = D.atom_off + 3 * D.n_mol + (u - D.n_mol);
         const double m = A.m[i], im = A.im[i];
         double k2 = 0;
@@ -282,82 +394,16 @@ __global__ void k_vv_second(const VVArgs A, double *__restrict__ kin)
             k2 += v * v;
         }
         if (kin) kin[i] = 0.5 * m * k2;
-        return;
     }
-    // as in k_vv_first: the kick and the RATTLE correction form one increment in
-    // T, integer-pipe conversions, and no FP64 value lives across the loop
-    const int i0 = D.atom_off + 3 * u;
-    const T hk = (T)hdt;
-    T r[3][3], r2[3], wv[3][3], wm[3];
-    {
-        T rel[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            wm[a] = to_t<T>(A.im[i0 + a]);
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                wv[a][d] = to_t<T>(A.v[3 * (i0 + a) + d]) + hk * to_t<T>(A.f[3 * (i0 + a) + d]) * wm[a];
-                rel[a][d] = a ? to_t<T>(A.x[3 * (i0 + a) + d] - A.x[3 * i0 + d]) : T(0);
-            }
-        }
-        // RATTLE velocity stage: zero the bond-parallel relative velocities
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            r2[c] = 0;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                r[c][d] = rel[bond_i(c)][d] - rel[bond_j(c)][d];
-                r2[c] += r[c][d] * r[c][d];
-            }
-        }
-    }
-    const T tol = (T)A.tol_v;
-    bool ok = false;
-    for (int it = 0; it < A.max_iter && !ok; it++) {
-        ok = true;
-        // FP64: |rv| <= tol (absolute, as the oracle).  FP32: |rv| <= tol |r| (|v_a| + |v_b|):
-        // the rounding of rv = r.(v_a - v_b) grows with the atoms' speeds (not with their
-        // difference, which can be tiny), so an absolute or |v_a - v_b|-relative test can stall
-        T spd[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            spd[a] = sizeof(T) == 4 ? sqrt(wv[a][0] * wv[a][0] + wv[a][1] * wv[a][1] + wv[a][2] * wv[a][2]) : T(0);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const int a = bond_i(c), b = bond_j(c);
-            T rv = 0;
-#pragma unroll
-            for (int d = 0; d < 3; d++) rv += r[c][d] * (wv[a][d] - wv[b][d]);
-            const T lim = sizeof(T) == 4 ? tol * sqrt(r2[c]) * (spd[a] + spd[b]) : tol;
-            if ((rv < T(0) ? -rv : rv) > lim) {
-                ok = false;
-                const T k = rv / (r2[c] * (wm[a] + wm[b]));
-#pragma unroll
-                for (int d = 0; d < 3; d++) { wv[a][d] -= k * wm[a] * r[c][d]; wv[b][d] += k * wm[b] * r[c][d]; }
-            }
-        }
-    }
-    if (!ok) { set_status(A.status, MSM_ENOCONV); atomicCAS(A.status + 1, 0, 2); atomicCAS(A.status + 3, 0, i0 + 1); }
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const int i = i0 + a;
-        double k2 = 0;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const double v = A.v[3 * i + d];
-            const double vv = v + to_d(wv[a][d] - to_t<T>(v));
-            A.v[3 * i + d] = vv;
-            k2 += vv * vv;
-        }
-        if (kin) kin[i] = 0.5 * A.m[i] * k2;
-    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 9 * nmb; e += VV_T) A.v[g0 + e] = sv[e];
 }
 
 template <typename T>
 int launch_vv_first(const VVArgs &a, cudaStream_t st)
 {
     if (a.max_units <= 0) return MSM_OK;
-    k_vv_first<T><<<dim3((a.max_units + 127) / 128, a.bt.B), 128, 0, st>>>(a);
+    k_vv_first<T><<<dim3((a.max_units + VV_T - 1) / VV_T, a.bt.B), VV_T, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -367,7 +413,7 @@ template <typename T>
 int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st)
 {
     if (a.max_units <= 0) return MSM_OK;
-    k_vv_second<T><<<dim3((a.max_units + 127) / 128, a.bt.B), 128, 0, st>>>(a, kin_atom);
+    k_vv_second<T><<<dim3((a.max_units + VV_T - 1) / VV_T, a.bt.B), VV_T, 0, st>>>(a, kin_atom);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
