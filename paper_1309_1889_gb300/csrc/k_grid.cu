@@ -198,39 +198,60 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
     return MSM_OK;
 }
 
-// Lattice cutoff, all levels 0..l-2 in one persistent launch.  A tile is
-// ST_TX x ST_TY x ST_TZ outputs of one level; each thread owns ST_RX outputs
-// along x times ST_RZ along z in registers.  The tile's input planes z' =
-// z0-rad .. z0+ST_TZ-1+rad are streamed through shared memory one at a time
-// (the plane plus an x/y halo of rad points); every plane row (y + dy) is read
-// into registers once and applied to the ST_RZ output planes it reaches
-// (dz = z' - z), walking the tap row (dy, dz) of the sphere with compile-time
-// offsets.  The weights W[n] = g^0(|n| h) depend on |n| only, so one octant of
-// the table sits in shared memory (small enough for many resident CTAs); the
-// level factor 2^{-k} is applied at the end.  CTAs take tiles from a counter.
-constexpr int ST_RX = 4, ST_RZ = 4;
-constexpr int ST_TXT = 8, ST_TYT = 8;                 // threads along x and y
-constexpr int ST_TX = ST_TXT * ST_RX, ST_TY = ST_TYT, ST_TZ = ST_RZ;
-constexpr int ST_THREADS = ST_TXT * ST_TYT;
+// Lattice cutoff, all levels 0..l-2 in one persistent launch.  A thread owns
+// ST_RX outputs along x times ST_RZ along z in registers.  The ST_NT threads of
+// a CTA cover TGX = min(ceil(n_x / ST_RX), ST_MAXGX) groups along x times
+// TYR = ST_NT / TGX rows along y, so a tile spans whole grid rows of short
+// levels (the 98-point level-0 rows of a 23.5 nm box waste 6 % of the
+// threads, fixed 32-point tiles 23 %).  The tile's input planes z' = z0-rad ..
+// z0+ST_RZ-1+rad pass through two shared-memory buffers filled by cp.async
+// (zero outside the grid), the next plane's copy in flight while the current
+// one is used.  Every plane row (y + dy) is read into registers once and
+// applied to the ST_RZ output planes it reaches (dz = z' - z), walking the tap
+// row (dy, dz) of the sphere with compile-time offsets.  The weights
+// W[n] = g^0(|n| h) depend on |n| only, so one octant of the table sits in
+// shared memory; the level factor 2^{-k} is applied at the end.  CTAs take
+// tiles from a counter.  Each output sums its taps in a fixed order (planes,
+// rows, then x offsets), whatever the tile shape.
+constexpr int ST_RX = 8, ST_RZ = 2, ST_NT = 128, ST_MAXGX = 16;
 constexpr int ST_MAXRAD = 12;
+
+struct StTile { int tgx, tyr, ntx, nty, ntz; };
+__host__ __device__ inline StTile st_tile(const LevelGeom &L)
+{
+    StTile t;
+    const int nxg = (L.n[0] + ST_RX - 1) / ST_RX;
+    t.tgx = nxg < ST_MAXGX ? nxg : ST_MAXGX;
+    t.tyr = ST_NT / t.tgx;
+    t.ntx = (nxg + t.tgx - 1) / t.tgx;
+    t.nty = (L.n[1] + t.tyr - 1) / t.tyr;
+    t.ntz = (L.n[2] + ST_RZ - 1) / ST_RZ;
+    return t;
+}
 
 // Plane rows and weight rows are padded to multiples of 4 values so that rows
 // start on 16-byte boundaries and are read four values per load.
 __host__ __device__ constexpr int st_up4(int v) { return (v + 3) & ~3; }
-__host__ __device__ constexpr int st_px(int rad) { return st_up4(ST_TX + 2 * rad); }
-__host__ __device__ constexpr int st_py(int rad) { return ST_TY + 2 * rad; }
 __host__ __device__ constexpr int st_r1p(int rad) { return st_up4(rad + 1); }
+__host__ __device__ inline int st_px(int tgx, int rad) { return st_up4(tgx * ST_RX + 2 * rad); }
+__host__ __device__ inline int st_py(int tgx, int rad) { return ST_NT / tgx + 2 * rad; }
 
 // Shared memory of one CTA: the weight octant W[|dz|][|dy|][|dx|] ((rad+1)^2
-// rows of st_r1p values; the weights depend on |n| only), one input plane with
-// its halo, and the half-widths of the tap rows by (|dz|, |dy|).
-template <typename T> size_t stencil_smem_bytes(int rad)
+// rows of st_r1p values), two plane buffers of `plane` values, and the
+// half-widths of the tap rows by (|dz|, |dy|).
+template <typename T> size_t stencil_smem_bytes(int rad, int plane)
 {
     const size_t r1 = (size_t)rad + 1;
-    return sizeof(T) * (r1 * r1 * (size_t)st_r1p(rad) + (size_t)st_px(rad) * st_py(rad)) + sizeof(int) * (r1 * r1 + 4);
+    return sizeof(T) * (r1 * r1 * (size_t)st_r1p(rad) + 2 * (size_t)plane) + sizeof(int) * (r1 * r1 + 4);
 }
-template size_t stencil_smem_bytes<float>(int);
-template size_t stencil_smem_bytes<double>(int);
+template size_t stencil_smem_bytes<float>(int, int);
+template size_t stencil_smem_bytes<double>(int, int);
+
+int stencil_plane_values(const LevelGeom &L, int rad)
+{
+    const StTile t = st_tile(L);
+    return st_px(t.tgx, rad) * st_py(t.tgx, rad);
+}
 
 // Values of one plane row in registers: ST_RX + 2 RAD used, rounded up to 4.
 template <int RAD> struct StRow { static constexpr int N = st_up4(ST_RX + 2 * RAD); };
@@ -269,28 +290,44 @@ __device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<R
     }
 }
 
-template <typename T, int RAD>
-__global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, int *__restrict__ counter)
+// Asynchronous copy of one value of type T from global to shared memory; with
+// ok = false nothing is read and the destination is zero-filled.
+template <typename T>
+__device__ __forceinline__ void st_copy(T *dst, const T *src, bool ok)
 {
-    constexpr int WD = 2 * RAD + 1, R1 = RAD + 1, R1P = st_r1p(RAD), PX = st_px(RAD), PY = st_py(RAD);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = ok ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void st_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void st_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T, int RAD>
+__global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *__restrict__ counter)
+{
+    constexpr int WD = 2 * RAD + 1, R1 = RAD + 1, R1P = st_r1p(RAD);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int PLANE = A.sg.plane;
     T *wt = reinterpret_cast<T *>(smem_raw);                 // R1 x R1 rows of R1P weights W[|dz|][|dy|][|dx|]
-    T *plane = wt + R1 * R1 * R1P;                           // PY x PX input plane
-    int *hw = reinterpret_cast<int *>(plane + PX * PY);      // R1^2 half widths by (|dz|, |dy|) (-1: empty)
+    T *buf0 = wt + R1 * R1 * R1P;                            // two plane buffers
+    int *hw = reinterpret_cast<int *>(buf0 + 2 * PLANE);     // R1^2 half widths by (|dz|, |dy|) (-1: empty)
     __shared__ int s_tile, s_ent;
     if (failed(A.status)) return;
     const int t = threadIdx.x;
-    for (int e = t; e < R1 * R1 * R1P; e += ST_THREADS) {
+    for (int e = t; e < R1 * R1 * R1P; e += ST_NT) {
         const int ax = e % R1P, ay = (e / R1P) % R1, az = e / (R1P * R1);
         wt[e] = ax < R1 ? A.w[((az + RAD) * WD + (ay + RAD)) * WD + (ax + RAD)] : T(0);
     }
-    for (int e = t; e < R1 * R1; e += ST_THREADS) hw[e] = -1;
+    for (int e = t; e < R1 * R1; e += ST_NT) hw[e] = -1;
     __syncthreads();
-    for (int e = t; e < A.sg.nrows; e += ST_THREADS) {
+    for (int e = t; e < A.sg.nrows; e += ST_NT) {
         const int4 r = A.rows[e];
         if (r.x >= 0 && r.y >= 0) hw[r.y * R1 + r.x] = r.z;
     }
-    const int lx = t % ST_TXT, ly = t / ST_TXT;
     const int total = A.total_tiles, nent = A.bt.B * A.nlev;
     for (;;) {
         __syncthreads();
@@ -311,65 +348,80 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
         const int ent = s_ent, lev = ent % A.nlev;
         const SysDesc &D = A.bt.sd[ent / A.nlev];
         const LevelGeom &L = D.gg.L[lev];
+        const StTile tg = st_tile(L);
+        const int PX = st_px(tg.tgx, RAD), PY = tg.tyr + 2 * RAD;
         const int b = tile - A.blk_off[ent];
-        const int ntx = (L.n[0] + ST_TX - 1) / ST_TX, nty = (L.n[1] + ST_TY - 1) / ST_TY;
-        const int tx = b % ntx, ty = (b / ntx) % nty, tz = b / (ntx * nty);
-        const int x0 = tx * ST_TX, y0 = ty * ST_TY, z0 = tz * ST_TZ;
+        const int tx = b % tg.ntx, ty = (b / tg.ntx) % tg.nty, tz = b / (tg.ntx * tg.nty);
+        const int x0 = tx * tg.tgx * ST_RX, y0 = ty * tg.tyr, z0 = tz * ST_RZ;
+        const int xg = t % tg.tgx, yr = t / tg.tgx;
+        const bool active = yr < tg.tyr;
         const T *__restrict__ q = A.q + D.grid_off + L.off;
+        const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+        // planes that exist: z' in [zb, ze)
+        const int zb = max(z0 - RAD, 0), ze = min(z0 + ST_RZ + RAD, nz);
+        auto fill = [&](int zp, T *dst) {
+            int px = t % PX, py = t / PX;
+            for (int e = t; e < PX * PY; e += ST_NT) {
+                const int gx = x0 + px - RAD, gy = y0 + py - RAD;
+                const bool ok = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+                st_copy(dst + e, ok ? q + ((size_t)zp * ny + gy) * nx + gx : q, ok);
+                px += ST_NT;
+                while (px >= PX) { px -= PX; py++; }
+            }
+            st_commit();
+        };
         T acc[ST_RZ][ST_RX];
 #pragma unroll
         for (int s = 0; s < ST_RZ; s++)
 #pragma unroll
             for (int r = 0; r < ST_RX; r++) acc[s][r] = 0;
-        for (int zp = z0 - RAD; zp < z0 + ST_TZ + RAD; zp++) {
-            const bool zin = zp >= 0 && zp < L.n[2];
+        if (zb < ze) fill(zb, buf0);
+        for (int zp = zb; zp < ze; zp++) {
+            T *cur = buf0 + ((zp - zb) & 1) * PLANE;
+            if (zp + 1 < ze) { fill(zp + 1, buf0 + ((zp + 1 - zb) & 1) * PLANE); st_wait_prev(); }
+            else st_wait_all();
             __syncthreads();
-            for (int e = t; e < PX * PY; e += ST_THREADS) {
-                const int px = e % PX, py = e / PX;
-                const int gx = x0 + px - RAD, gy = y0 + py - RAD;
-                T v = 0;
-                if (zin && gx >= 0 && gx < L.n[0] && gy >= 0 && gy < L.n[1]) v = q[(size_t)(zp * L.n[1] + gy) * L.n[0] + gx];
-                plane[e] = v;
-            }
-            __syncthreads();
-            if (!zin) continue;
+            if (active) {
 #pragma unroll 1
-            for (int dy = -RAD; dy <= RAD; dy++) {
-                constexpr int NV = StRow<RAD>::N;
-                T v[NV];
-                const T *row = plane + (ly + RAD + dy) * PX + lx * ST_RX;    // 16-byte aligned
-                if (sizeof(T) == sizeof(float)) {
+                for (int dy = -RAD; dy <= RAD; dy++) {
+                    constexpr int NV = StRow<RAD>::N;
+                    T v[NV];
+                    const T *row = cur + (yr + RAD + dy) * PX + xg * ST_RX;      // 16-byte aligned
+                    if (sizeof(T) == sizeof(float)) {
 #pragma unroll
-                    for (int i = 0; i < NV; i += 4) {
-                        const float4 f = *reinterpret_cast<const float4 *>(row + i);
-                        v[i] = f.x; v[i + 1] = f.y; v[i + 2] = f.z; v[i + 3] = f.w;
+                        for (int i = 0; i < NV; i += 4) {
+                            const float4 f = *reinterpret_cast<const float4 *>(row + i);
+                            v[i] = f.x; v[i + 1] = f.y; v[i + 2] = f.z; v[i + 3] = f.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NV; i++) v[i] = row[i];
                     }
-                } else {
 #pragma unroll
-                    for (int i = 0; i < NV; i++) v[i] = row[i];
-                }
-#pragma unroll
-                for (int s = 0; s < ST_RZ; s++) {
-                    const int dz = zp - (z0 + s);
-                    if (dz < -RAD || dz > RAD) continue;
-                    const int adz = dz < 0 ? -dz : dz, ady = dy < 0 ? -dy : dy;
-                    const int w = hw[adz * R1 + ady];
-                    if (w < 0) continue;
-                    stencil_row_dispatch<RAD>(w, v, wt + (adz * R1 + ady) * R1P, acc[s]);
+                    for (int s = 0; s < ST_RZ; s++) {
+                        const int dz = zp - (z0 + s);
+                        if (dz < -RAD || dz > RAD) continue;
+                        const int adz = dz < 0 ? -dz : dz, ady = dy < 0 ? -dy : dy;
+                        const int w = hw[adz * R1 + ady];
+                        if (w < 0) continue;
+                        stencil_row_dispatch<RAD>(w, v, wt + (adz * R1 + ady) * R1P, acc[s]);
+                    }
                 }
             }
+            __syncthreads();                          // the buffer is refilled two planes on
         }
         const T scale = (T)ldexp(1.0, -lev);        // g^k = 2^{-k} g^0 at level-k spacing
-        const int gy = y0 + ly;
+        const int gy = y0 + yr;
+        if (active && gy < ny) {
 #pragma unroll
-        for (int s = 0; s < ST_RZ; s++) {
-            const int gz = z0 + s;
-            if (gy < L.n[1] && gz < L.n[2]) {
-                T *out = A.ucut + D.grid_off + L.off + (size_t)(gz * L.n[1] + gy) * L.n[0];
+            for (int s = 0; s < ST_RZ; s++) {
+                const int gz = z0 + s;
+                if (gz >= nz) continue;
+                T *out = A.ucut + D.grid_off + L.off + ((size_t)gz * ny + gy) * nx;
 #pragma unroll
                 for (int r = 0; r < ST_RX; r++) {
-                    const int gx = x0 + lx * ST_RX + r;
-                    if (gx < L.n[0]) out[gx] = scale * acc[s][r];
+                    const int gx = x0 + xg * ST_RX + r;
+                    if (gx < nx) out[gx] = scale * acc[s][r];
                 }
             }
         }
@@ -379,13 +431,13 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil(const StencilArgs<T> A, 
 template <typename T, int RAD>
 static int launch_stencil_rad(const StencilArgs<T> &a, int *counter, int sms, cudaStream_t st)
 {
-    const size_t smem = stencil_smem_bytes<T>(RAD);
+    const size_t smem = stencil_smem_bytes<T>(RAD, a.sg.plane);
     CUDA_TRY(cudaFuncSetAttribute(k_stencil<T, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_THREADS, smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_NT, smem));
     if (per_sm < 1) return fail_msg(MSM_EINVAL, "lattice-cutoff tile does not fit (radius %d)", RAD);
     const int grid = std::min(a.total_tiles, sms * per_sm);
-    k_stencil<T, RAD><<<grid, ST_THREADS, smem, st>>>(a, counter);
+    k_stencil<T, RAD><<<grid, ST_NT, smem, st>>>(a, counter);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -418,7 +470,8 @@ int launch_stencil(const StencilArgs<T> &a, int *counter, cudaStream_t st)
 
 int stencil_tile_count(const LevelGeom &L)
 {
-    return ((L.n[0] + ST_TX - 1) / ST_TX) * ((L.n[1] + ST_TY - 1) / ST_TY) * ((L.n[2] + ST_TZ - 1) / ST_TZ);
+    const StTile t = st_tile(L);
+    return t.ntx * t.nty * t.ntz;
 }
 
 // ------------------------------------------------------------------ top level

@@ -133,6 +133,7 @@ struct StencilGeom {
     int rad;               // max |n_x| of a tap: largest r with r h < 2a
     int wdim;              // 2 rad + 1
     int nrows;             // non-empty (dy, dz) rows
+    int plane;             // values of one shared-memory plane buffer (largest tile of the batch)
 };
 template <typename T> struct StencilArgs {
     Batch bt;
@@ -147,8 +148,9 @@ template <typename T> struct StencilArgs {
     const int *status;
 };
 template <typename T> int launch_stencil(const StencilArgs<T> &a, int *tile_counter, cudaStream_t st);
-template <typename T> size_t stencil_smem_bytes(int rad);
+template <typename T> size_t stencil_smem_bytes(int rad, int plane);
 int stencil_tile_count(const LevelGeom &L);
+int stencil_plane_values(const LevelGeom &L, int rad);   // plane buffer a tile of level L needs
 
 int launch_top_table(const LevelGeom &top, double a_top, double h_top, double *table, cudaStream_t st);
 // utop: per system top_off; max_top = points of the largest top level

@@ -564,6 +564,9 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         CUDA_TRY(cudaStreamSynchronize(st));      // rows lives on the host stack
         h->stencil_ready = true;
     }
+    h->sg.plane = 1;
+    for (const SysDesc &D : d)
+        for (int k = 0; k + 1 < l; k++) h->sg.plane = std::max(h->sg.plane, stencil_plane_values(D.gg.L[k], h->sg.rad));
     h->hsd.swap(d);
     CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, h->hsd.data(), sizeof(SysDesc) * (size_t)B, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->blk_buf.p, h->h_blk.data(), sizeof(int) * h->h_blk.size(), cudaMemcpyHostToDevice, st));
