@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         }
         const bool valid = slot >= 0;
         const vec4<T> pi = valid ? A.apos[slot] : vec4<T>{big_t<T>(), big_t<T>(), big_t<T>(), T(0)};
-        const int fi = ((MODEL || LJP) && valid) ? A.aflag[slot] : -2;
+        const int fi = (MODEL && valid) ? A.aflag[slot] : -2;
 
         // ---- bounding box of the valid i atoms
         T lo[3], hi[3];
@@ -149,18 +149,21 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                 const T r2s = fma(dx, dx, fma(dyy, dyy, fma(dzz, dzz, r2_eps<T>())));
                 bool in = r2s < A.a2;
                 // j = i: the water model's molecule test excludes it (an atom is in its own
-                // molecule); bare charges test the distance
-                if (MODEL || LJP) in = in & ((unsigned)(fi ^ S.sf[wid][q0 + k]) >= 2u);
+                // molecule); bare charges and the LJ pass (whose sites are one per molecule)
+                // test the distance
+                if (MODEL) in = in & ((unsigned)(fi ^ S.sf[wid][q0 + k]) >= 2u);
                 else in = in & (r2s > T(2) * r2_eps<T>());
                 if (COUNT) { npair += in ? 1 : 0; continue; }
                 const T ri = rsqrt_t<T>(r2s);
                 const T ri2 = ri * ri;
                 if (LJP) {
-                    const T m = in ? T(1) : T(0);
-                    const T sr2 = A.lj_s2 * (in ? ri2 : T(0));   // masked pairs (j = i: r^2 = eps) stay finite
-                    const T sr6 = sr2 * sr2 * sr2;
-                    le = fma(m, fma(A.lj_4eps, sr6 * sr6 - sr6, -A.lj_shift), le);
-                    const T fl = m * A.lj_24eps * fma(T(2) * sr6, sr6, -sr6) * ri2;
+                    // masked pairs get sigma^2/r^2 = 0, so every term vanishes; the shift of
+                    // the cut-and-shifted potential is applied once per counted pair at the end
+                    const T sr2 = A.lj_s2 * (in ? ri2 : T(0));
+                    const T sr6 = sr2 * sr2 * sr2, sr12 = sr6 * sr6;
+                    le = fma(A.lj_4eps, sr12 - sr6, le);
+                    npair += in ? 1 : 0;
+                    const T fl = (A.lj_24eps * ri2) * fma(T(2), sr12, -sr6);
                     lx = fma(-fl, dx, lx); ly = fma(-fl, dyy, ly); lz = fma(-fl, dzz, lz);
                     continue;
                 }
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                     }
                     const int js = S.rs0[wid][lo_r] + (want - (lo_r ? S.rend[wid][lo_r - 1] : 0));
                     pj = A.apos[js];
-                    if (MODEL || LJP) fj = A.aflag[js];
+                    if (MODEL) fj = A.aflag[js];
                     const T ex = max(T(0), max(lo[0] - pj.x, pj.x - hi[0]));
                     const T ey = max(T(0), max(lo[1] - pj.y, pj.y - hi[1]));
                     const T ez = max(T(0), max(lo[2] - pj.z, pj.z - hi[2]));
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                 if (keep) {
                     const int q = (head + npend + __popc(m & lt)) & 63;
                     S.sj[wid][q] = pj;
-                    if (MODEL || LJP) S.sf[wid][q] = fj;
+                    if (MODEL) S.sf[wid][q] = fj;
                 }
                 npend += __popc(m);
                 __syncwarp();
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         if (valid) {
             if (COUNT) { A.cnt[slot] = (double)npair; continue; }
             const int atom = A.perm[slot];
-            if (LJP) { A.lj[atom] = vec4<T>{lx, ly, lz, le}; continue; }
+            if (LJP) { A.lj[atom] = vec4<T>{lx, ly, lz, fma(-A.lj_shift, (T)npair, le)}; continue; }
             A.sr[atom] = vec4<T>{-pi.w * ax, -pi.w * ay, -pi.w * az, phi};
             if (MODEL && !(fi & 1)) A.lj[atom] = vec4<T>{T(0), T(0), T(0), T(0)};
         }
