@@ -60,6 +60,8 @@ def args_parse():
     p.add_argument("--profile-steps", type=int, default=30, help="eager profiled steps after the timed region")
     p.add_argument("--batch-steps", type=int, default=100, help="steps of the uneven 7-box batch (0: skip)")
     p.add_argument("--parareal", type=int, default=1, help="run the 10,000-atom parareal leg (0: skip)")
+    p.add_argument("--paper-scale", type=int, default=0,
+                   help="run the 12.7 M-atom leg: one evaluation plus an 8-slice parareal run (1: run)")
     return p.parse_args()
 
 
@@ -290,6 +292,7 @@ def run_ours(a):
 
     batched = run_batch_leg(a, torch, api, inputs, dev) if a.batch_steps > 0 else None
     parareal = run_parareal_leg(a, torch, api, inputs, dev) if a.parareal else None
+    paper_scale = run_paper_scale_leg(a, torch, api, inputs, dev) if a.paper_scale else None
 
     if rank != 0:
         if world > 1:
@@ -335,6 +338,8 @@ def run_ours(a):
         "uneven_batch": batched,
         "parareal": parareal,
     }
+    if paper_scale is not None:
+        line["paper_scale"] = paper_scale
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -432,6 +437,69 @@ def run_parareal_leg(a, torch, api, inputs, dev):
             "serial_fine_s": t_serial, "parareal_s": t_par, "speedup": t_serial / t_par}
     out["note"] = ("speedup = serial fine time / parareal time, both on this one GPU; F of all open slices runs "
                    "as one batch, G slice by slice")
+    return out
+
+
+def run_paper_scale_leg(a, torch, api, inputs, dev):
+    """The paper-scale box: 12.7 M atoms of the water-like model in a 30 x 65 x 65 nm
+    box, a = 1.2 nm, h = 0.25 nm, 6 levels, FP32 bulk with FP64 reductions.  One
+    evaluation (timed, with the device memory in use), then an 8-slice parareal run
+    of 20 fine steps per slice with the 10,000-atom leg's coarse propagator
+    (a = 0.8 nm, h = 0.5 nm, 2 levels, 4 fs) against the serial fine trajectory, from
+    a state relaxed by 5 x 20 fine steps with velocities rescaled to 300 K."""
+    cfg = inputs.WORKLOADS["water12.7M"]
+    s0 = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=1.0, seed=0, vel_seed=1)
+    out = {"atoms": s0.n, "box_nm": [float(v) for v in s0.box[3:]], "levels": cfg["levels"]}
+    stream = torch.cuda.current_stream()
+    free0 = torch.cuda.mem_get_info()[0]
+    m = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", **WALL)
+    d = dev_system(torch, s0, dev)
+    m.system_forces(d)                                          # sizes buffers, autotunes
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    e, _, _ = m.system_forces(d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["evaluation_ms"] = e0.elapsed_time(e1)
+    out["energy_kj_mol"] = float(e)
+    out["device_gb_one_system"] = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
+    del m, d
+    # relax the lattice start (not timed), as the 10,000-atom leg does
+    dof = 6 * s0.n_mol + 3 * (s0.n - 3 * s0.n_mol)
+    mf = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", **WALL)
+    hs = inputs.System(pos=s0.pos.copy(), q=s0.q, mass=s0.mass, box=s0.box, vel=s0.vel.copy(), n_mol=s0.n_mol,
+                       lj=s0.lj)
+    for _ in range(5):
+        uk = mf.md_run(hs, DT, 20)
+        hs.vel *= np.sqrt(0.5 * dof * KB * 300.0 / uk[-1, 1])
+    n_slices, fsteps, tol = 8, 20, 1e-6
+    F = dict(a=A, h=H, levels=cfg["levels"], dt=DT, steps=fsteps, **WALL)
+    G = dict(a=0.8, h=0.5, levels=2, dt=2 * DT, steps=fsteps // 2, **WALL)
+    d = dev_system(torch, hs, dev)
+    serial = [d.pos.clone()]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n_slices):
+        mf.md_run(d, F["dt"], F["steps"], record=False)
+        serial.append(d.pos.clone())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_serial = e0.elapsed_time(e1) / 1e3
+    del mf, d
+    t = time.perf_counter()
+    free1 = torch.cuda.mem_get_info()[0]
+    try:
+        xs, vs, it, dx, conv = api.parareal_run(G, F, hs, n_slices, n_slices, tol, precision="fp32")
+    except api.MSMError as err:
+        out["parareal"] = {"error": str(err)}
+        return out
+    t_par = time.perf_counter() - t
+    err_nm = max(float((torch.from_numpy(xs[k]).to(dev) - serial[k]).abs().max()) for k in range(n_slices + 1))
+    out["parareal"] = {"slices": n_slices, "fine_steps": fsteps, "iterations": it, "converged": bool(conv),
+                       "last_max_dx_nm": dx, "max_error_vs_serial_nm": err_nm, "serial_fine_s": t_serial,
+                       "parareal_s": t_par, "speedup": t_serial / t_par,
+                       "device_gb_free_before": free1 / 1e9}
     return out
 
 

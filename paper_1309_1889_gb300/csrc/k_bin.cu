@@ -112,19 +112,25 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_blocks(int m, const int *__rest
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
+// One block scans the nb block sums in chunks of SCAN_B with a running carry
+// (any nb), and writes the grand total.
 __global__ void __launch_bounds__(SCAN_T) k_scan_sums(int nb, int *__restrict__ bsum, int *__restrict__ total,
                                                       const int *__restrict__ status)
 {
     if (failed(status)) return;
-    int b0 = threadIdx.x * SCAN_E;          // one block; nb <= SCAN_B
-    int v[SCAN_E], s = 0;
+    int carry = 0;
+    for (int c0 = 0; c0 < nb; c0 += SCAN_B) {
+        const int b0 = c0 + threadIdx.x * SCAN_E;
+        int v[SCAN_E], s = 0;
 #pragma unroll
-    for (int e = 0; e < SCAN_E; e++) { v[e] = (b0 + e < nb) ? bsum[b0 + e] : 0; s += v[e]; }
-    int tot;
-    int ex = block_excl_scan(s, &tot);
+        for (int e = 0; e < SCAN_E; e++) { v[e] = (b0 + e < nb) ? bsum[b0 + e] : 0; s += v[e]; }
+        int tot;
+        int ex = block_excl_scan(s, &tot) + carry;
 #pragma unroll
-    for (int e = 0; e < SCAN_E; e++) { if (b0 + e < nb) bsum[b0 + e] = ex; ex += v[e]; }
-    if (threadIdx.x == 0) *total = tot;
+        for (int e = 0; e < SCAN_E; e++) { if (b0 + e < nb) bsum[b0 + e] = ex; ex += v[e]; }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
 }
 
 __global__ void k_scan_add(int m, int *__restrict__ out, const int *__restrict__ bsum, const int *__restrict__ total,
@@ -215,16 +221,16 @@ int launch_diag_convert(int64_t n, const double *x, float *x32, const float *y, 
     return MSM_OK;
 }
 
-int scan_scratch_ints() { return SCAN_B + 1; }
+// block sums of a scan of m values, plus the total
+int scan_scratch_ints(int m) { return (m + SCAN_B - 1) / SCAN_B + 2; }
 
 // start[0..m] = exclusive prefix sums of count[0..m-1] (start[m] = total).
 int launch_scan(int m, const int *count, int *start, int *bsum, const int *status, cudaStream_t st)
 {
     const int nb = (m + SCAN_B - 1) / SCAN_B;
-    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
     k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, count, start, bsum, status);
-    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + SCAN_B, status);
-    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + SCAN_B, status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + nb, status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + nb, status);
     count_launch(3);
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -237,10 +243,9 @@ int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int
                        cudaStream_t st)
 {
     const int nb = (m + SCAN_B - 1) / SCAN_B;
-    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
     k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, count, start, bsum, status);
-    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + SCAN_B, status);
-    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + SCAN_B, status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, bsum, bsum + nb, status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, start, bsum, bsum + nb, status);
     count_launch(3);
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, key, start, count, perm, status);
@@ -256,7 +261,6 @@ int launch_bin(const BinArgs<T> &a, cudaStream_t st)
 {
     const int n = a.n_total, m = a.m_total, B = a.bt.B;
     const int nb = (m + SCAN_B - 1) / SCAN_B;
-    if (nb > SCAN_B) return fail_msg(MSM_EINVAL, "too many cells (%d) for the scan", m);
     CUDA_TRY(cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)(m + 1), st));
     const dim3 ga((a.max_n + 255) / 256, B);
     if (n > 0) {
@@ -264,8 +268,8 @@ int launch_bin(const BinArgs<T> &a, cudaStream_t st)
         count_launch();
     }
     k_scan_blocks<<<nb, SCAN_T, 0, st>>>(m, a.count, a.start, a.bsum, a.status);
-    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, a.bsum, a.bsum + SCAN_B, a.status);
-    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.bsum, a.bsum + SCAN_B, a.status);
+    k_scan_sums<<<1, SCAN_T, 0, st>>>(nb, a.bsum, a.bsum + nb, a.status);
+    k_scan_add<<<(m + 255) / 256, 256, 0, st>>>(m, a.start, a.bsum, a.bsum + nb, a.status);
     count_launch(3);
     if (n > 0) {
         k_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, a.key, a.start, a.count, a.perm, a.status);

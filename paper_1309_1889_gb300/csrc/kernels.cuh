@@ -28,7 +28,7 @@ template <typename T> struct BinArgs {
     int *count;            // m_total + 1 (histogram, left zeroed by the scatter)
     int *start;            // m_total + 1
     int *perm;             // n_total: sorted slot -> atom
-    int *bsum;             // scan scratch (scan_scratch_ints())
+    int *bsum;             // scan scratch (scan_scratch_ints(m_total))
     vec4<T> *rel;          // original order: (x - x0, y - y0, z - z0, q) of the atom's system
     vec4<T> *frac;         // original order: fractional position in the cell, q
     vec4<T> *apos;         // sorted copy of rel
@@ -41,7 +41,7 @@ template <typename T> struct BinArgs {
     int *status;
 };
 template <typename T> int launch_bin(const BinArgs<T> &a, cudaStream_t st);
-int scan_scratch_ints();
+int scan_scratch_ints(int m);             // scratch ints of a scan of m values
 int launch_diag_convert(int64_t n, const double *x, float *x32, const float *y, double *y64, cudaStream_t st);
 int launch_scan(int m, const int *count, int *start, int *bsum, const int *status, cudaStream_t st);
 int launch_sort_by_key(int n, int m, const int *key, int *count, int *start, int *perm, int *bsum, int *status,

@@ -514,7 +514,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         TRY(ensure(h->lj_count, sizeof(int) * (size_t)(M + 1)));
         TRY(ensure(h->lj_start, sizeof(int) * (size_t)(M + 1)));
     }
-    TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints()));
+    TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints((int)M)));
     TRY(ensure(h->qgrid, ts * (size_t)G));
     TRY(ensure(h->ucut, ts * (size_t)G));
     TRY(ensure(h->ugrid, ts * (size_t)G));

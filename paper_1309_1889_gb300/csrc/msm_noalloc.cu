@@ -92,7 +92,7 @@ extern "C" int msm_cell_list_noalloc(int64_t n, const double *pos, const double 
     // scratch layout: status[4] | bsum | count[ncells + 1] | key[n], each 256-byte aligned
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t o_bsum = 256;
-    const size_t o_count = o_bsum + up(sizeof(int) * (size_t)scan_scratch_ints());
+    const size_t o_count = o_bsum + up(sizeof(int) * (size_t)scan_scratch_ints((int)ncells));
     const size_t o_key = o_count + up(sizeof(int) * (size_t)(ncells + 1));
     const size_t need = o_key + up(sizeof(int) * (size_t)(n > 0 ? n : 1));
     if (need > MSM_NOALLOC_SCRATCH_BYTES)

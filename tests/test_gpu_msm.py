@@ -241,3 +241,27 @@ def test_fp32_and_fp64_paths_agree_at_full_size(api, torch):
     assert rel_rms(phi64[tg], ophi) <= 1e-12 and rel_rms(fs64[tg], of) <= 1e-12
     phi32, fs32 = m32.stage_atoms(s.n)
     assert rel_rms(phi32[tg], ophi) <= 1e-4 and rel_rms(fs32[tg], of) <= 1e-4
+
+
+def test_paper_scale_box_fp32_matches_fp64_and_oracle_rows(api, torch):
+    """12,700,000 atoms of the water-like model in a 30 x 65 x 65 nm box, 6 levels (the
+    paper-scale workload): one FP32 evaluation against the FP64 path (forces and energy),
+    sampled short-range rows against the oracle."""
+    cfg = inputs.WORKLOADS["water12.7M"]
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=0.5, with_velocities=False)
+    pos, q = _dev(torch, s.pos), _dev(torch, s.q)
+    m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32")
+    e32, f32, p32 = m32.energy_forces(pos, q, s.box)
+    rng = np.random.default_rng(1)
+    tg = rng.choice(s.n, 256, replace=False)
+    phi32, fs32 = m32.stage_atoms(s.n)
+    f32h = f32.cpu().numpy()
+    del m32, f32, p32
+    m64 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp64")
+    e64, f64, p64 = m64.energy_forces(pos, q, s.box)
+    assert abs(float(e32) - float(e64)) <= 1e-6 * abs(float(e64))
+    assert rel_rms(f32h, f64.cpu().numpy()) <= 1e-4
+    ophi, of = oracle.short_range(s.pos, s.q, A, s.box, targets=tg)
+    phi64, fs64 = m64.stage_atoms(s.n)
+    assert rel_rms(phi64[tg], ophi) <= 1e-12 and rel_rms(fs64[tg], of) <= 1e-12
+    assert rel_rms(phi32[tg], ophi) <= 1e-4 and rel_rms(fs32[tg], of) <= 1e-4
