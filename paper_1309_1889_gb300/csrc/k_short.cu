@@ -13,7 +13,8 @@
 // The warp finds its rows in parallel (one candidate row per lane, kept rows
 // compacted by ballot into a shared list with running end offsets), then
 // walks the concatenation of the rows 32 atoms at a time; a lane finds the
-// row of the atom it fetches by binary search over the offsets.  A fetched j
+// row of the atom it fetches by stepping forward from the row of the round's
+// first atom.  A fetched j
 // whose distance to the bounding box of the warp's i atoms is not below a
 // (cell rows overhang the cutoff sphere by up to a cell) is dropped there;
 // the rest enter a 64-entry FIFO in shared memory, which is drained 32 at a
@@ -222,20 +223,19 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                 r_next += 32;
             }
             __syncwarp();
-            // ---- fetch the segment's atoms 32 at a time, queue those near the box
+            // ---- fetch the segment's atoms 32 at a time, queue those near the box.  The
+            // rows are consumed in order: rc is the row holding atom cb of the concatenation,
+            // and a lane steps forward from it to the row holding its own atom.
+            int rc = 0;
             for (int cb = 0; cb < total; cb += 32) {
                 const int cnt = min(32, total - cb);
                 bool keep = false;
                 vec4<T> pj{T(0), T(0), T(0), T(0)};
-                int fj = 0;
+                int fj = 0, row = rc;
                 if (lane < cnt) {
                     const int want = cb + lane;
-                    int lo_r = 0, hi_r = nrows - 1;
-                    while (lo_r < hi_r) {
-                        const int mid = (lo_r + hi_r) >> 1;
-                        if (S.rend[wid][mid] > want) hi_r = mid; else lo_r = mid + 1;
-                    }
-                    const int js = S.rs0[wid][lo_r] + (want - (lo_r ? S.rend[wid][lo_r - 1] : 0));
+                    while (S.rend[wid][row] <= want) row++;
+                    const int js = S.rs0[wid][row] + (want - (row ? S.rend[wid][row - 1] : 0));
                     pj = A.apos[js];
                     if (MODEL) fj = A.aflag[js];
                     const T ex = max(T(0), max(lo[0] - pj.x, pj.x - hi[0]));
@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                     const T ez = max(T(0), max(lo[2] - pj.z, pj.z - hi[2]));
                     keep = fma(ex, ex, fma(ey, ey, fma(ez, ez, r2_eps<T>()))) < A.a2;
                 }
+                rc = __shfl_sync(0xffffffffu, row, 31);             // row of atom cb + 31
+                if (cnt == 32 && rc < nrows - 1 && S.rend[wid][rc] <= cb + 32) rc++;
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
                     const int q = (head + npend + __popc(m & lt)) & 63;
