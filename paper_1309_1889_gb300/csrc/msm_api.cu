@@ -140,6 +140,7 @@ struct Tuned {
     long long n;
     int nc[3];
     int bd[3];
+    int lj_bd[3];          // bricks of the LJ pass (water model; 0 = not tuned)
 };
 
 struct msm_handle {
@@ -371,6 +372,15 @@ static int brick_heuristic(int64_t n, const CellGeom &g, double target = 28.0)
     return pick;
 }
 
+static void set_lj_bricks(SysDesc &D, const int bd[3])
+{
+    for (int k = 0; k < 3; k++) {
+        D.lj_bd[k] = bd[k];
+        D.lj_nb[k] = (D.g.nc[k] + bd[k] - 1) / bd[k];
+    }
+    D.lj_nbricks = D.lj_nb[0] * D.lj_nb[1] * D.lj_nb[2];
+}
+
 static void set_bricks(SysDesc &D, const int bd[3])
 {
     for (int d = 0; d < 3; d++) {
@@ -474,12 +484,8 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         }
         if (h->p.model == MSM_MODEL_WATER) {
             // LJ pass: the O sites and single sites of the water completion
-            const int *lb = kBrickShapes[brick_heuristic(S.n_mol + (S.n - 3 * S.n_mol), D.g)];
-            for (int k = 0; k < 3; k++) {
-                D.lj_bd[k] = lb[k];
-                D.lj_nb[k] = (D.g.nc[k] + lb[k] - 1) / lb[k];
-            }
-            D.lj_nbricks = D.lj_nb[0] * D.lj_nb[1] * D.lj_nb[2];
+            const int n_lj = (int)(S.n_mol + (S.n - 3 * S.n_mol));
+            set_lj_bricks(D, (t && t->lj_bd[0]) ? t->lj_bd : kBrickShapes[brick_heuristic(n_lj, D.g)]);
         }
         D.grid_off = (int)G;
         G += tot;
@@ -657,7 +663,8 @@ static ShortArgs<T> short_args(msm_handle *h)
 
 // The brick autotuner: on the first evaluation of a single system's geometry,
 // time the short-range kernel for the five brick shapes around the heuristic's
-// choice (after binning, on the real atoms) and keep the fastest.  It runs
+// choice (after binning, on the real atoms) and keep the fastest; for the water
+// model, likewise the bricks of the LJ pass over the LJ-site list.  It runs
 // outside any graph capture and synchronises the stream.
 template <typename T>
 static int autotune_bricks(msm_handle *h, cudaStream_t st)
@@ -696,7 +703,48 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
     CUDA_TRY(cudaStreamSynchronize(st));
     Tuned t;
     t.n = D.n;
-    for (int k = 0; k < 3; k++) { t.nc[k] = D.g.nc[k]; t.bd[k] = D.bd[k]; }
+    for (int k = 0; k < 3; k++) { t.nc[k] = D.g.nc[k]; t.bd[k] = D.bd[k]; t.lj_bd[k] = 0; }
+    if (model && D.n > 0) {
+        // the LJ pass's bricks likewise, on the LJ-site list the evaluation builds next
+        const int *status = h->status.as<int>();
+        TRY(launch_lj_count<T>(h->M, h->start.as<int>(), h->aflag.as<int>(), h->lj_count.as<int>(), status, st));
+        TRY(launch_scan(h->M, h->lj_count.as<int>(), h->lj_start.as<int>(), h->bsum.as<int>(), status, st));
+        TRY(launch_lj_compact<T>(h->M, h->start.as<int>(), h->lj_start.as<int>(), h->apos.as<vec4<T>>(),
+                                 h->aflag.as<int>(), h->perm.as<int>(), h->lj_apos.as<vec4<T>>(),
+                                 h->lj_flag.as<int>(), h->lj_perm.as<int>(), status, st));
+        ShortArgs<T> sl = short_args<T>(h);
+        sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
+        sl.perm = h->lj_perm.as<int>();
+        const int l0 = brick_heuristic(D.n_mol + (D.n - 3 * D.n_mol), D.g);
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        float best_lj = 1e30f;
+        int best_l = l0;
+        for (int sidx = std::max(0, l0 - 2); sidx <= std::min(kNumShapes - 1, l0 + 2); sidx++) {
+            set_lj_bricks(D, kBrickShapes[sidx]);
+            CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+            sl.max_bricks = D.lj_nbricks;
+            TRY(launch_short_lj<T>(sl, st));                 // warm
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                CUDA_TRY(cudaEventRecord(e0, st));
+                TRY(launch_short_lj<T>(sl, st));
+                CUDA_TRY(cudaEventRecord(e1, st));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float tm = 0;
+                CUDA_TRY(cudaEventElapsedTime(&tm, e0, e1));
+                ms = std::min(ms, tm);
+            }
+            if (ms < best_lj) { best_lj = ms; best_l = sidx; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_lj_bricks(D, kBrickShapes[best_l]);
+        CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int k = 0; k < 3; k++) t.lj_bd[k] = D.lj_bd[k];
+        h->max_lj_bricks = D.lj_nbricks;
+    }
     h->tuned.push_back(t);
     h->max_bricks = D.nbricks;
     for (int k = 0; k < 3; k++) { h->bd[k] = D.bd[k]; h->nb[k] = D.nb[k]; }
