@@ -206,13 +206,14 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
 // threads, fixed 32-point tiles 23 %).  The tile's input planes z' = z0-rad ..
 // z0+ST_RZ-1+rad pass through two shared-memory buffers filled by cp.async
 // (zero outside the grid), the next plane's copy in flight while the current
-// one is used.  Every plane row (y + dy) is read into registers once and
-// applied to the ST_RZ output planes it reaches (dz = z' - z), walking the tap
-// row (dy, dz) of the sphere with compile-time offsets.  The weights
+// one is used.  The plane rows y + dy and y - dy (the weights depend on |dy|)
+// are added once in registers and applied to the ST_RZ output planes they
+// reach (dz = z' - z), walking the tap row (|dy|, |dz|) of the sphere with
+// compile-time offsets: half the multiply-adds of walking every row.  The weights
 // W[n] = g^0(|n| h) depend on |n| only, so one octant of the table sits in
 // shared memory; the level factor 2^{-k} is applied at the end.  CTAs take
 // tiles from a counter.  Each output sums its taps in a fixed order (planes,
-// rows, then x offsets), whatever the tile shape.
+// row pairs, then x offsets), whatever the tile shape.
 constexpr int ST_RX = 8, ST_RZ = 2, ST_NT = 128, ST_MAXGX = 16;
 constexpr int ST_MAXRAD = 12;
 
@@ -353,8 +354,10 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *
         const int b = tile - A.blk_off[ent];
         const int tx = b % tg.ntx, ty = (b / tg.ntx) % tg.nty, tz = b / (tg.ntx * tg.nty);
         const int x0 = tx * tg.tgx * ST_RX, y0 = ty * tg.tyr, z0 = tz * ST_RZ;
-        const int xg = t % tg.tgx, yr = t / tg.tgx;
-        const bool active = yr < tg.tyr;
+        // consecutive lanes take consecutive rows: the plane pitch is an odd number of
+        // 16-byte granules, so their row loads fall in different banks
+        const int yr = t % tg.tyr, xg = t / tg.tyr;
+        const bool active = xg < tg.tgx;
         const T *__restrict__ q = A.q + D.grid_off + L.off;
         const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
         // planes that exist: z' in [zb, ze)
@@ -382,26 +385,36 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *
             else st_wait_all();
             __syncthreads();
             if (active) {
+                // W depends on |dy|: rows y + dy and y - dy are added once and share
+                // the tap row of (|dz|, |dy|) for both output planes
 #pragma unroll 1
-                for (int dy = -RAD; dy <= RAD; dy++) {
+                for (int ady = 0; ady <= RAD; ady++) {
                     constexpr int NV = StRow<RAD>::N;
                     T v[NV];
-                    const T *row = cur + (yr + RAD + dy) * PX + xg * ST_RX;      // 16-byte aligned
+                    const T *row = cur + (yr + RAD + ady) * PX + xg * ST_RX;      // 16-byte aligned
+                    const T *mir = cur + (yr + RAD - ady) * PX + xg * ST_RX;
                     if (sizeof(T) == sizeof(float)) {
 #pragma unroll
                         for (int i = 0; i < NV; i += 4) {
                             const float4 f = *reinterpret_cast<const float4 *>(row + i);
                             v[i] = f.x; v[i + 1] = f.y; v[i + 2] = f.z; v[i + 3] = f.w;
                         }
+                        if (ady > 0) {
+#pragma unroll
+                            for (int i = 0; i < NV; i += 4) {
+                                const float4 f = *reinterpret_cast<const float4 *>(mir + i);
+                                v[i] += f.x; v[i + 1] += f.y; v[i + 2] += f.z; v[i + 3] += f.w;
+                            }
+                        }
                     } else {
 #pragma unroll
-                        for (int i = 0; i < NV; i++) v[i] = row[i];
+                        for (int i = 0; i < NV; i++) v[i] = ady > 0 ? row[i] + mir[i] : row[i];
                     }
 #pragma unroll
                     for (int s = 0; s < ST_RZ; s++) {
                         const int dz = zp - (z0 + s);
                         if (dz < -RAD || dz > RAD) continue;
-                        const int adz = dz < 0 ? -dz : dz, ady = dy < 0 ? -dy : dy;
+                        const int adz = dz < 0 ? -dz : dz;
                         const int w = hw[adz * R1 + ady];
                         if (w < 0) continue;
                         stencil_row_dispatch<RAD>(w, v, wt + (adz * R1 + ady) * R1P, acc[s]);
