@@ -76,7 +76,7 @@ template <typename T> struct ShortSmem {
     int rs0[SR_WARPS][SR_MAXROWS];      // first slot of each kept row
     int rend[SR_WARPS][SR_MAXROWS];     // running end of each row in the concatenation
     vec4<T> sj[SR_WARPS][64];           // FIFO of queued j atoms
-    int sf[SR_WARPS][64];               // their (molecule << 1 | LJ) flags
+    int sf[SR_WARPS][64];               // their molecule ids
 };
 
 // MODEL: rigid-water completion -- pairs inside one molecule are skipped (the
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
         }
         const bool valid = slot >= 0;
         const vec4<T> pi = valid ? A.apos[slot] : vec4<T>{big_t<T>(), big_t<T>(), big_t<T>(), T(0)};
-        const int fi = (MODEL && valid) ? A.aflag[slot] : -2;
+        const int mi = (MODEL && valid) ? A.aflag[slot] >> 1 : -1;     // molecule id (-1: no i atom)
 
         // ---- bounding box of the valid i atoms
         T lo[3], hi[3];
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                 // j = i: the water model's molecule test excludes it (an atom is in its own
                 // molecule); bare charges and the LJ pass (whose sites are one per molecule)
                 // test the distance
-                if (MODEL) in = in & ((unsigned)(fi ^ S.sf[wid][q0 + k]) >= 2u);
+                if (MODEL) in = in & (mi != S.sf[wid][q0 + k]);
                 else in = in & (r2s > T(2) * r2_eps<T>());
                 if (COUNT) { npair += in ? 1 : 0; continue; }
                 const T ri = rsqrt_t<T>(r2s);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
                     while (S.rend[wid][row] <= want) row++;
                     const int js = S.rs0[wid][row] + (want - (row ? S.rend[wid][row - 1] : 0));
                     pj = A.apos[js];
-                    if (MODEL) fj = A.aflag[js];
+                    if (MODEL) fj = A.aflag[js] >> 1;              // molecule id
                     const T ex = max(T(0), max(lo[0] - pj.x, pj.x - hi[0]));
                     const T ey = max(T(0), max(lo[1] - pj.y, pj.y - hi[1]));
                     const T ez = max(T(0), max(lo[2] - pj.z, pj.z - hi[2]));
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
             const int atom = A.perm[slot];
             if (LJP) { A.lj[atom] = vec4<T>{lx, ly, lz, fma(-A.lj_shift, (T)npair, le)}; continue; }
             A.sr[atom] = vec4<T>{-pi.w * ax, -pi.w * ay, -pi.w * az, phi};
-            if (MODEL && !(fi & 1)) A.lj[atom] = vec4<T>{T(0), T(0), T(0), T(0)};
+            if (MODEL && !(A.aflag[slot] & 1)) A.lj[atom] = vec4<T>{T(0), T(0), T(0), T(0)};
         }
     }
 }

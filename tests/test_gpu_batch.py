@@ -182,3 +182,20 @@ def test_uneven_water_batch_like_the_seven_cubes(api, torch):
         x = d.pos.cpu().numpy()[: 3 * s.n_mol].reshape(-1, 3, 3)
         oh = np.linalg.norm(x[:, 0] - x[:, 1], axis=1)
         assert np.abs(oh / inputs.D_OH - 1).max() < 2e-6
+
+
+def test_batch_with_more_cells_than_one_scan_pass_holds(api, torch):
+    """Two sparse 65 nm boxes (~18 M finest cells each, 36 M in the batch: the cell
+    scan runs its block sums in several passes) give the bits they give alone."""
+    systems = [inputs.random_cloud(3000, 65.0, seed=110 + k, neutral=True, margin=0.3) for k in range(2)]
+    m = api.MSM(a=A, h=H, levels=6, precision="fp32", autotune=False)
+    singles = [m.energy_forces(s.pos, s.q, s.box) for s in systems]
+    offsets = np.cumsum([0] + [len(s.q) for s in systems])
+    pos = np.concatenate([s.pos for s in systems]); q = np.concatenate([s.q for s in systems])
+    boxes = np.stack([np.asarray(s.box, dtype=np.float64) for s in systems])
+    mb = api.MSM(a=A, h=H, levels=6, precision="fp32", autotune=False)
+    e, f, p = mb.energy_forces_batched(offsets, pos, q, boxes)
+    for b, (es, fs, ps) in enumerate(singles):
+        o0, o1 = offsets[b], offsets[b + 1]
+        assert e[b] == es
+        assert np.array_equal(f[o0:o1], fs) and np.array_equal(p[o0:o1], ps)
