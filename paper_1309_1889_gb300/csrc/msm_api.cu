@@ -1101,9 +1101,12 @@ template <typename T> static double shake_tol() { return sizeof(T) == 4 ? 2e-6 :
 template <typename T> static double rattle_tol() { return sizeof(T) == 4 ? 2e-6 : 1e-14; }
 
 // (U, K) of every system into uk at the device step counter, then advance it.
-static int record_uk(msm_handle *h, const RunSys &s, double *uk, int64_t uk_stride, cudaStream_t st)
+// kin_ready: the per-atom kinetic energies are already in h->kin (written by
+// the second half kick).
+static int record_uk(msm_handle *h, const RunSys &s, double *uk, int64_t uk_stride, cudaStream_t st,
+                     bool kin_ready = false)
 {
-    TRY(launch_kinetic(h->N, s.v, s.m, h->kin.as<double>(), st));
+    if (!kin_ready) TRY(launch_kinetic(h->N, s.v, s.m, h->kin.as<double>(), st));
     const double *cols[1] = {h->kin.as<double>()};
     TRY(launch_sum(batch_of(h), h->max_n, h->PB, 1, cols, h->partials.as<double>(), h->kin_s.as<double>(), 1,
                    h->status.as<int>(), st));
@@ -1119,8 +1122,8 @@ static int md_step(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArg
 {
     { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
     TRY(evaluate_t<T>(h, io, st));
-    { PROF(ST_VV2); TRY(launch_vv_second<T>(va, nullptr, st)); }
-    if (uk) TRY(record_uk(h, s, uk, uk_stride, st));
+    { PROF(ST_VV2); TRY(launch_vv_second<T>(va, uk ? h->kin.as<double>() : nullptr, st)); }
+    if (uk) TRY(record_uk(h, s, uk, uk_stride, st, true));
     return MSM_OK;
 }
 
