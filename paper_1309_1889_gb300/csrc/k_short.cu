@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short
 
         // sum the cnt queued j's from FIFO position q0 (no wrap: q0 + cnt <= 64)
         auto pairs = [&](const int q0, const int cnt) {
-#pragma unroll 8
+#pragma unroll (LJP ? 8 : 32)
             for (int k = 0; k < cnt; k++) {
                 const vec4<T> pj = S.sj[wid][q0 + k];
                 const T dx = pj.x - pi.x, dyy = pj.y - pi.y, dzz = pj.z - pi.z;
