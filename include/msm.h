@@ -138,7 +138,9 @@ MSM_API void msm_default_params(msm_params *p);
 /* Create a handle (validates *p; allocates nothing on the device until the
  * first evaluation).  The handle owns its scratch: sorted atoms, cell lists,
  * grids for every level, stencil and top-level tables.  Not thread-safe:
- * one handle per host thread / stream.  Errors: MSM_EINVAL. */
+ * one handle per host thread / stream.  Errors: MSM_EINVAL (among others
+ * when n_levels > 1 and the lattice-cutoff radius, the largest r with
+ * r h < 2a, exceeds 12 grid points). */
 MSM_API int  msm_create(const msm_params *p, msm_handle **out);
 MSM_API void msm_destroy(msm_handle *h);
 

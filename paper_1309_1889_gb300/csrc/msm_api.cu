@@ -282,7 +282,8 @@ static int check_params(const msm_params *p)
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
     int rad = 0;
     while ((double)(rad + 1) * p->h < 2.0 * p->a) rad++;
-    if (rad > 12) return fail_msg(MSM_EINVAL, "2a/h = %.3g is too large (lattice-cutoff radius %d > 12)", 2 * p->a / p->h, rad);
+    if (rad > 12 && p->n_levels > 1)                       // one level has no lattice cutoff
+        return fail_msg(MSM_EINVAL, "2a/h = %.3g is too large (lattice-cutoff radius %d > 12)", 2 * p->a / p->h, rad);
     return MSM_OK;
 }
 

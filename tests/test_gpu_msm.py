@@ -265,3 +265,23 @@ def test_paper_scale_box_fp32_matches_fp64_and_oracle_rows(api, torch):
     phi64, fs64 = m64.stage_atoms(s.n)
     assert rel_rms(phi64[tg], ophi) <= 1e-12 and rel_rms(fs64[tg], of) <= 1e-12
     assert rel_rms(phi32[tg], ophi) <= 1e-4 and rel_rms(fs32[tg], of) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_long_cutoff_takes_the_row_list_in_segments(api, torch, prec):
+    """a = 2.4 nm on h = 0.2 nm cells (one level, dense top level): a warp's candidate
+    rows outnumber its row list, so the short-range kernel walks them in segments; the
+    short-range sums and the whole result still match the oracle."""
+    a, h = 2.4, 0.2
+    s = inputs.random_cloud(3000, (4.0, 4.0, 4.0), seed=41, neutral=True, margin=0.2)
+    m = api.MSM(a=a, h=h, levels=1, precision=prec)
+    e, f, p = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
+    phi, fs = m.stage_atoms(s.n)
+    t = TOL[prec]
+    ophi, of = oracle.short_range(s.pos, s.q, a, s.box)
+    assert rel_rms(phi, ophi) <= t["f"] and rel_rms(fs, of) <= t["f"]
+    ref = oracle.msm(s.pos, s.q, s.box, a, h, 1)
+    scale = abs(ref["energy"]) + 0.5 * oracle.KE * (s.q ** 2).sum() * 15.0 / (8.0 * a)
+    assert abs(float(e) - ref["energy"]) <= t["e"] * scale
+    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
+    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
