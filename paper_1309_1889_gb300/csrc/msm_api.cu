@@ -184,6 +184,8 @@ struct msm_handle {
     int h_e_cap = 0;
     // CUDA graph of one md step
     cudaStream_t cap_st = nullptr;
+    cudaStream_t grid_st = nullptr;                     // high-priority stream of the grid chain
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
     long long g_kernels = 0;                            // kernels per replayed step
@@ -326,6 +328,9 @@ extern "C" void msm_destroy(msm_handle *h)
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    if (h->grid_st) cudaStreamDestroy(h->grid_st);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -781,6 +786,64 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     { PROF(ST_BIN); TRY(launch_bin<T>(b, st)); }
     if (h->tune_pending) TRY(autotune_bricks<T>(h, st));
 
+    // The grid chain (steps 2-7) depends on the binning only, the short range (step 1)
+    // likewise; interpolation needs both.  Unless the stages are being timed one by one
+    // (or Verlet lists are on), the grid chain runs on a second, high-priority stream
+    // forked here and joined before interpolation: its small, latency-bound launches
+    // (the lattice cutoff keeps about four CTAs per SM busy) fill the SMs beside the
+    // issue-bound pair kernels.
+    const bool fork = !h->prof.on && !h->list_on;
+    cudaStream_t gs = st;
+    if (fork) {
+        if (!h->grid_st) {
+            int lo = 0, hi = 0;
+            CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CUDA_TRY(cudaStreamCreateWithPriority(&h->grid_st, cudaStreamNonBlocking, hi));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaEventRecord(h->ev_fork, st));
+        CUDA_TRY(cudaStreamWaitEvent(h->grid_st, h->ev_fork, 0));
+        gs = h->grid_st;
+    }
+    T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
+    {
+        cudaStream_t st = gs;                                  // the grid chain's stream
+        // step 2: anterpolation
+        AnterpArgs<T> an;
+        an.bt = bt; an.max_tiles = h->max_atiles; an.n_total = (int)h->N; an.start = h->start.as<int>();
+        an.aw = h->aw.as<vec4<T>>();
+        an.q = qg; an.status = status;
+        { PROF(ST_ANTERP); TRY(launch_anterp<T>(an, st)); }
+
+        // steps 3-4: restriction down the levels, then the lattice cutoff of levels 0..l-2 in one launch
+        const int l = h->p.n_levels;
+        {
+            PROF(ST_RESTRICT);
+            for (int k = 0; k + 1 < l; k++) TRY(launch_restrict<T>(bt, k, h->max_lev[k + 1], qg, status, st));
+        }
+        if (l > 1) {
+            StencilArgs<T> sa;
+            sa.bt = bt; sa.nlev = l - 1; sa.blk_off = h->blk_buf.as<int>(); sa.total_tiles = h->stiles; sa.sg = h->sg;
+            sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
+            PROF(ST_STENCIL);
+            TRY(launch_stencil<T>(sa, h->status.as<int>() + 2, st));
+        }
+        // step 5: top level in FP64
+        { PROF(ST_TOP); TRY(launch_top<T>(bt, h->max_top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
+        // steps 6-7: prolongation back to level 0
+        {
+            PROF(ST_PROLONG);
+            if (l == 1) {
+                TRY(launch_top_to_grid<T>(bt, h->max_top, h->utop.as<double>(), ug, status, st));
+            } else {
+                TRY(launch_prolong<T>(bt, l - 2, h->max_lev[l - 2], uc, h->utop.as<double>(), true, ug, status, st));
+                for (int k = l - 3; k >= 0; k--)
+                    TRY(launch_prolong<T>(bt, k, h->max_lev[k], uc, h->utop.as<double>(), false, ug, status, st));
+            }
+        }
+    }
+
     // step 1: short range
     ShortArgs<T> s = short_args<T>(h);
     // the lists address the bricks they were built for: never use them on another brick set
@@ -831,40 +894,11 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         }
     }
 
-    // step 2: anterpolation
-    T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
-    AnterpArgs<T> an;
-    an.bt = bt; an.max_tiles = h->max_atiles; an.n_total = (int)h->N; an.start = h->start.as<int>();
-    an.aw = h->aw.as<vec4<T>>();
-    an.q = qg; an.status = status;
-    { PROF(ST_ANTERP); TRY(launch_anterp<T>(an, st)); }
+    if (fork) {
+        CUDA_TRY(cudaEventRecord(h->ev_join, gs));
+        CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0));
+    }
 
-    // steps 3-4: restriction down the levels, then the lattice cutoff of levels 0..l-2 in one launch
-    const int l = h->p.n_levels;
-    {
-        PROF(ST_RESTRICT);
-        for (int k = 0; k + 1 < l; k++) TRY(launch_restrict<T>(bt, k, h->max_lev[k + 1], qg, status, st));
-    }
-    if (l > 1) {
-        StencilArgs<T> sa;
-        sa.bt = bt; sa.nlev = l - 1; sa.blk_off = h->blk_buf.as<int>(); sa.total_tiles = h->stiles; sa.sg = h->sg;
-        sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
-        PROF(ST_STENCIL);
-        TRY(launch_stencil<T>(sa, h->status.as<int>() + 2, st));
-    }
-    // step 5: top level in FP64
-    { PROF(ST_TOP); TRY(launch_top<T>(bt, h->max_top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
-    // steps 6-7: prolongation back to level 0
-    {
-        PROF(ST_PROLONG);
-        if (l == 1) {
-            TRY(launch_top_to_grid<T>(bt, h->max_top, h->utop.as<double>(), ug, status, st));
-        } else {
-            TRY(launch_prolong<T>(bt, l - 2, h->max_lev[l - 2], uc, h->utop.as<double>(), true, ug, status, st));
-            for (int k = l - 3; k >= 0; k--)
-                TRY(launch_prolong<T>(bt, k, h->max_lev[k], uc, h->utop.as<double>(), false, ug, status, st));
-        }
-    }
     // step 8-9: interpolation, totals, scatter to the caller's order
     InterpArgs<T> ia;
     ia.bt = bt; ia.max_n = h->max_n; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
