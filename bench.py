@@ -334,7 +334,8 @@ def run_ours(a):
                 "max_abs_dev_kj_mol": float(np.abs(etot - etot[0]).max()), "kinetic_kj_mol": float(uk[-1, 1])},
         "stage_ms_per_launch": stage_ms,
         "stage_share_of_step": step_share,
-        "timed_region": "CUDA-graph replay of every step after the first (profiler off)",
+        "timed_region": ("CUDA-graph replay of every step after the first (profiler off; the grid chain runs on a "
+                         "second stream beside the pair kernels); stage times come from a serialised profiled pass"),
         "uneven_batch": batched,
         "parareal": parareal,
     }
