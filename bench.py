@@ -308,6 +308,16 @@ def run_ours(a):
     sr_avg_s = sr_ms / sr_n / 1e3
     achieved = pairs * FLOPS_PER_PAIR / sr_avg_s / 1e12
     traffic = short_range_traffic(n)
+    # second stage: the lattice cutoff, FP32 ALU bound (2 flops per tap inside the sphere |n| h < 2a,
+    # per point of levels 0..l-2; the kernel issues about half of them, rows +-dy sharing a weight row)
+    rad = int(np.ceil(2 * A / H))
+    rng_ = np.arange(-rad, rad + 1)
+    dx_, dy_, dz_ = np.meshgrid(rng_, rng_, rng_, indexing="ij")
+    taps = int((np.sqrt(dx_ ** 2 + dy_ ** 2 + dz_ ** 2) * H < 2 * A).sum())
+    st_points = sum(int(np.prod(m32.grid_shape(k)[0])) for k in range(cfg["levels"] - 1))
+    st_ms, st_n = prof["lattice_cutoff"]
+    st_avg_s = st_ms / st_n / 1e3
+    st_achieved = 2 * taps * st_points / st_avg_s / 1e12
     stage_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]}
     step_share = {k: round(v[0] / t_prof, 4) for k, v in prof.items() if v[1]}
     drift = float(etot[-1] - etot[0])
@@ -323,6 +333,10 @@ def run_ours(a):
                      "work": f"{pairs} ordered pairs within a per launch x {FLOPS_PER_PAIR} flops",
                      "duration": f"{sr_avg_s * 1e3:.4f} ms average of {sr_n} launches (CUDA events on the "
                                  f"launching stream, {a.profile_steps} eager steps continuing the timed run)"},
+        "roofline_lattice_cutoff": {"bound": "alu", "achieved": st_achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                                    "frac": st_achieved / peak_tflops, "kernel": "k_stencil (levels 0..l-2)",
+                                    "work": f"{taps} taps x 2 flops x {st_points} grid points per launch",
+                                    "duration": f"{st_avg_s * 1e3:.4f} ms average of {st_n} launches"},
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
         "gpu_launches": launches,
