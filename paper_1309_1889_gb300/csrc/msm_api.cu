@@ -1165,15 +1165,22 @@ static int md_step(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArg
 // Capture one md step into a CUDA graph on the handle's own stream (capture
 // records the launches; nothing runs), or reuse the graph captured for the
 // same arrays, geometry and buffers.
-template <typename T>
-static int md_graph(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArgs &va, double dt, double *uk,
-                    int64_t uk_stride)
+static GraphKey graph_key(const msm_handle *h, const RunSys &s, const EvalIO &io, double dt, double *uk,
+                          int64_t uk_stride)
 {
     GraphKey k;
     memset(&k, 0, sizeof k);
     k.x = s.x; k.v = s.v; k.f = io.forces; k.q = s.q; k.m = s.m; k.lj = s.lj; k.uk = uk;
     k.uk_stride = uk_stride; k.geom_gen = h->geom_gen; k.alloc_gen = g_alloc_gen.load(); k.dt = dt;
     k.B = s.B; k.list_on = h->list_on ? 1 : 0;
+    return k;
+}
+
+template <typename T>
+static int md_graph(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArgs &va, double dt, double *uk,
+                    int64_t uk_stride)
+{
+    const GraphKey k = graph_key(h, s, io, dt, uk, uk_stride);
     if (h->gexec && memcmp(&k, &h->gkey, sizeof k) == 0) return MSM_OK;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (!h->cap_st) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
@@ -1195,9 +1202,10 @@ static int md_graph(msm_handle *h, const RunSys &s, const EvalIO &io, const VVAr
 
 // n_steps of velocity Verlet on a batch in device arrays; uk (device,
 // nullable) gets (U, K) of system b before the first and after every step at
-// uk[b * uk_stride + 2 * step].  The first step runs launch by launch; with
-// graphs on (and the profiler off) the others replay one captured graph.
-// No host synchronisation.
+// uk[b * uk_stride + 2 * step].  With graphs on (and the profiler off) the
+// steps replay one captured graph; the first step of a call runs launch by
+// launch unless the graph cached by an earlier call was captured for the same
+// arrays, geometry and buffers.  No host synchronisation.
 template <typename T>
 static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, double *uk, int64_t uk_stride,
                     cudaStream_t st)
@@ -1242,8 +1250,11 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
     const bool graphs = (h->p.flags & MSM_FLAG_GRAPHS) && !h->prof.on;
     bool captured = false;
     int rc = MSM_OK;
+    const bool warm = graphs && !h->tune_pending && h->gexec &&
+                      [&] { const GraphKey k = graph_key(h, s, io, dt, uk, uk_stride);
+                            return memcmp(&k, &h->gkey, sizeof k) == 0; }();
     for (int step = 0; step < n_steps && rc == MSM_OK; step++) {
-        if (!graphs || step == 0 || h->tune_pending) {
+        if (!graphs || (step == 0 && !warm) || h->tune_pending) {
             rc = md_step<T>(h, s, io, va, uk, uk_stride, st);
             continue;
         }
