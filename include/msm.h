@@ -57,7 +57,9 @@ extern "C" {
 #define MSM_MODEL_CHARGES 0  /* bare point charges: the paper's Coulomb sum     */
 #define MSM_MODEL_WATER   1  /* + rigid 3-site water completion (see msm_system) */
 
-#define MSM_FLAG_GRAPHS   1  /* md_run: steps after the first replay one captured CUDA graph */
+#define MSM_FLAG_GRAPHS   1  /* md_run: steps after the first replay one captured CUDA graph
+                                (the first too, when a previous call captured it for the
+                                same arrays, geometry and buffers)                         */
 #define MSM_FLAG_AUTOTUNE 2  /* time the short-range brick shapes on the first evaluation of
                                 each single-system geometry and keep the fastest           */
 
