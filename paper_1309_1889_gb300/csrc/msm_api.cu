@@ -486,7 +486,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         if (t) set_bricks(D, t->bd);
         else {
             set_bricks(D, kBrickShapes[brick_heuristic(S.n, D.g)]);
-            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && B == 1 && S.n > 0) pending = true;
+            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && S.n > 0) pending = true;
         }
         if (h->p.model == MSM_MODEL_WATER) {
             // LJ pass: the O sites and single sites of the water completion
@@ -667,52 +667,75 @@ static ShortArgs<T> short_args(msm_handle *h)
     return s;
 }
 
-// The brick autotuner: on the first evaluation of a single system's geometry,
-// time the short-range kernel for the five brick shapes around the heuristic's
-// choice (after binning, on the real atoms) and keep the fastest; for the water
-// model, likewise the bricks of the LJ pass over the LJ-site list.  It runs
+// The brick autotuner: on the first evaluation of a geometry, time the
+// short-range kernel for the five brick shapes around the heuristic's choice
+// (after binning, on the real atoms; in a batch, one shape for all systems
+// without a tuned entry, on the batched launch) and keep the fastest; for the
+// water model, likewise the bricks of the LJ pass over the LJ-site list.  It runs
 // outside any graph capture and synchronises the stream.
 template <typename T>
 static int autotune_bricks(msm_handle *h, cudaStream_t st)
 {
     h->tune_pending = false;
-    SysDesc &D = h->hsd[0];
-    const int h0 = brick_heuristic(D.n, D.g);
+    const int B = h->B;
+    // the systems without a tuned entry (set_batch gave them the heuristic's bricks) are
+    // tuned together: one shape for all of them, timed on the batched launch
+    std::vector<int> todo;
+    int big = -1;
+    for (int b = 0; b < B; b++) {
+        const SysDesc &D = h->hsd[(size_t)b];
+        if (D.n > 0 && !find_tuned(h, D.n, D.g)) {
+            todo.push_back(b);
+            if (big < 0 || D.n > h->hsd[(size_t)big].n) big = b;
+        }
+    }
+    if (todo.empty()) return MSM_OK;
+    const bool model = h->p.model == MSM_MODEL_WATER;
+    const int *status = h->status.as<int>();
+    auto upload = [&]() {
+        return cudaMemcpyAsync(h->sd_buf.p, h->hsd.data(), sizeof(SysDesc) * (size_t)B, cudaMemcpyHostToDevice, st);
+    };
+    auto most = [&](bool lj) {
+        int m = 0;
+        for (const SysDesc &D : h->hsd) m = std::max(m, lj ? D.lj_nbricks : D.nbricks);
+        return m;
+    };
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_s = h0;
-    const bool model = h->p.model == MSM_MODEL_WATER;
-    for (int sidx = std::max(0, h0 - 2); sidx <= std::min(kNumShapes - 1, h0 + 2); sidx++) {
-        set_bricks(D, kBrickShapes[sidx]);
-        CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
-        ShortArgs<T> s = short_args<T>(h);
-        s.max_bricks = D.nbricks;
-        TRY(launch_short<T>(s, model, st));                 // warm
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2; rep++) {                  // the faster of two timed launches
+    // time one configuration: the faster of two launches after a warm one
+    auto timed = [&](const ShortArgs<T> &a, bool lj, float *ms) -> int {
+        TRY(lj ? launch_short_lj<T>(a, st) : launch_short<T>(a, model, st));
+        *ms = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
             CUDA_TRY(cudaEventRecord(e0, st));
-            TRY(launch_short<T>(s, model, st));
+            TRY(lj ? launch_short_lj<T>(a, st) : launch_short<T>(a, model, st));
             CUDA_TRY(cudaEventRecord(e1, st));
             CUDA_TRY(cudaEventSynchronize(e1));
             float t = 0;
             CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-            ms = std::min(ms, t);
+            *ms = std::min(*ms, t);
         }
+        return MSM_OK;
+    };
+    const SysDesc &R = h->hsd[(size_t)big];
+    const int h0 = brick_heuristic(R.n, R.g);
+    float best = 1e30f;
+    int best_s = h0;
+    for (int sidx = std::max(0, h0 - 2); sidx <= std::min(kNumShapes - 1, h0 + 2); sidx++) {
+        for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
+        CUDA_TRY(upload());
+        ShortArgs<T> sa = short_args<T>(h);
+        sa.max_bricks = most(false);
+        float ms;
+        TRY(timed(sa, false, &ms));
         if (ms < best) { best = ms; best_s = sidx; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    set_bricks(D, kBrickShapes[best_s]);
-    CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    Tuned t;
-    t.n = D.n;
-    for (int k = 0; k < 3; k++) { t.nc[k] = D.g.nc[k]; t.bd[k] = D.bd[k]; t.lj_bd[k] = 0; }
-    if (model && D.n > 0) {
+    for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[best_s]);
+    CUDA_TRY(upload());
+    int best_l = 0;
+    if (model) {
         // the LJ pass's bricks likewise, on the LJ-site list the evaluation builds next
-        const int *status = h->status.as<int>();
         TRY(launch_lj_count<T>(h->M, h->start.as<int>(), h->aflag.as<int>(), h->lj_count.as<int>(), status, st));
         TRY(launch_scan(h->M, h->lj_count.as<int>(), h->lj_start.as<int>(), h->bsum.as<int>(), status, st));
         TRY(launch_lj_compact<T>(h->M, h->start.as<int>(), h->lj_start.as<int>(), h->apos.as<vec4<T>>(),
@@ -721,40 +744,39 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
         ShortArgs<T> sl = short_args<T>(h);
         sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
         sl.perm = h->lj_perm.as<int>();
-        const int l0 = brick_heuristic(D.n_mol + (D.n - 3 * D.n_mol), D.g);
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
+        const int l0 = brick_heuristic(R.n_mol + (R.n - 3 * R.n_mol), R.g);
         float best_lj = 1e30f;
-        int best_l = l0;
+        best_l = l0;
         for (int sidx = std::max(0, l0 - 2); sidx <= std::min(kNumShapes - 1, l0 + 2); sidx++) {
-            set_lj_bricks(D, kBrickShapes[sidx]);
-            CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
-            sl.max_bricks = D.lj_nbricks;
-            TRY(launch_short_lj<T>(sl, st));                 // warm
-            float ms = 1e30f;
-            for (int rep = 0; rep < 2; rep++) {
-                CUDA_TRY(cudaEventRecord(e0, st));
-                TRY(launch_short_lj<T>(sl, st));
-                CUDA_TRY(cudaEventRecord(e1, st));
-                CUDA_TRY(cudaEventSynchronize(e1));
-                float tm = 0;
-                CUDA_TRY(cudaEventElapsedTime(&tm, e0, e1));
-                ms = std::min(ms, tm);
-            }
+            for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
+            CUDA_TRY(upload());
+            sl.max_bricks = most(true);
+            float ms;
+            TRY(timed(sl, true, &ms));
             if (ms < best_lj) { best_lj = ms; best_l = sidx; }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        set_lj_bricks(D, kBrickShapes[best_l]);
-        CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, &D, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        for (int k = 0; k < 3; k++) t.lj_bd[k] = D.lj_bd[k];
-        h->max_lj_bricks = D.lj_nbricks;
+        for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[best_l]);
+        CUDA_TRY(upload());
     }
-    h->tuned.push_back(t);
-    h->max_bricks = D.nbricks;
-    for (int k = 0; k < 3; k++) { h->bd[k] = D.bd[k]; h->nb[k] = D.nb[k]; }
-    h->nbricks = D.nbricks;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int b : todo) {
+        const SysDesc &D = h->hsd[(size_t)b];
+        Tuned t;
+        t.n = D.n;
+        for (int k = 0; k < 3; k++) {
+            t.nc[k] = D.g.nc[k];
+            t.bd[k] = D.bd[k];
+            t.lj_bd[k] = model ? D.lj_bd[k] : 0;
+        }
+        h->tuned.push_back(t);
+    }
+    h->max_bricks = most(false);
+    h->max_lj_bricks = most(true);
+    const SysDesc &D0 = h->hsd[0];
+    for (int k = 0; k < 3; k++) { h->bd[k] = D0.bd[k]; h->nb[k] = D0.nb[k]; }
+    h->nbricks = D0.nbricks;
     h->geom_gen++;
     return MSM_OK;
 }
