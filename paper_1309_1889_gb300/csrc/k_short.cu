@@ -14,11 +14,10 @@
 // compacted by ballot into a shared list with running end offsets), then
 // walks the concatenation of the rows 32 atoms at a time; a lane finds the
 // row of the atom it fetches by stepping forward from the row of the round's
-// first atom.  A fetched j
-// whose distance to the bounding box of the warp's i atoms is not below a
-// (cell rows overhang the cutoff sphere by up to a cell) is dropped there;
-// the rest enter a 64-entry FIFO in shared memory, which is drained 32 at a
-// time, so the pair loop runs full.  All lanes read each queued j by
+// first atom.  A fetched j whose distance to the bounding box of the warp's i
+// atoms is not below a (cell rows overhang the cutoff sphere by up to a cell)
+// is dropped there; the rest enter a 64-entry FIFO in shared memory, which is
+// drained 32 at a time, so the pair loop runs full (and fully unrolled).  All lanes read each queued j by
 // broadcast.  Per candidate a lane evaluates one rsqrt and ~20 FP32 FMA-pipe
 // instructions; pairs beyond a, the pair j = i and pairs inside one rigid
 // molecule get charge zero (exact zero contributions), never a branch.  More
@@ -84,8 +83,9 @@ template <typename T> struct ShortSmem {
 // a zero LJ output.
 // COUNT: diagnostics only -- count the pairs inside the cutoff instead of summing.
 // LJP: the O-O Lennard-Jones pass of the water completion, over the LJ-site
-// cell list (i and j both LJ sites, other molecules, r < a): the same terms, in
-// the same ascending slot order, as summing them inside the Coulomb loop.
+// cell list (i and j both LJ sites, j != i, r < a), in ascending slot order;
+// the constant shift of the cut-and-shifted potential is applied once per
+// counted pair at the end.
 template <typename T, bool MODEL, bool COUNT, bool LJP>
 __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short(const ShortArgs<T> A)
 {
