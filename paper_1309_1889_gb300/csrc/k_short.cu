@@ -87,7 +87,7 @@ template <typename T> struct ShortSmem {
 // the constant shift of the cut-and-shifted potential is applied once per
 // counted pair at the end.
 template <typename T, bool MODEL, bool COUNT, bool LJP>
-__global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 8 : 4) k_short(const ShortArgs<T> A)
+__global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
