@@ -62,6 +62,9 @@ extern "C" {
                                 same arrays, geometry and buffers)                         */
 #define MSM_FLAG_AUTOTUNE 2  /* time the short-range brick shapes on the first evaluation of
                                 each single-system geometry and keep the fastest           */
+#define MSM_FLAG_SCALAR_PAIRS 4  /* diagnostic, FP32 only: the short-range pass takes its
+                                queued neighbours one at a time instead of two per packed
+                                FP32x2 step; the same bits, slower (off by default)        */
 
 /* Method parameters (Sec. 3).
  *   a          cutoff of the short-range part g* (nm); the level-k lattice
@@ -79,11 +82,12 @@ extern "C" {
  *              keeps atoms inside the open domain; an atom closer than
  *              wall_width to a box face feels 1/2 wall_k (wall_width - d)^2
  *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)
- *   flags      MSM_FLAG_* bits (default: both).  Neither changes a result bit:
- *              a graph replays exactly the launches of an eager step, and the
- *              short-range sum adds each atom's neighbours in ascending sorted
- *              order whatever the brick shape.  Graphs are not used while the
- *              profiler is on.
+ *   flags      MSM_FLAG_* bits (default: GRAPHS | AUTOTUNE).  None changes a
+ *              result bit: a graph replays exactly the launches of an eager
+ *              step, the short-range sum adds each atom's neighbours in
+ *              ascending sorted order whatever the brick shape, and the packed
+ *              and scalar pair steps do the same IEEE operations.  Graphs are
+ *              not used while the profiler is on.
  *   list_skin  md_run only: Verlet-list skin (nm) of the short-range sum;
  *              lists hold pairs within a + list_skin and are rebuilt when an
  *              atom has moved more than list_skin/2 (0 = cell search every

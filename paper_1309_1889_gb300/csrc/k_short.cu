@@ -17,9 +17,12 @@
 // first atom.  A fetched j whose distance to the bounding box of the warp's i
 // atoms is not below a (cell rows overhang the cutoff sphere by up to a cell)
 // is dropped there; the rest enter a 64-entry FIFO in shared memory, which is
-// drained 32 at a time, so the pair loop runs full (and fully unrolled).  All lanes read each queued j by
-// broadcast.  Per candidate a lane evaluates one rsqrt and ~20 FP32 FMA-pipe
-// instructions; pairs beyond a, the pair j = i and pairs inside one rigid
+// drained 32 at a time, so the pair loop runs full (and unrolled).  All lanes
+// read each queued j by broadcast.  Per candidate a lane evaluates one rsqrt and
+// 17 FP32 FMA-pipe operations; the FP32 Coulomb pass issues 13 of them (all but
+// the four accumulations) as packed FP32x2 instructions over two queued j's (the
+// FIFO then holds pair blocks x x y y z z q q, so each packed operand is one half
+// of a 16-byte load).  Pairs beyond a, the pair j = i and pairs inside one rigid
 // molecule get charge zero (exact zero contributions), never a branch.  More
 // rows than the list holds are taken in segments.
 //
@@ -74,9 +77,61 @@ template <> __device__ __forceinline__ double r2_eps<double>() { return 1e-30; }
 template <typename T> struct ShortSmem {
     int rs0[SR_WARPS][SR_MAXROWS];      // first slot of each kept row
     int rend[SR_WARPS][SR_MAXROWS];     // running end of each row in the concatenation
-    vec4<T> sj[SR_WARPS][64];           // FIFO of queued j atoms
+    union {
+        vec4<T> sj[SR_WARPS][64];       // FIFO of queued j atoms, (x, y, z, q) each
+        T sp[SR_WARPS][64 * 4];         // FP32 Coulomb pass: the same FIFO as pair blocks,
+                                        // entries 2p, 2p+1 at [8p, 8p+8): x x y y z z q q
+    };
     int sf[SR_WARPS][64];               // their molecule ids
 };
+
+// Two queued j's per step of the FP32 Coulomb pass, on packed FP32 pairs (one
+// f32x2 instruction does the same IEEE operation for both j's).  Every per-pair
+// value is computed by the operations of the scalar loop in k_short, in the same
+// order (x - y as x + (-y); -poly from the negated coefficients, exact since
+// rounding commutes with negation), and each accumulator takes its terms one j
+// at a time in queue order: the sums are bitwise those of the scalar loop.  P
+// points at pair block q0/2 of the warp's FIFO (q0 even), F at the molecule id of
+// entry q0; an odd cnt reads one pad entry of charge zero.
+template <bool MODEL>
+__device__ __forceinline__ void pair_steps_f32x2(const float *__restrict__ P, const int *__restrict__ F,
+                                                 const int cnt, const vec4<float> pi, const int mi,
+                                                 const ShortArgs<float> &A, float &phi, float &ax, float &ay,
+                                                 float &az)
+{
+    const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
+    const float2 eps = make_float2(r2_eps<float>(), r2_eps<float>());
+    const float2 nc0 = make_float2(-A.c0, -A.c0), nc1 = make_float2(-A.c1, -A.c1), nc2 = make_float2(-A.c2, -A.c2);
+    const float2 d0 = make_float2(A.d0, A.d0), d1 = make_float2(A.d1, A.d1);
+#pragma unroll 8
+    for (int k = 0; k < cnt; k += 2) {
+        const float4 xy = *reinterpret_cast<const float4 *>(P + 4 * k);
+        const float4 zq = *reinterpret_cast<const float4 *>(P + 4 * k + 4);
+        const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
+        const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
+        const float2 dz = __fadd2_rn(make_float2(zq.x, zq.y), npz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps)));
+        bool in0 = r2.x < A.a2, in1 = r2.y < A.a2;
+        if (MODEL) {
+            const int2 f = *reinterpret_cast<const int2 *>(F + k);
+            in0 = in0 & (mi != f.x);
+            in1 = in1 & (mi != f.y);
+        } else {
+            in0 = in0 & (r2.x > 2.f * r2_eps<float>());
+            in1 = in1 & (r2.y > 2.f * r2_eps<float>());
+        }
+        const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 qj = make_float2(in0 ? zq.z : 0.f, in1 ? zq.w : 0.f);
+        const float2 g = __fadd2_rn(ri, __ffma2_rn(__ffma2_rn(nc2, r2, nc1), r2, nc0));     // ri - poly
+        const float2 fs = __ffma2_rn(ri2, ri, __ffma2_rn(d1, r2, d0));
+        const float2 sc = __fmul2_rn(qj, fs);
+        phi = fmaf(qj.x, g.x, phi);
+        ax = fmaf(sc.x, dx.x, ax); ay = fmaf(sc.x, dy.x, ay); az = fmaf(sc.x, dz.x, az);
+        phi = fmaf(qj.y, g.y, phi);
+        ax = fmaf(sc.y, dx.y, ax); ay = fmaf(sc.y, dy.y, ay); az = fmaf(sc.y, dz.y, az);
+    }
+}
 
 // MODEL: rigid-water completion -- pairs inside one molecule are skipped (the
 // exclusion kernel removes their smooth part); atoms that are not LJ sites get
@@ -86,7 +141,9 @@ template <typename T> struct ShortSmem {
 // cell list (i and j both LJ sites, j != i, r < a), in ascending slot order;
 // the constant shift of the cut-and-shifted potential is applied once per
 // counted pair at the end.
-template <typename T, bool MODEL, bool COUNT, bool LJP>
+// PACKED: the FP32 Coulomb pass takes its queued j's two at a time on packed
+// FP32 pairs (pair_steps_f32x2); otherwise, and for FP64, one at a time.
+template <typename T, bool MODEL, bool COUNT, bool LJP, bool PACKED>
 __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
@@ -96,6 +153,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short
     const int brick = blockIdx.x * SR_WARPS + wid;
     if (brick >= (LJP ? D.lj_nbricks : D.nbricks) || failed(A.status)) return;
     if (A.vl_ctl && A.vl_ctl[1] == 0 && A.vl_ctl[2] == 0) return;     // the Verlet-list path ran
+    constexpr bool PK = PACKED && sizeof(T) == 4 && !COUNT && !LJP;
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
     const int bx = brick % NB[0], by = (brick / NB[0]) % NB[1], bz = brick / (NB[0] * NB[1]);
     const int cx0 = bx * BD[0], cx1 = min(cx0 + BD[0], nx);
@@ -248,13 +306,21 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
                     const int q = (head + npend + __popc(m & lt)) & 63;
-                    S.sj[wid][q] = pj;
+                    if constexpr (PK) {
+                        T *e = &S.sp[wid][8 * (q >> 1) + (q & 1)];
+                        e[0] = pj.x; e[2] = pj.y; e[4] = pj.z; e[6] = pj.w;
+                    } else {
+                        S.sj[wid][q] = pj;
+                    }
                     if (MODEL) S.sf[wid][q] = fj;
                 }
                 npend += __popc(m);
                 __syncwarp();
                 if (npend >= 32) {
-                    pairs(head, 32);
+                    if constexpr (PK)
+                        pair_steps_f32x2<MODEL>(&S.sp[wid][4 * head], &S.sf[wid][head], 32, pi, mi, A, phi, ax, ay, az);
+                    else
+                        pairs(head, 32);
                     head ^= 32;
                     npend -= 32;
                     __syncwarp();
@@ -262,7 +328,19 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short
             }
         }
         if (npend > 0) {
-            pairs(head, npend);
+            if constexpr (PK) {
+                if ((npend & 1) && lane == 0) {
+                    // pad entry: charge zero at the box centre (finite distances, zero terms)
+                    T *e = &S.sp[wid][8 * ((head + npend) >> 1) + 1];
+                    e[0] = T(0.5) * (lo[0] + hi[0]); e[2] = T(0.5) * (lo[1] + hi[1]);
+                    e[4] = T(0.5) * (lo[2] + hi[2]); e[6] = T(0);
+                    S.sf[wid][head + npend] = -2;
+                }
+                __syncwarp();
+                pair_steps_f32x2<MODEL>(&S.sp[wid][4 * head], &S.sf[wid][head], npend, pi, mi, A, phi, ax, ay, az);
+            } else {
+                pairs(head, npend);
+            }
             __syncwarp();
         }
         if (valid) {
@@ -280,8 +358,18 @@ int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    if (model) k_short<T, true, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
-    else k_short<T, false, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    bool packed = false;
+    if constexpr (sizeof(T) == 4) packed = !a.scalar_pairs;
+    if constexpr (sizeof(T) == 4) {
+        if (packed) {
+            if (model) k_short<T, true, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+            else k_short<T, false, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+        }
+    }
+    if (!packed) {
+        if (model) k_short<T, true, false, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+        else k_short<T, false, false, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    }
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -292,7 +380,7 @@ int launch_short_lj(const ShortArgs<T> &a, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    k_short<T, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    k_short<T, false, false, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -303,7 +391,7 @@ int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    k_short<T, false, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    k_short<T, false, true, false, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

@@ -279,7 +279,8 @@ static int check_params(const msm_params *p)
     if (p->precision != MSM_FP32 && p->precision != MSM_FP64) return fail_msg(MSM_EINVAL, "unknown precision");
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
-    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE)) return fail_msg(MSM_EINVAL, "unknown flags");
+    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE | MSM_FLAG_SCALAR_PAIRS))
+        return fail_msg(MSM_EINVAL, "unknown flags");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
     int rad = 0;
@@ -664,6 +665,7 @@ static ShortArgs<T> short_args(msm_handle *h)
     s.cnt = nullptr;
     s.vl_ctl = nullptr;
     s.status = h->status.as<int>();
+    s.scalar_pairs = (h->p.flags & MSM_FLAG_SCALAR_PAIRS) != 0;
     return s;
 }
 
