@@ -39,7 +39,10 @@
 
 namespace msm {
 
-constexpr int SR_WARPS = 4;
+// One warp per CTA: a brick's warp frees its slot as soon as it is done (bricks
+// differ in size), and 32 resident one-warp CTAs per SM at 64 registers hide the
+// rsqrt and shared-load latency of the pair steps better than fewer, larger ones.
+constexpr int SR_WARPS = 1;
 constexpr int SR_MAXROWS = 320;     // row-list capacity per warp (a segment)
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
@@ -144,7 +147,7 @@ __device__ __forceinline__ void pair_steps_f32x2(const float *__restrict__ P, co
 // PACKED: the FP32 Coulomb pass takes its queued j's two at a time on packed
 // FP32 pairs (pair_steps_f32x2); otherwise, and for FP64, one at a time.
 template <typename T, bool MODEL, bool COUNT, bool LJP, bool PACKED>
-__global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 6 : 4) k_short(const ShortArgs<T> A)
+__global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
