@@ -62,9 +62,10 @@ extern "C" {
                                 same arrays, geometry and buffers)                         */
 #define MSM_FLAG_AUTOTUNE 2  /* time the short-range brick shapes on the first evaluation of
                                 each single-system geometry and keep the fastest           */
-#define MSM_FLAG_SCALAR_PAIRS 4  /* diagnostic, FP32 only: the short-range pass takes its
-                                queued neighbours one at a time instead of two per packed
-                                FP32x2 step; the same bits, slower (off by default)        */
+#define MSM_FLAG_SCALAR_PAIRS 4  /* diagnostic, FP32 only: the short-range Coulomb and LJ
+                                passes take their queued neighbours one at a time instead
+                                of two per packed FP32x2 step; the same bits, slower (off
+                                by default)                                                */
 
 /* Method parameters (Sec. 3).
  *   a          cutoff of the short-range part g* (nm); the level-k lattice

@@ -19,8 +19,8 @@
 // is dropped there; the rest enter a 64-entry FIFO in shared memory, which is
 // drained 32 at a time, so the pair loop runs full (and unrolled).  All lanes
 // read each queued j by broadcast.  Per candidate a lane evaluates one rsqrt and
-// 17 FP32 FMA-pipe operations; the FP32 Coulomb pass issues 13 of them (all but
-// the four accumulations) as packed FP32x2 instructions over two queued j's (the
+// 17 FP32 FMA-pipe operations (19 in the LJ pass); the FP32 passes issue all but
+// the four accumulations as packed FP32x2 instructions over two queued j's (the
 // FIFO then holds pair blocks x x y y z z q q, so each packed operand is one half
 // of a 16-byte load).  Pairs beyond a, the pair j = i and pairs inside one rigid
 // molecule get charge zero (exact zero contributions), never a branch.  More
@@ -82,7 +82,7 @@ template <typename T> struct ShortSmem {
     int rend[SR_WARPS][SR_MAXROWS];     // running end of each row in the concatenation
     union {
         vec4<T> sj[SR_WARPS][64];       // FIFO of queued j atoms, (x, y, z, q) each
-        T sp[SR_WARPS][64 * 4];         // FP32 Coulomb pass: the same FIFO as pair blocks,
+        T sp[SR_WARPS][64 * 4];         // FP32 packed passes: the same FIFO as pair blocks,
                                         // entries 2p, 2p+1 at [8p, 8p+8): x x y y z z q q
     };
     int sf[SR_WARPS][64];               // their molecule ids
@@ -95,7 +95,7 @@ template <typename T> struct ShortSmem {
 // rounding commutes with negation), and each accumulator takes its terms one j
 // at a time in queue order: the sums are bitwise those of the scalar loop.  P
 // points at pair block q0/2 of the warp's FIFO (q0 even), F at the molecule id of
-// entry q0; an odd cnt reads one pad entry of charge zero.
+// entry q0; an odd cnt reads one pad entry of charge zero beyond a of every lane.
 template <bool MODEL>
 __device__ __forceinline__ void pair_steps_f32x2(const float *__restrict__ P, const int *__restrict__ F,
                                                  const int cnt, const vec4<float> pi, const int mi,
@@ -136,6 +136,45 @@ __device__ __forceinline__ void pair_steps_f32x2(const float *__restrict__ P, co
     }
 }
 
+// The same for the O-O Lennard-Jones pass (j != i by distance): sigma^2/r^2 and
+// its powers, the energy difference and the force factor on packed pairs; the
+// negated values the scalar loop forms by operand negation come from negated
+// constants ((-s)(-s) = s s exactly, RN(-x) = -RN(x)), and le, lx, ly, lz take
+// one j at a time in queue order, as in the scalar loop.
+__device__ __forceinline__ void pair_steps_lj_f32x2(const float *__restrict__ P, const int cnt,
+                                                    const vec4<float> pi, const ShortArgs<float> &A, float &le,
+                                                    float &lx, float &ly, float &lz, int &npair)
+{
+    const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
+    const float2 eps = make_float2(r2_eps<float>(), r2_eps<float>());
+    const float2 ns2 = make_float2(-A.lj_s2, -A.lj_s2), two = make_float2(2.f, 2.f);
+    const float2 n24 = make_float2(-A.lj_24eps, -A.lj_24eps);
+#pragma unroll 8
+    for (int k = 0; k < cnt; k += 2) {
+        const float4 xy = *reinterpret_cast<const float4 *>(P + 4 * k);
+        const float4 zq = *reinterpret_cast<const float4 *>(P + 4 * k + 4);
+        const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), npx);
+        const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), npy);
+        const float2 dz = __fadd2_rn(make_float2(zq.x, zq.y), npz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps)));
+        const bool in0 = (r2.x < A.a2) & (r2.x > 2.f * r2_eps<float>());
+        const bool in1 = (r2.y < A.a2) & (r2.y > 2.f * r2_eps<float>());
+        const float2 ri = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 nsr2 = __fmul2_rn(ns2, make_float2(in0 ? ri2.x : 0.f, in1 ? ri2.y : 0.f));   // -sigma^2/r^2
+        const float2 nsr6 = __fmul2_rn(__fmul2_rn(nsr2, nsr2), nsr2);                           // -(sr2^3)
+        const float2 sr12 = __fmul2_rn(nsr6, nsr6);
+        const float2 d = __fadd2_rn(sr12, nsr6);                                               // sr12 - sr6
+        const float2 nfl = __fmul2_rn(__fmul2_rn(n24, ri2), __ffma2_rn(two, sr12, nsr6));       // -fl
+        le = fmaf(A.lj_4eps, d.x, le);
+        npair += in0 ? 1 : 0;
+        lx = fmaf(nfl.x, dx.x, lx); ly = fmaf(nfl.x, dy.x, ly); lz = fmaf(nfl.x, dz.x, lz);
+        le = fmaf(A.lj_4eps, d.y, le);
+        npair += in1 ? 1 : 0;
+        lx = fmaf(nfl.y, dx.y, lx); ly = fmaf(nfl.y, dy.y, ly); lz = fmaf(nfl.y, dz.y, lz);
+    }
+}
+
 // MODEL: rigid-water completion -- pairs inside one molecule are skipped (the
 // exclusion kernel removes their smooth part); atoms that are not LJ sites get
 // a zero LJ output.
@@ -144,8 +183,9 @@ __device__ __forceinline__ void pair_steps_f32x2(const float *__restrict__ P, co
 // cell list (i and j both LJ sites, j != i, r < a), in ascending slot order;
 // the constant shift of the cut-and-shifted potential is applied once per
 // counted pair at the end.
-// PACKED: the FP32 Coulomb pass takes its queued j's two at a time on packed
-// FP32 pairs (pair_steps_f32x2); otherwise, and for FP64, one at a time.
+// PACKED: the FP32 Coulomb and LJ passes take their queued j's two at a time on
+// packed FP32 pairs (pair_steps_f32x2, pair_steps_lj_f32x2); otherwise, and for
+// FP64 and the pair count, one at a time.
 template <typename T, bool MODEL, bool COUNT, bool LJP, bool PACKED>
 __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_short(const ShortArgs<T> A)
 {
@@ -156,7 +196,7 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
     const int brick = blockIdx.x * SR_WARPS + wid;
     if (brick >= (LJP ? D.lj_nbricks : D.nbricks) || failed(A.status)) return;
     if (A.vl_ctl && A.vl_ctl[1] == 0 && A.vl_ctl[2] == 0) return;     // the Verlet-list path ran
-    constexpr bool PK = PACKED && sizeof(T) == 4 && !COUNT && !LJP;
+    constexpr bool PK = PACKED && sizeof(T) == 4 && !COUNT;
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
     const int bx = brick % NB[0], by = (brick / NB[0]) % NB[1], bz = brick / (NB[0] * NB[1]);
     const int cx0 = bx * BD[0], cx1 = min(cx0 + BD[0], nx);
@@ -320,7 +360,9 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
                 npend += __popc(m);
                 __syncwarp();
                 if (npend >= 32) {
-                    if constexpr (PK)
+                    if constexpr (PK && LJP)
+                        pair_steps_lj_f32x2(&S.sp[wid][4 * head], 32, pi, A, le, lx, ly, lz, npair);
+                    else if constexpr (PK)
                         pair_steps_f32x2<MODEL>(&S.sp[wid][4 * head], &S.sf[wid][head], 32, pi, mi, A, phi, ax, ay, az);
                     else
                         pairs(head, 32);
@@ -333,14 +375,18 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
         if (npend > 0) {
             if constexpr (PK) {
                 if ((npend & 1) && lane == 0) {
-                    // pad entry: charge zero at the box centre (finite distances, zero terms)
+                    // pad entry: charge zero, 2a beyond the box in x (out of range of every
+                    // lane, finite distances: exact zero terms in both passes)
                     T *e = &S.sp[wid][8 * ((head + npend) >> 1) + 1];
-                    e[0] = T(0.5) * (lo[0] + hi[0]); e[2] = T(0.5) * (lo[1] + hi[1]);
+                    e[0] = lo[0] - T(2) * A.a; e[2] = T(0.5) * (lo[1] + hi[1]);
                     e[4] = T(0.5) * (lo[2] + hi[2]); e[6] = T(0);
                     S.sf[wid][head + npend] = -2;
                 }
                 __syncwarp();
-                pair_steps_f32x2<MODEL>(&S.sp[wid][4 * head], &S.sf[wid][head], npend, pi, mi, A, phi, ax, ay, az);
+                if constexpr (LJP)
+                    pair_steps_lj_f32x2(&S.sp[wid][4 * head], npend, pi, A, le, lx, ly, lz, npair);
+                else
+                    pair_steps_f32x2<MODEL>(&S.sp[wid][4 * head], &S.sf[wid][head], npend, pi, mi, A, phi, ax, ay, az);
             } else {
                 pairs(head, npend);
             }
@@ -383,7 +429,12 @@ int launch_short_lj(const ShortArgs<T> &a, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
-    k_short<T, false, false, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    bool packed = false;
+    if constexpr (sizeof(T) == 4) {
+        packed = !a.scalar_pairs;
+        if (packed) k_short<T, false, false, true, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+    }
+    if (!packed) k_short<T, false, false, true, false><<<grid, SR_WARPS * 32, 0, st>>>(a);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

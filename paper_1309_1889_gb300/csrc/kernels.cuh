@@ -64,7 +64,7 @@ template <typename T> struct ShortArgs {
     double *cnt;           // counting mode: per sorted atom, number of j with r_ij < a
     const int *vl_ctl;     // Verlet-list flags (nullable): skip when the list path ran
     const int *status;
-    bool scalar_pairs;     // FP32 pair pass: one queued j per step instead of packed pairs
+    bool scalar_pairs;     // FP32 pair passes: one queued j per step instead of packed pairs
 };
 // model = true: skip pairs of the same molecule (their smooth part is removed by
 // the exclusion kernel) and write a zero LJ output for atoms that are not LJ

@@ -1,9 +1,10 @@
-"""The FP32 short-range pass on packed FP32x2 pairs against the scalar loop.
+"""The FP32 short-range passes on packed FP32x2 pairs against the scalar loop.
 
 The packed step does, for each of its two queued neighbours, the IEEE
 operations of the scalar loop in the same order, and every accumulator still
 takes one neighbour at a time in queue order; so the two give the same bits,
-for the short-range sums themselves and for everything computed from them.
+for the short-range sums themselves and for everything computed from them
+(the water model's totals include the O-O Lennard-Jones pass).
 MSM_FLAG_SCALAR_PAIRS selects the scalar loop.  The cases cover odd queue
 tails (the packed step then reads one pad entry of charge zero), systems with
 no pair at all, both models, a batch of uneven systems and the 1,000,000-atom
