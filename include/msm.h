@@ -11,10 +11,12 @@
  * Conventions shared by every entry point
  *   - Units: nm, ps, e, amu, kJ/mol; k_e = 1/(4 pi eps0) = 138.935458 kJ mol^-1 nm e^-2.
  *   - Arrays are plain C-contiguous FP64 (atoms x 3 for vectors).  Array
- *     arguments may be device pointers or host pointers (pageable or
- *     pinned); the library detects which and stages host data through its
- *     own device buffers.  The caller keeps ownership of every array; the
- *     library only borrows it for the duration of the call.
+ *     arguments may be device pointers of the current device or host
+ *     pointers (pageable or pinned); the library detects which and stages
+ *     host data through its own device buffers.  An array allocated on
+ *     another GPU is rejected with MSM_EINVAL before anything is launched.
+ *     The caller keeps ownership of every array; the library only borrows
+ *     it for the duration of the call.
  *   - box[6] = {x0, y0, z0, Lx, Ly, Lz} (host memory): the open,
  *     non-periodic domain of the grids.  An atom is inside when, on every
  *     axis, t = (x - x0) * (1/h) (IEEE FP64, 1/h rounded once) satisfies
@@ -277,7 +279,7 @@ MSM_API int  msm_count_pairs(msm_handle *h, int64_t *ordered_pairs);
  * Scratch lives in a 24 MiB static device array inside the library, held by
  * every GPU that loads it until the process exits: 4 bytes per atom plus 4
  * per cell must fit (about 1 M atoms with 4 M cells); larger requests return
- * MSM_EINVAL, as do host pointers.  The first call on a device, with that
+ * MSM_EINVAL, as do host pointers and arrays on another GPU.  The first call on a device, with that
  * device current, looks up the array's device address; make that first call
  * before any stream capture.  Every call reuses the same array and clears
  * the parts that must start at zero; calls that overlap on the GPU (other

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "kernels.cuh"
@@ -92,12 +93,41 @@ static void release(DevBuf &b)
     b.cap = 0;
 }
 
+// Device memory of the current device, or managed memory: used in place.
+// Anything else is treated as host memory and staged (see foreign_device).
 static bool on_device(const void *p)
 {
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.device == dev;
+}
+
+// A device allocation made on a GPU other than the current one.  The kernels
+// run on the current device and would dereference it there (an illegal
+// address without peer access), and staging it as host memory is wrong too,
+// so every entry point rejects such arrays with MSM_EINVAL before any launch.
+static bool foreign_device(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return true; }
+    return at.device != dev;
+}
+
+static int check_arrays(std::initializer_list<const void *> ptrs)
+{
+    for (const void *p : ptrs)
+        if (foreign_device(p))
+            return fail_msg(MSM_EINVAL, "an array lives on another GPU than the current device");
+    return MSM_OK;
 }
 
 // ------------------------------------------------------------------ handle
@@ -1011,6 +1041,7 @@ static int forces_impl(msm_handle *h, int B, const SysIn *sys, const double *pos
         n += sys[s].n;
     }
     if (n > 0 && (!pos || !q)) return fail_msg(MSM_EINVAL, "pos and q are required");
+    TRY(check_arrays({pos, q, lj, energies, forces, pot, virials}));
     const size_t nn = (size_t)n;
     EvalIO io;
     const void *dp, *dq, *dl;
@@ -1319,6 +1350,7 @@ extern "C" int md_run(msm_handle *h, msm_system *sys, double dt, int32_t n_steps
 {
     if (!h) return fail_msg(MSM_EINVAL, "handle is NULL");
     TRY(check_system(sys));
+    TRY(check_arrays({sys->x, sys->v, sys->q, sys->m, sys->lj, sys->f, uk}));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nn = (size_t)sys->n;
     SysIn si;
@@ -1380,6 +1412,7 @@ static int gather_systems(msm_handle *h, int B, const msm_system *systems, std::
         if (S.n < 0 || S.n_mol < 0 || 3 * S.n_mol > S.n) return fail_msg(MSM_EINVAL, "bad atom counts (system %d)", b);
         if (S.n > 0 && (!S.x || !S.q || (need_v && (!S.v || !S.m))))
             return fail_msg(MSM_EINVAL, "system %d lacks x, v, q or m", b);
+        TRY(check_arrays({S.x, S.v, S.q, S.m, S.lj, S.f}));
         sys[(size_t)b].n = S.n; sys[(size_t)b].n_mol = S.n_mol;
         memcpy(sys[(size_t)b].box, S.box, sizeof S.box);
         off[(size_t)b + 1] = off[(size_t)b] + S.n;
@@ -1439,6 +1472,7 @@ extern "C" int md_run_batched(msm_handle *h, int32_t n_sys, msm_system *systems,
                               double *uk, void *stream)
 {
     if (!h || n_sys < 1 || !systems) return fail_msg(MSM_EINVAL, "bad batched arguments");
+    TRY(check_arrays({uk}));
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<SysIn> sys;
     std::vector<int64_t> off;
@@ -1558,6 +1592,7 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
         return fail_msg(MSM_EINVAL, "G and F must span the same slice length");
     const msm_system &s0 = *state0;
     if (s0.n <= 0 || !s0.x || !s0.v || !s0.q || !s0.m) return fail_msg(MSM_EINVAL, "state0 incomplete");
+    TRY(check_arrays({s0.x, s0.v, s0.q, s0.m, s0.lj, slices_x, slices_v}));
     cudaStream_t st = (cudaStream_t)stream;
     msm_handle *hG = nullptr, *hF = nullptr;
     TRY(msm_create(G, &hG));

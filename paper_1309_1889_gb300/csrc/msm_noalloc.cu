@@ -61,11 +61,18 @@ __global__ void k_noalloc_keys(int n, const double *__restrict__ pos, CellGeom g
     atomicAdd(&count[k], 1);
 }
 
+// Device memory of the current device (the one the kernels run on), or
+// managed memory.  Host memory and allocations on another GPU are refused:
+// the kernels would dereference them on the current device.
 static bool device_accessible(const void *p)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    if (at.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.device == dev;
 }
 
 extern "C" int msm_cell_list_noalloc(int64_t n, const double *pos, const double box[6], double h, int32_t *perm,
@@ -99,7 +106,7 @@ extern "C" int msm_cell_list_noalloc(int64_t n, const double *pos, const double 
         return fail_msg(MSM_EINVAL, "msm_cell_list_noalloc: %lld atoms and %lld cells need %zu bytes of scratch, "
                         "more than its fixed %u", (long long)n, (long long)ncells, need, MSM_NOALLOC_SCRATCH_BYTES);
     if ((n > 0 && (!device_accessible(pos) || !device_accessible(perm))) || !device_accessible(cell_start))
-        return fail_msg(MSM_EINVAL, "msm_cell_list_noalloc takes device arrays only");
+        return fail_msg(MSM_EINVAL, "msm_cell_list_noalloc takes device arrays of the current device only");
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;

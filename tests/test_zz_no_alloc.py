@@ -83,3 +83,47 @@ def test_noalloc_rejects_oversized_requests(api, torch):
     rc = api.lib().msm_cell_list_noalloc(10, C.c_void_p(pos.data_ptr()), big, H, C.c_void_p(perm.data_ptr()),
                                          C.c_void_p(start.data_ptr()), 401 ** 3 + 1, None)
     assert rc == -1 and b"scratch" in api.lib().msm_last_error()
+
+
+def _noalloc_rc(api, torch, pos_np, box, ncells):
+    pos = torch.tensor(pos_np, dtype=torch.float64, device="cuda")
+    n = pos_np.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    start = torch.empty(ncells + 1, dtype=torch.int32, device="cuda")
+    cbox = (C.c_double * 6)(*[float(v) for v in box])
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return api.lib().msm_cell_list_noalloc(n, C.c_void_p(pos.data_ptr()), cbox, H, C.c_void_p(perm.data_ptr()),
+                                           C.c_void_p(start.data_ptr()), ncells + 1, stream)
+
+
+def test_noalloc_recovers_after_failed_calls(api, torch):
+    """A call that fails on the device (an atom outside the box, a NaN coordinate)
+    leaves its status word and histogram in the shared array; the next valid call
+    must clear them and still give the regular path's cell list bit for bit."""
+    s = inputs.water_box(3000, 3.1, margin=0.5, with_velocities=False)
+    ref = _regular(api, torch, s)
+    nc = [int(np.floor(s.box[3 + k] / H)) + 1 for k in range(3)]
+    ncells = nc[0] * nc[1] * nc[2]
+    bad = s.pos.copy(); bad[123, 1] = s.box[1] - 0.01                  # below the box
+    assert _noalloc_rc(api, torch, bad, s.box, ncells) == -2           # MSM_ERANGE
+    got = _noalloc(api, torch, s)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    bad = s.pos.copy(); bad[7, 0] = np.nan
+    assert _noalloc_rc(api, torch, bad, s.box, ncells) == -1           # MSM_EINVAL
+    got = _noalloc(api, torch, s)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_noalloc_rejects_arrays_of_another_gpu(api, torch):
+    """Arrays allocated on a GPU other than the current one are refused before any launch."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    s = inputs.random_cloud(10, 1.0, seed=1)
+    pos = torch.tensor(s.pos, dtype=torch.float64, device="cuda:1")
+    perm = torch.empty(10, dtype=torch.int32, device="cuda:0")
+    start = torch.empty(6 ** 3 + 1, dtype=torch.int32, device="cuda:0")
+    with torch.cuda.device(0):
+        box = (C.c_double * 6)(*[float(v) for v in s.box])
+        rc = api.lib().msm_cell_list_noalloc(10, C.c_void_p(pos.data_ptr()), box, H, C.c_void_p(perm.data_ptr()),
+                                             C.c_void_p(start.data_ptr()), 6 ** 3 + 1, None)
+    assert rc == -1 and b"current device" in api.lib().msm_last_error()
