@@ -71,6 +71,7 @@ def lib():
         L.orc_interpolate.restype = None; L.orc_interpolate.argtypes = [p, p, d, p, i64, p, p, p, p]
         L.orc_msm.restype = i; L.orc_msm.argtypes = [p, i, i64, p, p, p, p, p, p, p]
         L.orc_direct.restype = None; L.orc_direct.argtypes = [i64, p, p, d, p, p, p]
+        L.orc_cutoff.restype = i; L.orc_cutoff.argtypes = [i, d, d, d, i64, i64, p, p, p, p, p]
         L.orc_model_forces.restype = i
         L.orc_model_forces.argtypes = [p, i, i64, i64, p, p, p, p, p, p, p]
         L.orc_md_run.restype = i
@@ -268,17 +269,32 @@ def direct(pos, q, ke=KE):
     return dict(energy=float(e[0]), forces=f, pot=p)
 
 
+METHODS = {"msm": 0, "cutoff": 1, "wolf": 2}
+
+
+def cutoff(pos, q, a, method="cutoff", alpha=0.0, ke=KE, n_mol=0):
+    """Coarse-propagator electrostatics (Sec. 5): simple cutoff or Wolf summation,
+    brute force over all pairs.  dict(energy, forces, pot)."""
+    pos = _f64(pos); q = _f64(q)
+    n = pos.shape[0]
+    e = np.zeros(1); f = np.zeros((n, 3)); p = np.zeros(n)
+    _check(lib().orc_cutoff(METHODS[method], float(a), float(alpha), float(ke), n, int(n_mol), _ptr(pos), _ptr(q),
+                            _ptr(e), _ptr(f), _ptr(p)))
+    return dict(energy=float(e[0]), forces=f, pot=p)
+
+
 # --- water model, dynamics, parareal ----------------------------------------
 
 LJ_SIGMA = 0.315061    # nm, O-O
 LJ_EPSILON = 0.6364    # kJ/mol
 
 
-def model_params(a, h, ke=KE, sigma=LJ_SIGMA, eps=LJ_EPSILON, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0):
+def model_params(a, h, ke=KE, sigma=LJ_SIGMA, eps=LJ_EPSILON, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
+                 method="msm", wolf_alpha=0.0):
     if d_hh is None:
         import math
         d_hh = 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
-    return _f64([a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_width])
+    return _f64([a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_width, METHODS[method], wolf_alpha])
 
 
 def model_forces(sys, a, h, levels, ke=KE, pos=None, **kw):
@@ -317,11 +333,13 @@ def project_rigid(x, v, mass, n_mol, d_oh=0.09572, d_hh=None):
 
 
 def parareal(sys, G: dict, F: dict, n_slices, max_iter, tol, ke=KE):
-    """G, F: dict(a, h, levels, dt, steps).  Returns (xs, vs, iters, last_dx, status)."""
+    """G, F: dict(a, h, levels, dt, steps[, method, wolf_alpha, wall_k, wall_width]).
+    Returns (xs, vs, iters, last_dx, status)."""
     n = sys.n
 
     def pack(p):
-        mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0))
+        mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0),
+                           method=p.get("method", "msm"), wolf_alpha=p.get("wolf_alpha", 0.0))
         return _f64(list(mdp) + [p["dt"], p["steps"], p["levels"]])
 
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))

@@ -26,6 +26,9 @@
  *   orc_interpolate ......... Sec. 3, u_i^long = sum_mu phi^0_mu(r_i) u^0_mu (+ gradient)
  *   orc_msm ................. Sec. 3 example steps 1-9, U_i = k_e (u^short + u^long)
  *   orc_direct .............. Sec. 2, eq. (coulomb), read as sum over i<j
+ *   orc_cutoff .............. Sec. 5, the coarse propagator's electrostatics:
+ *                             simple cutoff (Coulomb's law for pairs within a)
+ *                             or Wolf summation (damped, shifted, neutralised)
  *   orc_md_run .............. Sec. 2, F = -dU/dr and velocity Verlet
  *   orc_parareal ............ Sec. 4, lambda^{k+1}_{n+1} = G(lambda^{k+1}_n)
  *                                       + F(lambda^k_n) - G(lambda^k_n)
@@ -583,6 +586,69 @@ void orc_direct(int64_t n, const double *pos, const double *q, double ke,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cutoff electrostatics for the coarse propagator (Sec. 5)                  */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_METHOD_MSM 0
+#define ORC_METHOD_CUTOFF 1
+#define ORC_METHOD_WOLF 2
+#define ORC_PI 3.14159265358979323846
+
+/* Sec. 5 lists the coarse approximations G the paper weighs and keeps two:
+ *   method 1, simple cutoff: Coulomb's law between the pairs closer than the
+ *     cutoff a, nothing beyond (the paper's chosen G):
+ *       U = 1/2 sum_i sum_{j != i, r_ij < a} k_e q_i q_j / r_ij;
+ *   method 2, Wolf summation (Wolf, Keblinski, Phillpot & Eggebrecht 1999,
+ *     the paper's proposed later G): the pair term damped by erfc, shifted to
+ *     zero at a, and the charge-neutralisation self term,
+ *       U = 1/2 sum_i sum_{j != i, r_ij < a} k_e q_i q_j [erfc(alpha r)/r - erfc(alpha a)/a]
+ *           - k_e [erfc(alpha a)/(2a) + alpha/sqrt(pi)] sum_i q_i^2.
+ * Potentials phi_i = dU/dq_i (so U = 1/2 sum q_i phi_i), forces the exact
+ * gradient F_i = -dU/dr_i (the shift is constant inside a).  Pairs inside one
+ * rigid triple (atoms 3m..3m+2, m < n_mol) are skipped: with no grid there is
+ * no smooth part to remove.  Brute force over all pairs, FP64. */
+int orc_cutoff(int method, double a, double alpha, double ke, int64_t n, int64_t n_mol, const double *pos,
+               const double *q, double *energy, double *forces, double *pot)
+{
+    if ((method != ORC_METHOD_CUTOFF && method != ORC_METHOD_WOLF) || !(a > 0) || !(alpha >= 0)) return ORC_EINVAL;
+    const int wolf = method == ORC_METHOD_WOLF;
+    const double shift = wolf ? erfc(alpha * a) / a : 0.0;
+    const double selfc = wolf ? erfc(alpha * a) / a + 2.0 * alpha / sqrt(ORC_PI) : 0.0;
+    double *phi = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!phi) return ORC_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t mi = i < 3 * n_mol ? i / 3 : -1 - i;
+        double p = 0, fx = 0, fy = 0, fz = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (j < 3 * n_mol && j / 3 == mi) continue;
+            double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1], dz = pos[3 * i + 2] - pos[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (!(r < a)) continue;
+            double g, mdg;                               /* pair term and -d/dr of it */
+            if (wolf) {
+                g = erfc(alpha * r) / r - shift;
+                mdg = erfc(alpha * r) / (r * r) + 2.0 * alpha / sqrt(ORC_PI) * exp(-alpha * alpha * r * r) / r;
+            } else {
+                g = 1.0 / r;
+                mdg = 1.0 / (r * r);
+            }
+            p += q[j] * g;
+            double s = q[i] * q[j] * mdg / r;
+            fx += s * dx; fy += s * dy; fz += s * dz;
+        }
+        phi[i] = ke * (p - selfc * q[i]);
+        if (forces) { forces[3 * i] = ke * fx; forces[3 * i + 1] = ke * fy; forces[3 * i + 2] = ke * fz; }
+    }
+    double U = 0;
+    for (int64_t i = 0; i < n; i++) { U += q[i] * phi[i]; if (pot) pot[i] = phi[i]; }
+    if (energy) *energy = 0.5 * U;
+    free(phi);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Model completion for rigid 3-site water (outside the paper)               */
 /* ------------------------------------------------------------------------ */
 
@@ -599,9 +665,14 @@ void orc_direct(int64_t n, const double *pos, const double *q, double ke,
  *   - a harmonic flat-bottom wall keeping atoms inside the open domain (the
  *     paper states no boundary conditions): an atom closer than wall_w to a
  *     face of the box gets 1/2 wall_k (wall_w - distance)^2 (wall_k = 0: off).
- * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh, wall_k, wall_w}. */
+ * The electrostatics is the MSM (method 0) or, for a coarse propagator, one
+ * of the cutoff methods of orc_cutoff (1 simple cutoff, 2 Wolf summation with
+ * damping wolf_alpha), which skip the intramolecular pairs instead of
+ * subtracting them.
+ * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh, wall_k, wall_w, method, wolf_alpha}. */
 typedef struct {
-    double a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_w;
+    double a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_w, alpha;
+    int method;
     int l;
     int64_t n, n_mol;
     const double *q, *m;
@@ -614,6 +685,7 @@ static void model_from(orc_model *md, const double *mdp, int l, int64_t n, int64
 {
     md->a = mdp[0]; md->h = mdp[1]; md->ke = mdp[2]; md->sigma = mdp[3]; md->eps = mdp[4];
     md->d_oh = mdp[5]; md->d_hh = mdp[6]; md->wall_k = mdp[7]; md->wall_w = mdp[8];
+    md->method = (int)mdp[9]; md->alpha = mdp[10];
     md->l = l; md->n = n; md->n_mol = n_mol;
     md->q = q; md->m = m; md->lj = lj; md->box = box;
 }
@@ -624,11 +696,23 @@ static int model_forces(const orc_model *md, const double *x, double *U, double 
     int64_t n = md->n;
     double *phi = pot ? pot : malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     if (!phi) return ORC_ENOMEM;
-    int rc = orc_msm(prm, md->l, n, x, md->q, md->box, U, F, phi, NULL);
+    int rc;
+    if (md->method == ORC_METHOD_MSM) {
+        rc = orc_msm(prm, md->l, n, x, md->q, md->box, U, F, phi, NULL);
+    } else {
+        /* the cutoff methods need no grid, but atoms must still lie in the open
+         * domain (the binning contract, the same for every method) */
+        int64_t *key = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        if (!key) { if (!pot) free(phi); return ORC_ENOMEM; }
+        rc = orc_bin(n, x, md->box, md->h, NULL, key, NULL, NULL);
+        free(key);
+        if (rc == ORC_OK) rc = orc_cutoff(md->method, md->a, md->alpha, md->ke, n, md->n_mol, x, md->q, U, F, phi);
+    }
     if (rc) { if (!pot) free(phi); return rc; }
     double dU = 0;
-    /* intramolecular exclusions: subtract k_e q_i q_j / r for (O,H1), (O,H2), (H1,H2) */
-    for (int64_t mo = 0; mo < md->n_mol; mo++) {
+    /* intramolecular exclusions (MSM only: the cutoff methods skipped these pairs):
+     * subtract k_e q_i q_j / r for (O,H1), (O,H2), (H1,H2) */
+    for (int64_t mo = 0; md->method == ORC_METHOD_MSM && mo < md->n_mol; mo++) {
         static const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
         for (int c = 0; c < 3; c++) {
             int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
@@ -837,7 +921,7 @@ int orc_md_run(const double *mdp, int l, int64_t n, int64_t n_mol, double *x, do
  *              bitwise the bracket is exactly 0 and slice n+1 equals F);
  *   stop when max_{n,i,d} |x^{k+1} - x^k| <= tol, or after max_iter iterations.
  * slices_x/v: (n_slices+1) * n * 3, slot 0 holds state0 on entry.
- * gp/fp: {mdp (9 values), dt, steps, levels}. */
+ * gp/fp: {mdp (11 values), dt, steps, levels}. */
 /* Parareal's correction F + (G_new - G_old) adds positions of rigid molecules
  * taken from different trajectories, so the corrected molecules need not have
  * the rigid bond lengths; a grossly distorted one would start the next coarse
@@ -916,10 +1000,10 @@ int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
                  int *iters_done, double *last_dx)
 {
     orc_model G, F;
-    model_from(&G, gp, (int)gp[11], n, n_mol, q, m, lj, box);
-    model_from(&F, fp, (int)fp[11], n, n_mol, q, m, lj, box);
-    double dtG = gp[9], dtF = fp[9];
-    int sG = (int)gp[10], sF = (int)fp[10];
+    model_from(&G, gp, (int)gp[13], n, n_mol, q, m, lj, box);
+    model_from(&F, fp, (int)fp[13], n, n_mol, q, m, lj, box);
+    double dtG = gp[11], dtF = fp[11];
+    int sG = (int)gp[12], sF = (int)fp[12];
     size_t sz = 3 * (size_t)n;
     int rc = ORC_OK;
     double *gold_x = malloc(sizeof(double) * sz * (size_t)n_slices), *gold_v = malloc(sizeof(double) * sz * (size_t)n_slices);

@@ -63,17 +63,24 @@ def _run_serial(s, p, n_slices):
     xs = [s.pos.copy()]; vs = [s.vel.copy()]
     for _ in range(n_slices):
         x, v, _ = oracle.md_run(s, a=p["a"], h=p["h"], levels=p["levels"], dt=p["dt"], n_steps=p["steps"],
-                                x=xs[-1], v=vs[-1])
+                                x=xs[-1], v=vs[-1], method=p.get("method", "msm"),
+                                wolf_alpha=p.get("wolf_alpha", 0.0))
         xs.append(x); vs.append(v)
     return np.array(xs), np.array(vs)
 
 
-@pytest.fixture(scope="module")
-def pr_setup():
+# coarse propagators: MSM with a shorter cutoff and coarser grid, the simple cutoff
+# (Sec. 5, the paper's choice) and Wolf summation (Sec. 5, its proposed later G)
+COARSE = {"msm": dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=2),
+          "cutoff": dict(a=0.8, h=0.5, levels=1, dt=0.004, steps=2, method="cutoff"),
+          "wolf": dict(a=0.8, h=0.5, levels=1, dt=0.004, steps=2, method="wolf", wolf_alpha=2.5)}
+
+
+@pytest.fixture(scope="module", params=sorted(COARSE))
+def pr_setup(request):
     s = inputs.water_box(15, 0.8, margin=0.5, seed=5, vel_seed=6)
     F = dict(a=1.2, h=0.25, levels=2, dt=0.002, steps=4)
-    G = dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=2)
-    return s, F, G
+    return s, F, COARSE[request.param]
 
 
 def test_parareal_zero_iterations_is_the_coarse_sweep(pr_setup):
