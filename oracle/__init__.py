@@ -78,6 +78,8 @@ def lib():
         L.orc_md_run.argtypes = [p, i, i64, i64, p, p, p, p, p, p, d, i, p]
         L.orc_parareal.restype = i
         L.orc_parareal.argtypes = [p, p, i64, i64, p, p, p, p, i, i, d, p, p, p, p]
+        L.orc_parareal_window.restype = i
+        L.orc_parareal_window.argtypes = [p, p, i64, i64, p, p, p, p, i, i, i, d, p, p, p, p]
         L.orc_num_threads.restype = i; L.orc_num_threads.argtypes = []
         L.orc_project_rigid.restype = i
         L.orc_project_rigid.argtypes = [i64, i64, p, d, d, p, p]
@@ -330,6 +332,28 @@ def project_rigid(x, v, mass, n_mol, d_oh=0.09572, d_hh=None):
     x = _f64(x).copy(); v = _f64(v).copy()
     _check(lib().orc_project_rigid(len(mass), int(n_mol), _ptr(_f64(mass)), float(d_oh), float(d_hh), _ptr(x), _ptr(v)))
     return x, v
+
+
+def _pack(p, ke):
+    mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0),
+                       method=p.get("method", "msm"), wolf_alpha=p.get("wolf_alpha", 0.0))
+    return _f64(list(mdp) + [p["dt"], p["steps"], p["levels"]])
+
+
+def parareal_window(sys, G: dict, F: dict, n_slices, window, max_iter, tol, ke=KE):
+    """Parareal over a sliding window of at most `window` slices (Sec. 4).
+    Returns (xs, vs, iters, last_dx, status)."""
+    n = sys.n
+    xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))
+    xs[0] = sys.pos; vs[0] = sys.vel
+    it = C.c_int(0); dx = C.c_double(0)
+    lj = np.ascontiguousarray(sys.lj, dtype=np.uint8)
+    rc = lib().orc_parareal_window(_ptr(_pack(G, ke)), _ptr(_pack(F, ke)), n, int(sys.n_mol), _ptr(_f64(sys.q)),
+                                   _ptr(_f64(sys.mass)), _ptr(lj), _ptr(_f64(sys.box)), int(n_slices), int(window),
+                                   int(max_iter), float(tol), _ptr(xs), _ptr(vs), C.byref(it), C.byref(dx))
+    if rc not in (0, -6):
+        _check(rc)
+    return xs, vs, it.value, dx.value, rc
 
 
 def parareal(sys, G: dict, F: dict, n_slices, max_iter, tol, ke=KE):

@@ -32,6 +32,8 @@
  *   orc_md_run .............. Sec. 2, F = -dU/dr and velocity Verlet
  *   orc_parareal ............ Sec. 4, lambda^{k+1}_{n+1} = G(lambda^{k+1}_n)
  *                                       + F(lambda^k_n) - G(lambda^k_n)
+ *   orc_parareal_window ..... Sec. 4, the same recurrence over a sliding
+ *                             computational window of at most W slices
  *   orc_project_rigid ....... water completion: corrected parareal states
  *                             projected back onto the rigid constraints
  * Readings of points the paper leaves open (self-interaction, open boundaries,
@@ -1052,6 +1054,95 @@ int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
     if (*last_dx > tol) rc = ORC_ENOCONV;
 out:
     free(gold_x); free(gold_v); free(f_x); free(f_v); free(nx); free(nv); free(tx); free(tv);
+    return rc;
+}
+
+/* Parareal over a sliding computational window (Sec. 4: the iteration runs on
+ * a window of T_W time points; Sec. 6.1 sizes the window).  The paper states
+ * the window but not how it moves; reading: the window holds slices [b, e),
+ * e - b <= W.  Each iteration applies the recurrence of orc_parareal to the
+ * window (F of every window slice from the current iterate, then the
+ * sequential correction sweep from the window's first state lambda_b, which
+ * is final).  A slice n is converged when max |x^{k+1}_{n+1} - x^k_{n+1}| <=
+ * tol; b advances past slice b (its end F(lambda_b) is exact once computed)
+ * and past the converged slices that follow it, and the window is refilled up
+ * to W slices, the new slices' first iterate being the coarse propagation G
+ * from the last state of the window.  Stops when b reaches n_slices or after
+ * max_iter iterations.  With W = n_slices and tol = 0 the iterates equal
+ * orc_parareal's bit for bit (which needs one more iteration to see that the
+ * last slice no longer changes); with W = 1 it is the serial fine run.
+ * slices_x/v: (n_slices+1) * n * 3, slot 0 = state0 on entry; on return the
+ * converged slice ends are final and the rest the last iterate.
+ * *iters_done counts iterations, *last_dx is the largest change of the last one. */
+int orc_parareal_window(const double *gp, const double *fp, int64_t n, int64_t n_mol,
+                        const double *q, const double *m, const unsigned char *lj, const double *box,
+                        int n_slices, int window, int max_iter, double tol, double *slices_x, double *slices_v,
+                        int *iters_done, double *last_dx)
+{
+    if (window < 1 || n_slices < 1) return ORC_EINVAL;
+    orc_model G, F;
+    model_from(&G, gp, (int)gp[13], n, n_mol, q, m, lj, box);
+    model_from(&F, fp, (int)fp[13], n, n_mol, q, m, lj, box);
+    double dtG = gp[11], dtF = fp[11];
+    int sG = (int)gp[12], sF = (int)fp[12];
+    const size_t sz = 3 * (size_t)n, ns = (size_t)n_slices;
+    int rc = ORC_OK;
+    /* per slice n: its coarse propagation of the current iterate (gold), its fine one (f) */
+    double *gold_x = malloc(sizeof(double) * sz * ns), *gold_v = malloc(sizeof(double) * sz * ns);
+    double *f_x = malloc(sizeof(double) * sz * ns), *f_v = malloc(sizeof(double) * sz * ns);
+    double *tx = malloc(sizeof(double) * sz), *tv = malloc(sizeof(double) * sz);
+    double *nx = malloc(sizeof(double) * sz), *nv = malloc(sizeof(double) * sz);
+    double *dxs = malloc(sizeof(double) * ns);
+    if (!gold_x || !gold_v || !f_x || !f_v || !tx || !tv || !nx || !nv || !dxs) { rc = ORC_ENOMEM; goto out; }
+    int b = 0, e = 0;
+    *iters_done = 0;
+    *last_dx = INFINITY;
+    for (int k = 0; b < n_slices && k < max_iter; k++) {
+        /* fill the window: first iterates of the new slices by G, in order */
+        int e_new = b + window < n_slices ? b + window : n_slices;
+        for (int s = e; s < e_new; s++) {
+            memcpy(tx, slices_x + sz * s, sizeof(double) * sz);
+            memcpy(tv, slices_v + sz * s, sizeof(double) * sz);
+            if (md_steps(&G, tx, tv, dtG, sG, NULL)) { rc = ORC_ENOCONV; goto out; }
+            memcpy(gold_x + sz * s, tx, sizeof(double) * sz); memcpy(gold_v + sz * s, tv, sizeof(double) * sz);
+            memcpy(slices_x + sz * (s + 1), tx, sizeof(double) * sz);
+            memcpy(slices_v + sz * (s + 1), tv, sizeof(double) * sz);
+        }
+        e = e_new;
+        for (int s = b; s < e; s++) {                                      /* f_n = F(lambda^k_n) */
+            memcpy(f_x + sz * s, slices_x + sz * s, sizeof(double) * sz);
+            memcpy(f_v + sz * s, slices_v + sz * s, sizeof(double) * sz);
+            if ((rc = md_steps(&F, f_x + sz * s, f_v + sz * s, dtF, sF, NULL))) goto out;
+        }
+        /* sequential correction over the window, from its final first state */
+        memcpy(nx, slices_x + sz * b, sizeof(double) * sz);
+        memcpy(nv, slices_v + sz * b, sizeof(double) * sz);
+        double dmax = 0;
+        for (int s = b; s < e; s++) {
+            memcpy(tx, nx, sizeof(double) * sz);
+            memcpy(tv, nv, sizeof(double) * sz);
+            if (md_steps(&G, tx, tv, dtG, sG, NULL)) { rc = ORC_ENOCONV; goto out; }
+            for (size_t c = 0; c < sz; c++) {
+                nx[c] = f_x[sz * s + c] + (tx[c] - gold_x[sz * s + c]);
+                nv[c] = f_v[sz * s + c] + (tv[c] - gold_v[sz * s + c]);
+            }
+            if ((rc = project_rigid(&F, nx, nv))) goto out;
+            double d = 0;
+            for (size_t c = 0; c < sz; c++) { double t = fabs(nx[c] - slices_x[sz * (s + 1) + c]); if (t > d) d = t; }
+            dxs[s] = d;
+            if (d > dmax) dmax = d;
+            memcpy(gold_x + sz * s, tx, sizeof(double) * sz); memcpy(gold_v + sz * s, tv, sizeof(double) * sz);
+            memcpy(slices_x + sz * (s + 1), nx, sizeof(double) * sz);
+            memcpy(slices_v + sz * (s + 1), nv, sizeof(double) * sz);
+        }
+        *iters_done = k + 1;
+        *last_dx = dmax;
+        b++;                                   /* slice b's end F(lambda_b) is exact: final */
+        while (b < e && dxs[b] <= tol) b++;    /* and the converged slices that follow it */
+    }
+    if (b < n_slices) rc = ORC_ENOCONV;
+out:
+    free(gold_x); free(gold_v); free(f_x); free(f_v); free(tx); free(tv); free(nx); free(nv); free(dxs);
     return rc;
 }
 

@@ -178,3 +178,36 @@ def test_projection_leaves_rigid_molecules_bitwise_unchanged():
     x, v, _ = oracle.md_run(s, dt=0.002, n_steps=3, **FINE)       # SHAKE/RATTLE output
     xp, vp = oracle.project_rigid(x, v, s.mass, s.n_mol)
     assert np.array_equal(xp, x) and np.array_equal(vp, v)
+
+
+def test_windowed_parareal_with_full_window_is_plain_parareal(pr_setup):
+    """A window as long as the run, tol = 0: the same iterates bit for bit."""
+    s, F, G = pr_setup
+    for k in (1, 2, 6):
+        a = oracle.parareal(s, G, F, n_slices=4, max_iter=k, tol=0.0)
+        b = oracle.parareal_window(s, G, F, n_slices=4, window=4, max_iter=k, tol=0.0)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        if k < 4:
+            assert a[2] == b[2] == k and a[3] == b[3]
+        else:
+            # the window knows slice 3 is exact after iteration 4; plain parareal needs a
+            # fifth iteration to see no change
+            assert b[2] == 4 and b[4] == 0 and a[2] == 5 and a[3] == 0.0
+
+
+def test_windowed_parareal_small_windows_reach_serial_fine(pr_setup):
+    """W = 1 is the serial fine run (one iteration per slice); W = 2 with tol = 0
+    iterated to the end also gives every slice exactly."""
+    s, F, G = pr_setup
+    fx, fv = _run_serial(s, F, 5)
+    xs, vs, it, dx, rc = oracle.parareal_window(s, G, F, n_slices=5, window=1, max_iter=50, tol=0.0)
+    assert rc == 0 and it == 5
+    assert np.array_equal(xs, fx) and np.array_equal(vs, fv)
+    xs, vs, it, dx, rc = oracle.parareal_window(s, G, F, n_slices=5, window=2, max_iter=50, tol=0.0)
+    assert rc == 0 and np.array_equal(xs, fx) and np.array_equal(vs, fv)
+    # one iteration of a 2-slice window: slice 0's end is exact, slice 1's is G-corrected,
+    # the slices beyond the window are not reached
+    xs, vs, it, dx, rc = oracle.parareal_window(s, G, F, n_slices=5, window=2, max_iter=1, tol=0.0)
+    assert rc == -6 and it == 1
+    assert np.array_equal(xs[1], fx[1]) and not np.array_equal(xs[2], fx[2])
+    assert not np.any(xs[3:])
