@@ -59,6 +59,23 @@ extern "C" {
 #define MSM_MODEL_CHARGES 0  /* bare point charges: the paper's Coulomb sum     */
 #define MSM_MODEL_WATER   1  /* + rigid 3-site water completion (see msm_system) */
 
+/* Electrostatics method (msm_params.method).  The MSM is the fine propagator's
+ * method (Sec. 3); Sec. 5 weighs cheaper methods for the parareal coarse
+ * propagator and keeps two, both sums over the pairs closer than a (no grids):
+ *   MSM_METHOD_CUTOFF  simple cutoff, U = 1/2 sum_{i != j, r_ij < a} k_e q_i q_j / r_ij
+ *                      (the paper's chosen coarse propagator)
+ *   MSM_METHOD_WOLF    Wolf summation (Wolf, Keblinski, Phillpot & Eggebrecht 1999):
+ *                      pair term k_e q_i q_j [erfc(alpha r)/r - erfc(alpha a)/a],
+ *                      self term -k_e [erfc(alpha a)/(2a) + alpha/sqrt(pi)] q_i^2,
+ *                      alpha = msm_params.wolf_alpha (1/nm)
+ * For both, forces are the exact gradient (the shift is constant inside a),
+ * potentials phi_i = dU/dq_i, n_levels is ignored, h is only the edge of the
+ * cells the pair search uses (and the box contract is the same), and the water
+ * completion skips its intramolecular pairs instead of subtracting them. */
+#define MSM_METHOD_MSM    0
+#define MSM_METHOD_CUTOFF 1
+#define MSM_METHOD_WOLF   2
+
 #define MSM_FLAG_GRAPHS   1  /* md_run: steps after the first replay one captured CUDA graph
                                 (the first too, when a previous call captured it for the
                                 same arrays, geometry and buffers)                         */
@@ -94,7 +111,9 @@ extern "C" {
  *   list_skin  md_run only: Verlet-list skin (nm) of the short-range sum;
  *              lists hold pairs within a + list_skin and are rebuilt when an
  *              atom has moved more than list_skin/2 (0 = cell search every
- *              step; the default).  Exact either way: pairs are still tested against a.  */
+ *              step; the default).  Exact either way: pairs are still tested against a.
+ *   method     MSM_METHOD_* (default MSM_METHOD_MSM)
+ *   wolf_alpha damping of MSM_METHOD_WOLF (1/nm, >= 0)  */
 typedef struct msm_params {
     double  a;
     double  h;
@@ -112,6 +131,9 @@ typedef struct msm_params {
     double  wall_k;
     double  wall_width;
     double  list_skin;
+    int32_t method;
+    int32_t reserved1;
+    double  wolf_alpha;
 } msm_params;
 
 /* An MD system in the library's layout.  Rigid water occupies the first
@@ -228,12 +250,40 @@ MSM_API int  md_run_batched(msm_handle *h, int32_t n_sys, msm_system *systems, d
  * than 10x the fine propagator's SHAKE tolerance (exact states pass unchanged).
  * Returns MSM_ENOCONV, with a message starting "parareal:", if tol was not met
  * or if the coarse propagator broke down on a corrected state (the iteration
- * diverged); the last complete iterate is written either way. */
+ * diverged); the last complete iterate is written either way.  The correction
+ * sweep of an iteration is enqueued without host synchronisation (each coarse
+ * propagation's status is kept on the device); the host reads the sweep's
+ * outcome once per iteration.  G (or F) may use a cutoff method (msm_params
+ * method, Sec. 5). */
 MSM_API int  parareal_run(const msm_params *G, double dtG, int32_t stepsG,
                   const msm_params *F, double dtF, int32_t stepsF,
                   const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
                   double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx,
                   void *stream);
+
+/* Parareal over a sliding computational window (Sec. 4: the iteration runs on
+ * a window of time points).  At most `window` slices [b, e) are iterated at
+ * once: each iteration runs F on every window slice as one batch and the
+ * correction sweep from lambda_b, which is final.  Then b moves past slice b
+ * (its end F(lambda_b) is exact) and past the following slices whose end
+ * moved by at most tol (max |x^{k+1} - x^k|, nm), and new slices enter the
+ * window with the coarse propagation of its last state as their first
+ * iterate.  Device memory holds window + 1 states (plus the batch's copies)
+ * instead of n_slices + 1, so long runs fit.  Arguments as parareal_run;
+ * max_iter bounds the iterations of the whole run (each iteration finalises
+ * at least one slice, so n_slices iterations always suffice).  slices_x/v
+ * receive every slice end: final ones for the converged slices, the last
+ * iterate for the rest (slices the window never reached are not written).
+ * *last_dx is the largest change of the last iteration.  With window =
+ * n_slices and tol = 0 the iterates equal parareal_run's; with window = 1 the
+ * run is the serial fine propagation.  Returns MSM_ENOCONV ("parareal: ...")
+ * if max_iter ran out first or the coarse propagator broke down; the last
+ * complete iterate is written either way. */
+MSM_API int  parareal_run_window(const msm_params *G, double dtG, int32_t stepsG,
+                  const msm_params *F, double dtF, int32_t stepsF,
+                  const msm_system *state0, int32_t n_slices, int32_t window, int32_t max_iter,
+                  double tol, double *slices_x, double *slices_v, int32_t *iters_done,
+                  double *last_dx, void *stream);
 
 /* Inspection of the last evaluation on h (host outputs, synchronous).
  * msm_grid_shape: level k's point counts (nx, ny, nz) and index origin
@@ -244,7 +294,9 @@ MSM_API int  parareal_run(const msm_params *G, double dtG, int32_t stepsG,
  * (atoms ordered by finest-grid cell, then index) and cell_start[ncells+1],
  * *ncells receiving the cell count (cells floor(L/h)+1 per axis, x fastest).
  * msm_stage_atoms: which = 0 short-range potential sum_j q_j g*(r_ij) (n),
- * 1 short-range force sum (n*3), both before k_e, in original atom order. */
+ * 1 short-range force sum (n*3), both before k_e, in original atom order
+ * (for the cutoff methods: the pair sums of their pair term).  The cutoff
+ * methods have no grids: msm_grid_shape and msm_stage_grid return MSM_EINVAL. */
 MSM_API int  msm_grid_shape(msm_handle *h, int32_t level, int64_t shape[3], int64_t lo[3]);
 MSM_API int  msm_stage_grid(msm_handle *h, int32_t level, int32_t which, double *out, int64_t count);
 MSM_API int  msm_cell_list(msm_handle *h, int64_t *perm, int64_t *cell_start, int64_t *ncells);

@@ -81,6 +81,7 @@ def lib():
         L.orc_parareal_window.restype = i
         L.orc_parareal_window.argtypes = [p, p, i64, i64, p, p, p, p, i, i, i, d, p, p, p, p]
         L.orc_num_threads.restype = i; L.orc_num_threads.argtypes = []
+        L.orc_set_num_threads.restype = None; L.orc_set_num_threads.argtypes = [i]
         L.orc_project_rigid.restype = i
         L.orc_project_rigid.argtypes = [i64, i64, p, d, d, p, p]
         _lib = L
@@ -136,6 +137,11 @@ def dPhi(t):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads of the oracle's OpenMP loops (its results are the same for any count)."""
+    lib().orc_set_num_threads(int(k))
 
 
 # --- grids -----------------------------------------------------------------

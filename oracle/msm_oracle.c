@@ -1154,3 +1154,13 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops from now on (results do not depend on it). */
+void orc_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}

@@ -22,6 +22,7 @@ KE = 138.935458
 FP64, FP32 = 0, 1
 MODEL_CHARGES, MODEL_WATER = 0, 1
 FLAG_GRAPHS, FLAG_AUTOTUNE, FLAG_SCALAR_PAIRS = 1, 2, 4
+METHODS = {"msm": 0, "cutoff": 1, "wolf": 2}
 CODES = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOCONV"}
 
 
@@ -37,7 +38,8 @@ class Params(C.Structure):
                 ("coulomb_k", C.c_double), ("gamma_kind", C.c_int32), ("basis_kind", C.c_int32),
                 ("model", C.c_int32), ("flags", C.c_int32), ("lj_sigma", C.c_double),
                 ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double),
-                ("wall_k", C.c_double), ("wall_width", C.c_double), ("list_skin", C.c_double)]
+                ("wall_k", C.c_double), ("wall_width", C.c_double), ("list_skin", C.c_double),
+                ("method", C.c_int32), ("reserved1", C.c_int32), ("wolf_alpha", C.c_double)]
 
 
 class SystemC(C.Structure):
@@ -51,7 +53,7 @@ EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
            "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats",
-           "msm_system_forces_batched", "md_run_batched", "msm_diag_convert")
+           "msm_system_forces_batched", "md_run_batched", "msm_diag_convert", "parareal_run_window")
 
 
 def lib():
@@ -77,6 +79,9 @@ def lib():
         L.parareal_run.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, d, p, p,
                                    P(i32), P(d), p]
         L.parareal_run.restype = C.c_int
+        L.parareal_run_window.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, i32, d, p, p,
+                                          P(i32), P(d), p]
+        L.parareal_run_window.restype = C.c_int
         L.msm_grid_shape.argtypes = [p, i32, p, p]; L.msm_grid_shape.restype = C.c_int
         L.msm_stage_grid.argtypes = [p, i32, i32, p, i64]; L.msm_stage_grid.restype = C.c_int
         L.msm_cell_list.argtypes = [p, p, p, p]; L.msm_cell_list.restype = C.c_int
@@ -166,7 +171,8 @@ def _box(box):
 
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
                 lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
-                list_skin=0.0, graphs=True, autotune=True, scalar_pairs=False) -> Params:
+                list_skin=0.0, graphs=True, autotune=True, scalar_pairs=False, method="msm",
+                wolf_alpha=0.0) -> Params:
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -180,6 +186,8 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
     p.list_skin = float(list_skin)
     p.flags = ((FLAG_GRAPHS if graphs else 0) | (FLAG_AUTOTUNE if autotune else 0)
                | (FLAG_SCALAR_PAIRS if scalar_pairs else 0))
+    p.method = METHODS[method] if isinstance(method, str) else int(method)
+    p.wolf_alpha = float(wolf_alpha)
     return p
 
 
@@ -425,23 +433,35 @@ def _system_struct(sys, need_v=False):
 
 
 def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float, model="water",
-                 precision="fp32", stream=None):
-    """Parareal over md_run: G and F are dict(a, h, levels, dt, steps).
+                 precision="fp32", stream=None, window=None):
+    """Parareal over md_run: G and F are dict(a, h, levels, dt, steps[, method, wolf_alpha,
+    wall_k, wall_width, ...]); method "cutoff" or "wolf" makes a cutoff coarse propagator.
+
+    window: None runs parareal_run (every slice iterated); an integer runs
+    parareal_run_window with at most that many slices per iteration.
 
     Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
     def params(P):
-        return make_params(P["a"], P["h"], P["levels"], P.get("precision", precision), model,
+        return make_params(P["a"], P["h"], P.get("levels", 1), P.get("precision", precision), model,
                            wall_k=P.get("wall_k", 0.0), wall_width=P.get("wall_width", 0.0),
                            list_skin=P.get("list_skin", 0.0), graphs=P.get("graphs", True),
-                           autotune=P.get("autotune", True))
+                           autotune=P.get("autotune", True), method=P.get("method", "msm"),
+                           wolf_alpha=P.get("wolf_alpha", 0.0))
     pg, pf = params(G), params(F)
     s, keep = _system_struct(sys, need_v=True)
     n = int(s.n)
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))
     it = C.c_int32(0); dx = C.c_double(0)
-    rc = lib().parareal_run(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
-                            int(F["steps"]), C.byref(s), int(n_slices), int(max_iter), float(tol), _ptr(xs),
-                            _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
+    xs[0] = np.asarray(sys.pos.cpu() if _is_tensor(sys.pos) else sys.pos)
+    vs[0] = np.asarray(sys.vel.cpu() if _is_tensor(sys.vel) else sys.vel)
+    if window is None:
+        rc = lib().parareal_run(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
+                                int(F["steps"]), C.byref(s), int(n_slices), int(max_iter), float(tol), _ptr(xs),
+                                _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
+    else:
+        rc = lib().parareal_run_window(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
+                                       int(F["steps"]), C.byref(s), int(n_slices), int(window), int(max_iter),
+                                       float(tol), _ptr(xs), _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
     if rc != 0 and not (rc == -6 and lib().msm_last_error().decode().startswith("parareal:")):
         _check(rc)                     # a propagator failed (not merely a slow convergence)
     return xs, vs, it.value, dx.value, rc == 0

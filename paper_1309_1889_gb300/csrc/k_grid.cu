@@ -651,11 +651,12 @@ __global__ void k_interp(const InterpArgs<T> A)
     phi_weights_d(f.y, wy, dy);
     phi_weights_d(f.z, wz, dz);
     const LevelGeom &L = D.gg.L[0];
-    // grid point mu = c - 1 + o sits at array index c - 1 + o - lo = c + o (lo = -1)
-    const T *u = A.u + D.grid_off + L.off;
     T p = 0, gx = 0, gy = 0, gz = 0;
+    // grid point mu = c - 1 + o sits at array index c - 1 + o - lo = c + o (lo = -1);
+    // no grids (u = NULL): the cutoff methods, whose pair sums are the whole result
+    const T *u = A.u ? A.u + D.grid_off + L.off : nullptr;
 #pragma unroll
-    for (int oz = 0; oz < 4; oz++) {
+    for (int oz = 0; u && oz < 4; oz++) {
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
             const T *row = u + (size_t)((cz + oz) * L.n[1] + (cy + oy)) * L.n[0] + cx;
@@ -673,21 +674,27 @@ __global__ void k_interp(const InterpArgs<T> A)
             gz = fma(dz[oz] * wy[oy], rp, gz);
         }
     }
-    // Per-atom combination in T, then one conversion to the FP64 outputs (on the
-    // integer pipe: GB300 runs FP64 instructions at 1/64 of the FP32 rate).
+    // Forces combined per atom in T, then one conversion to the FP64 outputs (on the
+    // integer pipe: GB300 runs FP64 instructions at 1/64 of the FP32 rate).  The
+    // potential and energy are combined in FP64 (a handful of FP64 operations per
+    // atom): the grid potential carries each atom's own smooth self-interaction,
+    // removed here by q_i gamma(0)/a, and for molecules this nearly cancels against
+    // the excluded pairs' smooth terms (FP64 in k_exclusions); an FP32 k_e or self
+    // coefficient would round alike for every atom and bias U far beyond 1e-6.
     const int i = A.perm[s];
     const vec4<T> sr = A.sr[i];
     const T q = to_t<T>(A.q[i]);
     const T ke = to_t<T>(A.ke), ih = to_t<T>(D.inv_h);
-    const T phi = ke * (sr.w + p - q * to_t<T>(A.self));
     T F[3] = {ke * (sr.x - q * gx * ih), ke * (sr.y - q * gy * ih), ke * (sr.z - q * gz * ih)};
-    T e = T(0.5) * q * phi;
+    const double qd = A.q[i];
+    const double phid = A.ke * ((to_d(sr.w) + to_d(p)) - qd * A.self);
+    double ed = (0.5 * qd) * phid;
     if (A.lj) {
         const vec4<T> lj = A.lj[i];
         F[0] += lj.x; F[1] += lj.y; F[2] += lj.z;
-        e += T(0.5) * lj.w;
+        ed = fma(0.5, to_d(lj.w), ed);
     }
-    double Fd[3] = {to_d(F[0]), to_d(F[1]), to_d(F[2])}, ed = to_d(e);
+    double Fd[3] = {to_d(F[0]), to_d(F[1]), to_d(F[2])};
     const double x[3] = {A.pos[3 * i], A.pos[3 * i + 1], A.pos[3 * i + 2]};
     const int c[3] = {cx, cy, cz};
     if (A.wall_k > 0.0 && (c[0] < D.wall_lo[0] || c[0] > D.wall_hi[0] || c[1] < D.wall_lo[1] ||
@@ -701,7 +708,7 @@ __global__ void k_interp(const InterpArgs<T> A)
         }
     }
     if (A.forces) { A.forces[3 * i] = Fd[0]; A.forces[3 * i + 1] = Fd[1]; A.forces[3 * i + 2] = Fd[2]; }
-    if (A.pot) A.pot[i] = to_d(phi);
+    if (A.pot) A.pot[i] = phid;
     A.eatom[i] = ed;
     A.vatom[i] = x[0] * Fd[0] + x[1] * Fd[1] + x[2] * Fd[2];
 }

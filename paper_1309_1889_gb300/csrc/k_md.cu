@@ -2,9 +2,9 @@
 //   k_exclusions   rigid-water completion: the short-range kernel skipped the
 //                  three intramolecular pairs of each (O, H, H) triple, so only
 //                  their smooth part k_e q_i q_j gamma(r/a)/a, which the grids
-//                  carry, is subtracted here (in T, accumulated into the FP64
-//                  outputs); together this removes the full 1/r = g* +
-//                  gamma(r/a)/a of every excluded pair
+//                  carry, is subtracted here (forces in T, energy and
+//                  potentials in FP64); together this removes the full 1/r =
+//                  g* + gamma(r/a)/a of every excluded pair
 //   k_sum_*        deterministic FP64 sums (fixed partition, fixed tree) for
 //                  the energy, the virial and the kinetic energy
 //   k_vv_first     velocity Verlet (Sec. 2): half kick, drift, then SHAKE
@@ -31,39 +31,47 @@ __global__ void k_exclusions(const ExclArgs A)
     if (mo >= D.n_mol || failed(A.status)) return;
     const int i0 = D.atom_off + 3 * mo;
     // bond vectors from two FP64 differences against the O atom, then T
-    T rel[3][3], q[3], F[3][3], dphi[3], de[3];
+    T rel[3][3], q[3], F[3][3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         q[a] = to_t<T>(A.q[i0 + a]);
-        dphi[a] = de[a] = 0;
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             rel[a][d] = a ? to_t<T>(A.x[3 * (i0 + a) + d] - A.x[3 * i0 + d]) : T(0);
             F[a][d] = 0;
         }
     }
-    const T ke = to_t<T>(A.ke), ia = T(1) / to_t<T>(A.a);
+    const T ke = to_t<T>(A.ke), ia = to_t<T>(A.inv_a);
+    // The energy and potential terms are formed in FP64.  Per molecule they cancel the
+    // atoms' self terms q_i^2 gamma(0)/a (also FP64, in k_interp) to a small remainder
+    // (a neutral molecule's own smooth field nearly vanishes at its atoms), while each
+    // is ~1e2 kJ/mol; an FP32 k_e, 1/a or gamma would round alike for every molecule of
+    // the rigid model and leave a bias of ~1e-7 of that sum: ~1e-5 of U for water.
+    const double kd = A.ke * A.inv_a, ia2 = A.inv_a * A.inv_a;
+    double qd[3], dphid[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 3; a++) qd[a] = A.q[i0 + a];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const int a = c == 2 ? 1 : 0, b = c == 0 ? 1 : 2;
         const T dx = rel[a][0] - rel[b][0], dy = rel[a][1] - rel[b][1], dz = rel[a][2] - rel[b][2];
-        const T r = sqrt(dx * dx + dy * dy + dz * dz);
+        const T r2t = dx * dx + dy * dy + dz * dz;
+        const T r = sqrt(r2t);
         const T rho = r * ia;
-        T gam, dgam;                                   // gamma(rho), gamma'(rho)
-        if (rho < T(1)) {
-            const T r2 = rho * rho;
-            gam = T(GAMMA_C0) + T(GAMMA_C1) * r2 + T(GAMMA_C2) * r2 * r2;
-            dgam = T(2 * GAMMA_C1) * rho + T(4 * GAMMA_C2) * r2 * rho;
+        T dgam;                                        // gamma'(rho)
+        const double rho2 = to_d(r2t) * ia2;
+        double gam;                                    // gamma(rho), FP64
+        if (rho2 < 1.0) {
+            gam = GAMMA_C0 + rho2 * (GAMMA_C1 + GAMMA_C2 * rho2);
+            dgam = T(2 * GAMMA_C1) * rho + T(4 * GAMMA_C2) * (rho * rho) * rho;
         } else {
-            gam = T(1) / rho;
-            dgam = -gam * gam;
+            gam = 1.0 / sqrt(rho2);
+            const T g = T(1) / rho;
+            dgam = -g * g;
         }
-        const T sm = gam * ia;                         // smooth part of 1/r
-        const T e = ke * q[a] * q[b] * sm;
-        dphi[a] -= ke * q[b] * sm;
-        dphi[b] -= ke * q[a] * sm;
-        de[a] -= T(0.5) * e;
-        de[b] -= T(0.5) * e;
+        const double kg = kd * gam;                    // k_e gamma(r/a)/a: smooth part of k_e/r
+        dphid[a] = fma(-kg, qd[b], dphid[a]);
+        dphid[b] = fma(-kg, qd[a], dphid[b]);
         // U_corr = -k_e q_a q_b gamma(r/a)/a  =>  F_a = k_e q_a q_b gamma'(r/a)/a^2 (r_a - r_b)/r
         const T s = ke * q[a] * q[b] * dgam * ia * ia / r;
         F[a][0] += s * dx; F[a][1] += s * dy; F[a][2] += s * dz;
@@ -79,8 +87,8 @@ __global__ void k_exclusions(const ExclArgs A)
             if (A.forces) A.forces[3 * i + d] += fd;
             v += A.x[3 * i + d] * fd;
         }
-        if (A.pot) A.pot[i] += to_d(dphi[a]);
-        A.eatom[i] += to_d(de[a]);
+        if (A.pot) A.pot[i] += dphid[a];
+        A.eatom[i] += 0.5 * qd[a] * dphid[a];          // each pair's -1/2 e to both atoms
         A.vatom[i] += v;
     }
 }
@@ -659,6 +667,52 @@ __global__ void k_max_reduce(int m, const double *__restrict__ v, double *__rest
 int launch_max_reduce(int m, const double *v, double *out, cudaStream_t st)
 {
     k_max_reduce<<<1, PR_T, 0, st>>>(m, v, out);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// Per-segment maxima: out[s] = max(v[s*m .. s*m + m)), one block per segment.
+__global__ void k_max_reduce_seg(int m, const double *__restrict__ v, double *__restrict__ out)
+{
+    __shared__ double ws[PR_T / 32];
+    const double *vs = v + (size_t)blockIdx.x * m;
+    double r = 0;
+    for (int i = threadIdx.x; i < m; i += PR_T) r = fmax(r, vs[i]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) ws[w] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int k = 0; k < PR_T / 32; k++) t = fmax(t, ws[k]);
+        out[blockIdx.x] = t;
+    }
+}
+
+int launch_max_reduce_seg(int nseg, int m, const double *v, double *out, cudaStream_t st)
+{
+    if (nseg <= 0) return MSM_OK;
+    k_max_reduce_seg<<<nseg, PR_T, 0, st>>>(m, v, out);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+// Keep the first failure of a sequence of propagations: src is a propagation's
+// status word (reset by its next run), dst[0..3] = (code, kind, tag, atom + 1)
+// of the first one that failed, tag = the caller's label of that propagation.
+__global__ void k_status_fold(const int *__restrict__ src, int *__restrict__ dst, int tag)
+{
+    if (src[0] != 0 && dst[0] == 0) {
+        dst[0] = src[0]; dst[1] = src[1]; dst[2] = tag; dst[3] = src[3];
+    }
+}
+
+int launch_status_fold(const int *src, int *dst, int tag, cudaStream_t st)
+{
+    k_status_fold<<<1, 1, 0, st>>>(src, dst, tag);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

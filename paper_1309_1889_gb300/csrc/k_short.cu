@@ -2,6 +2,9 @@
 //   u_i^short = sum_{j != i, r_ij < a} q_j g*(r_ij),  g*(r) = 1/r - gamma(r/a)/a,
 //   F_i^short = -q_i sum_j q_j g*'(r_ij) (r_i - r_j)/r_ij
 //             =  q_i sum_j q_j [1/r^3 - 5/(2a^3) + 3r^2/(2a^5)] (r_i - r_j).
+// The same kernel sums the pair terms of the coarse propagators of Sec. 5:
+// the simple cutoff (g = 1/r: the gamma coefficients are zero) and Wolf
+// summation (g = erfc(alpha r)/r - erfc(alpha a)/a, the WOLF instance).
 //
 // Layout: atoms sorted by finest-grid cell (x fastest), so a run of cells
 // along x is one contiguous slot range.  One warp owns one brick of
@@ -186,7 +189,8 @@ __device__ __forceinline__ void pair_steps_lj_f32x2(const float *__restrict__ P,
 // PACKED: the FP32 Coulomb and LJ passes take their queued j's two at a time on
 // packed FP32 pairs (pair_steps_f32x2, pair_steps_lj_f32x2); otherwise, and for
 // FP64 and the pair count, one at a time.
-template <typename T, bool MODEL, bool COUNT, bool LJP, bool PACKED>
+// WOLF: the pair term of Wolf summation (one j at a time; erfc and exp per pair).
+template <typename T, bool MODEL, bool COUNT, bool LJP, bool PACKED, bool WOLF = false>
 __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_short(const ShortArgs<T> A)
 {
     __shared__ ShortSmem<T> S;
@@ -270,9 +274,19 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
                     continue;
                 }
                 const T qj = in ? pj.w : T(0);
-                const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
-                phi = fma(qj, ri - poly, phi);
-                const T fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
+                T g, fs;                 // pair term and -g'(r)/r
+                if constexpr (WOLF) {
+                    const T ar = A.w_alpha * (r2s * ri);
+                    const T ec = erfc(ar);
+                    const T ex = exp(-ar * ar);
+                    g = fma(ec, ri, -A.w_shift);
+                    fs = fma(ec, ri, A.w_c * ex) * ri2;
+                } else {
+                    const T poly = fma(fma(A.c2, r2s, A.c1), r2s, A.c0);
+                    g = ri - poly;
+                    fs = fma(ri2, ri, fma(A.d1, r2s, A.d0));
+                }
+                phi = fma(qj, g, phi);
                 const T sc = qj * fs;
                 ax = fma(sc, dx, ax); ay = fma(sc, dyy, ay); az = fma(sc, dzz, az);
             }
@@ -407,6 +421,13 @@ int launch_short(const ShortArgs<T> &a, bool model, cudaStream_t st)
 {
     if (a.max_bricks <= 0) return MSM_OK;
     const dim3 grid((a.max_bricks + SR_WARPS - 1) / SR_WARPS, a.bt.B);
+    if (a.wolf) {
+        if (model) k_short<T, true, false, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+        else k_short<T, false, false, false, false, true><<<grid, SR_WARPS * 32, 0, st>>>(a);
+        count_launch();
+        CUDA_TRY(cudaGetLastError());
+        return MSM_OK;
+    }
     bool packed = false;
     if constexpr (sizeof(T) == 4) packed = !a.scalar_pairs;
     if constexpr (sizeof(T) == 4) {

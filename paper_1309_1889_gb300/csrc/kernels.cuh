@@ -57,6 +57,9 @@ template <typename T> struct ShortArgs {
     T a, a2, a_sel;        // cutoff, its square, row-selection radius (cutoff + rounding pad)
     T c0, c1, c2;          // gamma(r/a)/a = c0 + c1 r^2 + c2 r^4
     T d0, d1;              // -g*'(r)/r - 1/r^3 = d0 + d1 r^2
+                           // (all five 0 for the simple cutoff: the pair term is 1/r)
+    bool wolf;             // Wolf summation: pair term erfc(alpha r)/r - w_shift
+    T w_alpha, w_shift, w_c;   // alpha, erfc(alpha a)/a, 2 alpha/sqrt(pi)
     T lj_s2, lj_4eps, lj_24eps, lj_shift;
     const int *perm;       // sorted slot -> atom
     vec4<T> *sr;           // by atom: (F_x, F_y, F_z, phi) of the g* sum, before k_e
@@ -175,10 +178,10 @@ template <typename T> struct InterpArgs {
     const vec4<T> *afrac;
     const vec4<T> *sr;
     const vec4<T> *lj;     // nullable
-    const T *u;            // concatenated grids
+    const T *u;            // concatenated grids (NULL: no grid part, the cutoff methods)
     const double *pos;     // original order (virial, wall)
     const double *q;       // original order
-    double ke, self;       // k_e, gamma(0)/a
+    double ke, self;       // k_e, self coefficient: phi_i -= q_i self (gamma(0)/a for the MSM)
     double wall_k, wall_w; // wall_k = 0: no wall
     double *forces;        // original order (nullable)
     double *pot;           // (nullable)
@@ -194,7 +197,7 @@ struct ExclArgs {
     int max_mol;
     const double *x;
     const double *q;
-    double ke, a;
+    double ke, a, inv_a;   // k_e, a and 1/a (rounded once, FP64)
     double *forces, *pot, *eatom, *vatom;
     const int *status;
 };
@@ -238,5 +241,9 @@ int launch_max_reduce(int m, const double *v, double *out, cudaStream_t st);
 int launch_pr_project(int n_mol, double *x, double *v, const double *m, double d_oh2, double d_hh2, double thresh,
                       double tol, double tol_v, int *status, cudaStream_t st);
 int launch_absdiff_partials(int count, const double *a, const double *b, double *part, cudaStream_t st);
+// out[s] = max of v[s*m .. s*m + m), s < nseg.
+int launch_max_reduce_seg(int nseg, int m, const double *v, double *out, cudaStream_t st);
+// First failure of a sequence of propagations: dst = (code, kind, tag, atom + 1) of src once.
+int launch_status_fold(const int *src, int *dst, int tag, cudaStream_t st);
 
 }  // namespace msm

@@ -297,7 +297,11 @@ extern "C" void msm_default_params(msm_params *p)
     p->wall_k = 0.0;
     p->wall_width = 0.0;
     p->list_skin = 0.0;
+    p->method = MSM_METHOD_MSM;
+    p->wolf_alpha = 0.0;
 }
+
+static bool has_grids(const msm_params &p) { return p.method == MSM_METHOD_MSM; }
 
 static int check_params(const msm_params *p)
 {
@@ -313,6 +317,12 @@ static int check_params(const msm_params *p)
         return fail_msg(MSM_EINVAL, "unknown flags");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
+    if (p->method != MSM_METHOD_MSM && p->method != MSM_METHOD_CUTOFF && p->method != MSM_METHOD_WOLF)
+        return fail_msg(MSM_EINVAL, "unknown method");
+    if (!(p->wolf_alpha >= 0) || !std::isfinite(p->wolf_alpha)) return fail_msg(MSM_EINVAL, "wolf_alpha must be >= 0");
+    if (p->method == MSM_METHOD_WOLF && p->list_skin > 0)
+        return fail_msg(MSM_EINVAL, "Verlet lists serve the MSM and the simple cutoff only");
+    if (p->method != MSM_METHOD_MSM) return MSM_OK;          // no grids: n_levels is not used
     int rad = 0;
     while ((double)(rad + 1) * p->h < 2.0 * p->a) rad++;
     if (rad > 12 && p->n_levels > 1)                       // one level has no lattice cutoff
@@ -462,7 +472,8 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     if (same) return MSM_OK;
 
     const double hh = h->p.h;
-    const int l = h->p.n_levels;
+    const bool grids = has_grids(h->p);
+    const int l = grids ? h->p.n_levels : 1;              // the cutoff methods keep level 0's geometry only
     std::vector<SysDesc> d((size_t)B);
     std::vector<std::array<int, 4>> tops;          // (nx, ny, nz, table offset)
     int64_t N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, ST = 0;
@@ -524,6 +535,9 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             const int n_lj = (int)(S.n_mol + (S.n - 3 * S.n_mol));
             set_lj_bricks(D, (t && t->lj_bd[0]) ? t->lj_bd : kBrickShapes[brick_heuristic(n_lj, D.g)]);
         }
+        D.part_off = (int)PB;
+        PB += sum_blocks((int)S.n);
+        if (!grids) continue;                              // no grid buffers, tables or tiles
         D.grid_off = (int)G;
         G += tot;
         const LevelGeom &Lt = D.gg.L[l - 1];
@@ -538,8 +552,6 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             found = (int)tops.size() - 1;
         }
         D.ttab_off = tops[(size_t)found][3];
-        D.part_off = (int)PB;
-        PB += sum_blocks((int)S.n);
         for (int k = 0; k + 1 < l; k++) {
             h->h_blk.push_back((int)ST);
             ST += stencil_tile_count(D.gg.L[k]);
@@ -581,7 +593,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         TRY(launch_top_table(Lt, sc * h->p.a, sc * hh, h->ttop.as<double>() + t[3], st));
     }
     // lattice-cutoff weights W[n] = g^0(|n| h), |n| h < 2a, and the rows of the tap sphere
-    if (!h->stencil_ready) {
+    if (grids && !h->stencil_ready) {
         int rad = 0;
         while ((double)(rad + 1) * hh < 2.0 * h->p.a) rad++;
         const int wd = 2 * rad + 1;
@@ -626,6 +638,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         h->max_units = std::max(h->max_units, D.n_mol + (D.n - 3 * D.n_mol));
         h->max_bricks = std::max(h->max_bricks, D.nbricks);
         h->max_lj_bricks = std::max(h->max_lj_bricks, D.lj_nbricks);
+        if (!grids) continue;
         h->max_atiles = std::max(h->max_atiles, anterp_tiles(D.gg.L[0]));
         for (int k = 0; k < l; k++) h->max_lev[k] = std::max(h->max_lev[k], D.gg.L[k].n[0] * D.gg.L[k].n[1] * D.gg.L[k].n[2]);
     }
@@ -683,8 +696,15 @@ static ShortArgs<T> short_args(msm_handle *h)
     s.start = h->start.as<int>(); s.apos = h->apos.as<vec4<T>>(); s.aflag = h->aflag.as<int>();
     const double a = h->p.a;
     s.a = (T)a; s.a2 = (T)(a * a); s.a_sel = (T)(a + 1e-3 * h->p.h);
-    s.c0 = (T)(GAMMA_C0 / a); s.c1 = (T)(GAMMA_C1 / (a * a * a)); s.c2 = (T)(GAMMA_C2 / (a * a * a * a * a));
-    s.d0 = (T)(-2.5 / (a * a * a)); s.d1 = (T)(1.5 / (a * a * a * a * a));
+    if (h->p.method == MSM_METHOD_MSM) {
+        s.c0 = (T)(GAMMA_C0 / a); s.c1 = (T)(GAMMA_C1 / (a * a * a)); s.c2 = (T)(GAMMA_C2 / (a * a * a * a * a));
+        s.d0 = (T)(-2.5 / (a * a * a)); s.d1 = (T)(1.5 / (a * a * a * a * a));
+    } else {                                               // pair term 1/r (Wolf: its own instance)
+        s.c0 = s.c1 = s.c2 = s.d0 = s.d1 = T(0);
+    }
+    const double al = h->p.wolf_alpha;
+    s.wolf = h->p.method == MSM_METHOD_WOLF;
+    s.w_alpha = (T)al; s.w_shift = (T)(erfc(al * a) / a); s.w_c = (T)(2.0 * al / sqrt(M_PI));
     const double sg2 = h->p.lj_sigma * h->p.lj_sigma;
     const double sa6 = pow(sg2 / (a * a), 3.0);
     s.lj_s2 = (T)sg2; s.lj_4eps = (T)(4.0 * h->p.lj_epsilon); s.lj_24eps = (T)(24.0 * h->p.lj_epsilon);
@@ -846,7 +866,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     // forked here and joined before interpolation: its small, latency-bound launches
     // (the lattice cutoff keeps about four CTAs per SM busy) fill the SMs beside the
     // issue-bound pair kernels.
-    const bool fork = !h->prof.on && !h->list_on;
+    const bool grids = has_grids(h->p);
+    const bool fork = grids && !h->prof.on && !h->list_on;
     cudaStream_t gs = st;
     if (fork) {
         if (!h->grid_st) {
@@ -861,7 +882,7 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         gs = h->grid_st;
     }
     T *qg = h->qgrid.as<T>(), *uc = h->ucut.as<T>(), *ug = h->ugrid.as<T>();
-    {
+    if (grids) {
         cudaStream_t st = gs;                                  // the grid chain's stream
         // step 2: anterpolation
         AnterpArgs<T> an;
@@ -957,15 +978,20 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     InterpArgs<T> ia;
     ia.bt = bt; ia.max_n = h->max_n; ia.perm = h->perm.as<int>(); ia.akey = h->akey.as<int>();
     ia.afrac = h->afrac.as<vec4<T>>(); ia.sr = h->sr.as<vec4<T>>(); ia.lj = model ? h->lj.as<vec4<T>>() : nullptr;
-    ia.u = ug; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k; ia.self = GAMMA_C0 / h->p.a;
+    ia.u = grids ? ug : nullptr; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k;
+    // self coefficient: phi_i -= q_i self (the MSM's gamma(0)/a; Wolf's neutralisation term)
+    const double al = h->p.wolf_alpha, a_ = h->p.a;
+    ia.self = h->p.method == MSM_METHOD_MSM ? GAMMA_C0 / a_
+            : h->p.method == MSM_METHOD_WOLF ? erfc(al * a_) / a_ + 2.0 * al / sqrt(M_PI) : 0.0;
     ia.wall_k = model ? h->p.wall_k : 0.0; ia.wall_w = h->p.wall_width;
     ia.forces = io.forces; ia.pot = io.pot; ia.eatom = h->eatom.as<double>(); ia.vatom = h->vatom.as<double>();
     ia.status = status;
     { PROF(ST_INTERP); TRY(launch_interp<T>(ia, st)); }
     PROF(ST_SUMS);
-    if (model && h->max_mol > 0) {
+    if (model && grids && h->max_mol > 0) {           // the cutoff methods skipped these pairs outright
         ExclArgs ex;
         ex.bt = bt; ex.max_mol = h->max_mol; ex.x = io.pos; ex.q = io.q; ex.ke = h->p.coulomb_k; ex.a = h->p.a;
+        ex.inv_a = 1.0 / h->p.a;
         ex.forces = io.forces; ex.pot = io.pot; ex.eatom = h->eatom.as<double>(); ex.vatom = h->vatom.as<double>();
         ex.status = status;
         TRY(launch_exclusions<T>(ex, st));
@@ -1575,15 +1601,299 @@ extern "C" int msm_count_pairs(msm_handle *h, int64_t *ordered_pairs)
 
 // ----------------------------------------------------------------- parareal
 
-// F of every slice that is not yet exact runs as one batch (all slices in the
-// same launches); G runs slice by slice, as the correction sweep requires.
-// For slices n < k after k iterations the correction is exactly zero (the
-// bracket G(lambda^{k+1}_n) - G(lambda^k_n) vanishes bitwise because both
-// states are equal and G is deterministic), so those slices are copied
-// instead of recomputed: the result is bitwise what recomputing gives.
-extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F, double dtF,
-                            int32_t stepsF, const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
-                            double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx, void *stream)
+// Parareal (Sec. 4) on one GPU.  The fine propagations F of an iteration run
+// as one batch (md_run_batched over the slices of the iteration); the
+// sequential correction sweep runs the coarse propagations G slice by slice.
+// The sweep is enqueued without any host synchronisation: each G's status word
+// is folded on the device into the sweep's (first failure, with its slice),
+// the per-slice max |dx| and the projection status are read once, after the
+// sweep.  The iteration runs over a window of slices [b, e) (Sec. 4's
+// computational window):
+//   plain   (parareal_run): the window is the whole run, b = the iteration
+//           index (slices before it are exact: the bracket G(lambda^{k+1}_n) -
+//           G(lambda^k_n) vanishes bitwise, so they are copied, not recomputed),
+//           stop when the largest change of an iteration is <= tol;
+//   sliding (parareal_run_window): at most W slices; after an iteration b moves
+//           past slice b (exact) and the converged slices that follow it
+//           (max |dx| <= tol), and new slices enter at the end with the coarse
+//           propagation of the last window state as their first iterate; stop
+//           when b reaches n_slices.  Device memory holds W + 1 states, not
+//           n_slices + 1.
+// States live in slot n mod (W + 1) (lambda) and n mod W (G of the current
+// iterate); the F batch is gathered into slots 0 .. e-b-1 of its own buffer.
+struct PararealRun {
+    const msm_params *G, *F;
+    double dtG, dtF;
+    int stepsG, stepsF;
+    const msm_system *s0;
+    int n_slices, window, max_iter;
+    bool sliding;
+    double tol;
+    double *slices_x, *slices_v;
+    int *iters_done;
+    double *last_dx;
+};
+
+static int parareal_impl(const PararealRun &P, cudaStream_t st)
+{
+    const msm_system &s0 = *P.s0;
+    msm_handle *hG = nullptr, *hF = nullptr;
+    TRY(msm_create(P.G, &hG));
+    int rc = msm_create(P.F, &hF);
+    if (rc) { msm_destroy(hG); return rc; }
+    const int ns = P.n_slices, W = P.window;
+    const size_t n3 = 3 * (size_t)s0.n, nn = (size_t)s0.n, w = (size_t)W;
+    const size_t nblk = (n3 + 255) / 256;
+    DevBuf lam_x, lam_v, new_x, new_v, gold_x, gold_v, f_x, f_v, cur_x, cur_v, tmp_x, tmp_v, q, m, lj, part, dxs,
+        pst, gst;
+    double *h_dx = nullptr;
+    int *h_st = nullptr;
+    auto cleanup = [&]() {
+        DevBuf *all[] = {&lam_x, &lam_v, &new_x, &new_v, &gold_x, &gold_v, &f_x, &f_v, &cur_x, &cur_v, &tmp_x,
+                         &tmp_v, &q, &m, &lj, &part, &dxs, &pst, &gst};
+        for (DevBuf *b : all) release(*b);
+        if (h_dx) cudaFreeHost(h_dx);
+        if (h_st) cudaFreeHost(h_st);
+        msm_destroy(hG);
+        msm_destroy(hF);
+    };
+    auto body = [&]() -> int {
+        TRY(ensure(lam_x, sizeof(double) * n3 * (w + 1)));
+        TRY(ensure(lam_v, sizeof(double) * n3 * (w + 1)));
+        if (!P.sliding) {
+            // plain mode keeps the previous iterate whole until a sweep has succeeded
+            // (a diverged sweep hands it back): the sweep writes a second set of states
+            TRY(ensure(new_x, sizeof(double) * n3 * (w + 1)));
+            TRY(ensure(new_v, sizeof(double) * n3 * (w + 1)));
+        }
+        TRY(ensure(gold_x, sizeof(double) * n3 * w));
+        TRY(ensure(gold_v, sizeof(double) * n3 * w));
+        TRY(ensure(f_x, sizeof(double) * n3 * w));
+        TRY(ensure(f_v, sizeof(double) * n3 * w));
+        TRY(ensure(cur_x, sizeof(double) * n3));
+        TRY(ensure(cur_v, sizeof(double) * n3));
+        TRY(ensure(tmp_x, sizeof(double) * n3));
+        TRY(ensure(tmp_v, sizeof(double) * n3));
+        TRY(ensure(q, sizeof(double) * nn * w));            // per-slice copies for the batched F
+        TRY(ensure(m, sizeof(double) * nn * w));
+        TRY(ensure(lj, nn * w));
+        TRY(ensure(part, sizeof(double) * nblk * w));
+        TRY(ensure(dxs, sizeof(double) * w));
+        TRY(ensure(pst, sizeof(int)));
+        TRY(ensure(gst, sizeof(int) * 4));
+        CUDA_TRY(cudaMallocHost(&h_dx, sizeof(double) * w));
+        CUDA_TRY(cudaMallocHost(&h_st, sizeof(int) * 8));
+        CUDA_TRY(cudaMemsetAsync(pst.p, 0, sizeof(int), st));
+        // projection of corrected states: threshold 10x, target 1x the fine propagator's SHAKE tolerance
+        const double ptol = P.F->precision == MSM_FP32 ? shake_tol<float>() : shake_tol<double>();
+        const double d_oh2 = P.F->d_oh * P.F->d_oh, d_hh2 = P.F->d_hh * P.F->d_hh;
+        auto LX = [&](int n) { return lam_x.as<double>() + (size_t)(n % (W + 1)) * n3; };
+        auto LV = [&](int n) { return lam_v.as<double>() + (size_t)(n % (W + 1)) * n3; };
+        // where the sweep writes the new iterate: the same slots (sliding) or the second set (plain)
+        auto NXp = [&](int n) { return (P.sliding ? lam_x : new_x).as<double>() + (size_t)(n % (W + 1)) * n3; };
+        auto NVp = [&](int n) { return (P.sliding ? lam_v : new_v).as<double>() + (size_t)(n % (W + 1)) * n3; };
+        auto GX = [&](int n) { return gold_x.as<double>() + (size_t)(n % W) * n3; };
+        auto GV = [&](int n) { return gold_v.as<double>() + (size_t)(n % W) * n3; };
+        auto D2D = [&](double *dst, const double *src) {
+            return cudaMemcpyAsync(dst, src, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st);
+        };
+        CUDA_TRY(cudaMemcpyAsync(LX(0), s0.x, sizeof(double) * n3, cudaMemcpyDefault, st));
+        CUDA_TRY(cudaMemcpyAsync(LV(0), s0.v, sizeof(double) * n3, cudaMemcpyDefault, st));
+        for (size_t k = 0; k < w; k++) {
+            CUDA_TRY(cudaMemcpyAsync(q.as<double>() + k * nn, s0.q, sizeof(double) * nn, cudaMemcpyDefault, st));
+            CUDA_TRY(cudaMemcpyAsync(m.as<double>() + k * nn, s0.m, sizeof(double) * nn, cudaMemcpyDefault, st));
+            if (s0.lj) CUDA_TRY(cudaMemcpyAsync(lj.as<uint8_t>() + k * nn, s0.lj, nn, cudaMemcpyDefault, st));
+            else CUDA_TRY(cudaMemsetAsync(lj.as<uint8_t>() + k * nn, 0, nn, st));
+        }
+        // the caller's copy of slice n's end state (slot n+1 of slices_x/v)
+        auto publish = [&](int n1) -> int {
+            CUDA_TRY(cudaMemcpyAsync(P.slices_x + (size_t)n1 * n3, LX(n1), sizeof(double) * n3, cudaMemcpyDefault, st));
+            CUDA_TRY(cudaMemcpyAsync(P.slices_v + (size_t)n1 * n3, LV(n1), sizeof(double) * n3, cudaMemcpyDefault, st));
+            return MSM_OK;
+        };
+        TRY(publish(0));
+        SysIn si;
+        si.n = s0.n; si.n_mol = s0.n_mol;
+        memcpy(si.box, s0.box, sizeof si.box);
+        std::vector<SysIn> sis(w, si);
+        // G on tmp, no host synchronisation; its status is folded into gst (tag = slice).
+        // With Verlet lists G needs the host between runs (list maintenance): it then
+        // synchronises after each propagation, as md_run does.
+        const bool g_sync = P.G->list_skin > 0;
+        auto runG = [&](int slice) -> int {
+            RunSys t;
+            t.B = 1; t.sys = &si; t.x = tmp_x.as<double>(); t.v = tmp_v.as<double>();
+            t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
+            int r = run_md(hG, t, P.dtG, P.stepsG, nullptr, 0, st);
+            if (r == MSM_OK && g_sync) r = finish(hG, st);
+            if (r != MSM_OK) {
+                char msg[512];
+                snprintf(msg, sizeof msg, "%s", msm_last_error());
+                return fail_msg(r, "coarse propagator G: %s", msg);
+            }
+            return launch_status_fold(hG->status.as<int>(), gst.as<int>(), slice, st);
+        };
+        // read the sweep's outcome: per-slice changes, first G failure, projection status
+        auto read_sweep = [&](int nseg, int *g_status) -> int {
+            if (nseg > 0) {
+                TRY(launch_max_reduce_seg(nseg, (int)nblk, part.as<double>(), dxs.as<double>(), st));
+                CUDA_TRY(cudaMemcpyAsync(h_dx, dxs.p, sizeof(double) * (size_t)nseg, cudaMemcpyDeviceToHost, st));
+            }
+            CUDA_TRY(cudaMemcpyAsync(h_st, gst.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(h_st + 4, pst.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            prof_resolve(hG);
+            if (h_st[4]) return fail_msg(MSM_ENOCONV, "projection of a corrected slice onto the rigid "
+                                                      "constraints did not converge");
+            *g_status = h_st[0];
+            return MSM_OK;
+        };
+        auto g_failure = [&](int it) {
+            const int code = h_st[0], kind = h_st[1], slice = h_st[2], atom = h_st[3] - 1;
+            char what[256];
+            if (code == MSM_ENOCONV && kind)
+                snprintf(what, sizeof what, "%s did not converge (molecule starting at atom %d)",
+                         kind == 1 ? "SHAKE" : "RATTLE", atom);
+            else
+                snprintf(what, sizeof what, "%s", status_text(code));
+            return fail_msg(MSM_ENOCONV, "parareal: diverged at iteration %d, slice %d (coarse propagator G: %s)",
+                            it, slice, what);
+        };
+        // first iterates of slices [e0, e1): lambda^0_{n+1} = G(lambda^0_n), sequentially
+        auto fill = [&](int e0, int e1) -> int {
+            for (int n = e0; n < e1; n++) {
+                CUDA_TRY(D2D(tmp_x.as<double>(), LX(n)));
+                CUDA_TRY(D2D(tmp_v.as<double>(), LV(n)));
+                TRY(runG(n));
+                CUDA_TRY(D2D(GX(n), tmp_x.as<double>()));
+                CUDA_TRY(D2D(GV(n), tmp_v.as<double>()));
+                CUDA_TRY(D2D(LX(n + 1), tmp_x.as<double>()));
+                CUDA_TRY(D2D(LV(n + 1), tmp_v.as<double>()));
+            }
+            return MSM_OK;
+        };
+        CUDA_TRY(cudaMemsetAsync(gst.p, 0, sizeof(int) * 4, st));
+        int b = 0, e = std::min(W, ns);
+        TRY(fill(0, e));
+        int done = 0;
+        double dxh = INFINITY;
+        bool diverged = false;
+        {
+            int gs = 0;
+            TRY(read_sweep(0, &gs));
+            if (gs) return fail_msg(MSM_ENOCONV, "coarse propagator G failed on the initial sweep (%s)",
+                                    status_text(gs));
+        }
+        if (P.sliding) for (int n = 1; n <= e; n++) TRY(publish(n));
+        for (int it = 0; it < P.max_iter && b < ns; it++) {
+            if (P.sliding) {
+                // refill the window: first iterates of the slices entering it, by G in order
+                const int e2 = std::min(b + W, ns);
+                if (e2 > e) {
+                    CUDA_TRY(cudaMemsetAsync(gst.p, 0, sizeof(int) * 4, st));
+                    TRY(fill(e, e2));
+                    for (int n = e + 1; n <= e2; n++) TRY(publish(n));
+                    e = e2;
+                    int g2 = 0;
+                    TRY(read_sweep(0, &g2));
+                    if (g2) { g_failure(it + 1); diverged = true; break; }
+                }
+            }
+            if (!P.sliding) b = std::min(it, ns);              // slices before the iteration index are exact
+            if (b >= e) {
+                // plain mode, every slice exact: this iteration would change nothing
+                done = it + 1;
+                dxh = 0;
+                break;
+            }
+            const int nb = e - b;
+            // f_n = F(lambda^k_n) for every slice of the window: one batch
+            for (int n = b; n < e; n++) {
+                CUDA_TRY(D2D(f_x.as<double>() + (size_t)(n - b) * n3, LX(n)));
+                CUDA_TRY(D2D(f_v.as<double>() + (size_t)(n - b) * n3, LV(n)));
+            }
+            {
+                RunSys t;
+                t.B = nb; t.sys = sis.data(); t.x = f_x.as<double>(); t.v = f_v.as<double>();
+                t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
+                int r = run_md(hF, t, P.dtF, P.stepsF, nullptr, 0, st);
+                if (r == MSM_OK) r = finish(hF, st);
+                if (r != MSM_OK) {
+                    char msg[512];
+                    snprintf(msg, sizeof msg, "%s", msm_last_error());
+                    return fail_msg(r, "fine propagator F: %s", msg);
+                }
+            }
+            // sequential correction sweep from the window's first state (final)
+            CUDA_TRY(D2D(cur_x.as<double>(), LX(b)));
+            CUDA_TRY(D2D(cur_v.as<double>(), LV(b)));
+            if (!P.sliding) {                                  // the exact slices carry over unchanged
+                CUDA_TRY(cudaMemcpyAsync(NXp(0), LX(0), sizeof(double) * n3 * (size_t)(b + 1), cudaMemcpyDeviceToDevice, st));
+                CUDA_TRY(cudaMemcpyAsync(NVp(0), LV(0), sizeof(double) * n3 * (size_t)(b + 1), cudaMemcpyDeviceToDevice, st));
+            }
+            CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * nblk * (size_t)nb, st));
+            CUDA_TRY(cudaMemsetAsync(gst.p, 0, sizeof(int) * 4, st));
+            for (int n = b; n < e; n++) {
+                CUDA_TRY(D2D(tmp_x.as<double>(), cur_x.as<double>()));
+                CUDA_TRY(D2D(tmp_v.as<double>(), cur_v.as<double>()));
+                TRY(runG(n));
+                const double *fx = f_x.as<double>() + (size_t)(n - b) * n3, *fv = f_v.as<double>() + (size_t)(n - b) * n3;
+                TRY(launch_parareal_update((int)n3, fx, tmp_x.as<double>(), GX(n), cur_x.as<double>(), nullptr, nullptr, st));
+                TRY(launch_parareal_update((int)n3, fv, tmp_v.as<double>(), GV(n), cur_v.as<double>(), nullptr, nullptr, st));
+                TRY(launch_pr_project((int)s0.n_mol, cur_x.as<double>(), cur_v.as<double>(), m.as<double>(), d_oh2,
+                                      d_hh2, 10.0 * ptol, ptol, 1e-14, pst.as<int>(), st));
+                TRY(launch_absdiff_partials((int)n3, cur_x.as<double>(), LX(n + 1),
+                                            part.as<double>() + (size_t)(n - b) * nblk, st));
+                CUDA_TRY(D2D(GX(n), tmp_x.as<double>()));
+                CUDA_TRY(D2D(GV(n), tmp_v.as<double>()));
+                CUDA_TRY(D2D(NXp(n + 1), cur_x.as<double>()));
+                CUDA_TRY(D2D(NVp(n + 1), cur_v.as<double>()));
+            }
+            int gs = 0;
+            TRY(read_sweep(nb, &gs));
+            if (gs) {
+                // the coarse propagator broke down on a corrected state: the iteration diverged.
+                // The caller gets the last complete iterate: plain mode still holds it in lam;
+                // sliding mode published it after the previous iteration.
+                g_failure(it + 1);
+                diverged = true;
+                break;
+            }
+            if (!P.sliding) { std::swap(lam_x, new_x); std::swap(lam_v, new_v); }
+            dxh = 0;
+            for (int k = 0; k < nb; k++) dxh = std::max(dxh, h_dx[k]);
+            done = it + 1;
+            if (P.sliding) {
+                int nb2 = b + 1;                                // slice b's end is exact
+                while (nb2 < e && h_dx[nb2 - b] <= P.tol) nb2++;
+                for (int n = b + 1; n <= e; n++) TRY(publish(n));
+                b = nb2;
+            } else if (dxh <= P.tol) {
+                break;
+            }
+        }
+        if (!P.sliding)
+            for (int n = 1; n <= ns; n++) TRY(publish(n));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (P.iters_done) *P.iters_done = done;
+        if (P.last_dx) *P.last_dx = dxh;
+        if (diverged) return MSM_ENOCONV;                       // message set by g_failure
+        if (P.sliding) {
+            if (b < ns) return fail_msg(MSM_ENOCONV, "parareal: %d of %d slices converged after %d iterations",
+                                        b, ns, done);
+            return MSM_OK;
+        }
+        if (P.max_iter > 0 && !(dxh <= P.tol)) return fail_msg(MSM_ENOCONV, "parareal: max |dx| = %g after %d iterations", dxh, done);
+        return MSM_OK;
+    };
+    rc = body();
+    cleanup();
+    return rc;
+}
+
+static int parareal_args(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F, double dtF,
+                         int32_t stepsF, const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
+                         double *slices_x, double *slices_v)
 {
     if (!G || !F || !state0 || !slices_x || !slices_v) return fail_msg(MSM_EINVAL, "NULL argument");
     if (n_slices < 1 || max_iter < 0 || stepsG < 0 || stepsF < 0 || !(tol >= 0))
@@ -1593,151 +1903,29 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
     const msm_system &s0 = *state0;
     if (s0.n <= 0 || !s0.x || !s0.v || !s0.q || !s0.m) return fail_msg(MSM_EINVAL, "state0 incomplete");
     TRY(check_arrays({s0.x, s0.v, s0.q, s0.m, s0.lj, slices_x, slices_v}));
-    cudaStream_t st = (cudaStream_t)stream;
-    msm_handle *hG = nullptr, *hF = nullptr;
-    TRY(msm_create(G, &hG));
-    int rc = msm_create(F, &hF);
-    if (rc) { msm_destroy(hG); return rc; }
-    const size_t n3 = 3 * (size_t)s0.n, nn = (size_t)s0.n, ns = (size_t)n_slices;
-    DevBuf lam_x, lam_v, new_x, new_v, gold_x, gold_v, f_x, f_v, tmp_x, tmp_v, q, m, lj, part, dx, pst;
-    auto cleanup = [&]() {
-        DevBuf *all[] = {&lam_x, &lam_v, &new_x, &new_v, &gold_x, &gold_v, &f_x, &f_v, &tmp_x, &tmp_v, &q, &m, &lj,
-                         &part, &dx, &pst};
-        for (DevBuf *b : all) release(*b);
-        msm_destroy(hG);
-        msm_destroy(hF);
-    };
-    auto body = [&]() -> int {
-        TRY(ensure(lam_x, sizeof(double) * n3 * (ns + 1)));
-        TRY(ensure(lam_v, sizeof(double) * n3 * (ns + 1)));
-        TRY(ensure(new_x, sizeof(double) * n3 * (ns + 1)));
-        TRY(ensure(new_v, sizeof(double) * n3 * (ns + 1)));
-        TRY(ensure(gold_x, sizeof(double) * n3 * ns));
-        TRY(ensure(gold_v, sizeof(double) * n3 * ns));
-        TRY(ensure(f_x, sizeof(double) * n3 * ns));
-        TRY(ensure(f_v, sizeof(double) * n3 * ns));
-        TRY(ensure(tmp_x, sizeof(double) * n3));
-        TRY(ensure(tmp_v, sizeof(double) * n3));
-        TRY(ensure(q, sizeof(double) * nn * ns));          // per-slice copies for the batched F
-        TRY(ensure(m, sizeof(double) * nn * ns));
-        TRY(ensure(lj, nn * ns));
-        const size_t nblk = (n3 + 255) / 256;
-        TRY(ensure(part, sizeof(double) * nblk * ns));
-        TRY(ensure(dx, sizeof(double)));
-        TRY(ensure(pst, sizeof(int)));
-        CUDA_TRY(cudaMemsetAsync(pst.p, 0, sizeof(int), st));
-        // projection of corrected states: threshold 10x, target 1x the fine propagator's SHAKE tolerance
-        const double ptol = F->precision == MSM_FP32 ? shake_tol<float>() : shake_tol<double>();
-        const double d_oh2 = F->d_oh * F->d_oh, d_hh2 = F->d_hh * F->d_hh;
-        CUDA_TRY(cudaMemcpyAsync(lam_x.p, s0.x, sizeof(double) * n3, cudaMemcpyDefault, st));
-        CUDA_TRY(cudaMemcpyAsync(lam_v.p, s0.v, sizeof(double) * n3, cudaMemcpyDefault, st));
-        for (size_t k = 0; k < ns; k++) {
-            CUDA_TRY(cudaMemcpyAsync(q.as<double>() + k * nn, s0.q, sizeof(double) * nn, cudaMemcpyDefault, st));
-            CUDA_TRY(cudaMemcpyAsync(m.as<double>() + k * nn, s0.m, sizeof(double) * nn, cudaMemcpyDefault, st));
-            if (s0.lj) CUDA_TRY(cudaMemcpyAsync(lj.as<uint8_t>() + k * nn, s0.lj, nn, cudaMemcpyDefault, st));
-            else CUDA_TRY(cudaMemsetAsync(lj.as<uint8_t>() + k * nn, 0, nn, st));
-        }
-        auto X = [&](DevBuf &b, size_t k) { return b.as<double>() + k * n3; };
-        SysIn si;
-        si.n = s0.n; si.n_mol = s0.n_mol;
-        memcpy(si.box, s0.box, sizeof si.box);
-        std::vector<SysIn> sis(ns, si);
-        // one system, G, on tmp
-        auto runG = [&]() -> int {
-            RunSys t;
-            t.B = 1; t.sys = &si; t.x = tmp_x.as<double>(); t.v = tmp_v.as<double>();
-            t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
-            int r = run_md(hG, t, dtG, stepsG, nullptr, 0, st);
-            if (r == MSM_OK) r = finish(hG, st);
-            if (r != MSM_OK) {
-                char m[512];
-                snprintf(m, sizeof m, "%s", msm_last_error());
-                return fail_msg(r, "coarse propagator G: %s", m);
-            }
-            return MSM_OK;
-        };
-        // init row: lambda^0_{n+1} = G(lambda^0_n)
-        for (size_t k = 0; k < ns; k++) {
-            CUDA_TRY(cudaMemcpyAsync(tmp_x.p, X(lam_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(tmp_v.p, X(lam_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            TRY(runG());
-            CUDA_TRY(cudaMemcpyAsync(X(gold_x, k), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(X(gold_v, k), tmp_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(X(lam_x, k + 1), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(X(lam_v, k + 1), tmp_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-        }
-        int done = 0;
-        double dxh = INFINITY;
-        bool diverged = false;
-        for (int it = 0; it < max_iter; it++) {
-            const size_t k0 = (size_t)std::min(it, n_slices);    // slices k < it are exact
-            // f_n = F(lambda^k_n) for every slice n >= it: one batch
-            if (k0 < ns) {
-                CUDA_TRY(cudaMemcpyAsync(X(f_x, k0), X(lam_x, k0), sizeof(double) * n3 * (ns - k0), cudaMemcpyDeviceToDevice, st));
-                CUDA_TRY(cudaMemcpyAsync(X(f_v, k0), X(lam_v, k0), sizeof(double) * n3 * (ns - k0), cudaMemcpyDeviceToDevice, st));
-                RunSys t;
-                t.B = (int)(ns - k0); t.sys = sis.data(); t.x = X(f_x, k0); t.v = X(f_v, k0);
-                t.q = q.as<double>(); t.m = m.as<double>(); t.lj = lj.as<uint8_t>();
-                int r = run_md(hF, t, dtF, stepsF, nullptr, 0, st);
-                if (r == MSM_OK) r = finish(hF, st);
-                if (r != MSM_OK) {
-                    char m[512];
-                    snprintf(m, sizeof m, "%s", msm_last_error());
-                    return fail_msg(r, "fine propagator F: %s", m);
-                }
-            }
-            // sequential correction sweep over the slices that are not exact yet
-            CUDA_TRY(cudaMemcpyAsync(new_x.p, lam_x.p, sizeof(double) * n3 * (k0 + 1), cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemcpyAsync(new_v.p, lam_v.p, sizeof(double) * n3 * (k0 + 1), cudaMemcpyDeviceToDevice, st));
-            CUDA_TRY(cudaMemsetAsync(part.p, 0, sizeof(double) * nblk * ns, st));
-            for (size_t k = k0; k < ns; k++) {
-                CUDA_TRY(cudaMemcpyAsync(tmp_x.p, X(new_x, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                CUDA_TRY(cudaMemcpyAsync(tmp_v.p, X(new_v, k), sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                const int rg = runG();
-                if (rg != MSM_OK) {
-                    // the coarse propagator broke down on a corrected state: the iteration
-                    // diverged; hand back the last complete iterate
-                    char m[512];
-                    snprintf(m, sizeof m, "%s", msm_last_error());
-                    diverged = true;
-                    fail_msg(MSM_ENOCONV, "parareal: diverged at iteration %d, slice %zu (%s)", it + 1, k, m);
-                    break;
-                }
-                TRY(launch_parareal_update((int)n3, X(f_x, k), tmp_x.as<double>(), X(gold_x, k), X(new_x, k + 1),
-                                           nullptr, nullptr, st));
-                TRY(launch_parareal_update((int)n3, X(f_v, k), tmp_v.as<double>(), X(gold_v, k), X(new_v, k + 1),
-                                           nullptr, nullptr, st));
-                TRY(launch_pr_project((int)s0.n_mol, X(new_x, k + 1), X(new_v, k + 1), m.as<double>(), d_oh2, d_hh2,
-                                      10.0 * ptol, ptol, 1e-14, pst.as<int>(), st));
-                TRY(launch_absdiff_partials((int)n3, X(new_x, k + 1), X(lam_x, k + 1), part.as<double>() + k * nblk, st));
-                CUDA_TRY(cudaMemcpyAsync(X(gold_x, k), tmp_x.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-                CUDA_TRY(cudaMemcpyAsync(X(gold_v, k), tmp_v.p, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
-            }
-            if (diverged) break;
-            TRY(launch_max_reduce((int)(nblk * ns), part.as<double>(), dx.as<double>(), st));
-            CUDA_TRY(cudaMemcpyAsync(&hF->h_scal[0], dx.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaMemcpyAsync(hF->h_status + 2, pst.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaStreamSynchronize(st));
-            if (hF->h_status[2]) return fail_msg(MSM_ENOCONV, "projection of a corrected slice onto the rigid "
-                                                              "constraints did not converge");
-            dxh = hF->h_scal[0];
-            std::swap(lam_x, new_x);
-            std::swap(lam_v, new_v);
-            done = it + 1;
-            if (dxh <= tol) break;
-        }
-        CUDA_TRY(cudaMemcpyAsync(slices_x, lam_x.p, sizeof(double) * n3 * (ns + 1), cudaMemcpyDefault, st));
-        CUDA_TRY(cudaMemcpyAsync(slices_v, lam_v.p, sizeof(double) * n3 * (ns + 1), cudaMemcpyDefault, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-        if (iters_done) *iters_done = done;
-        if (last_dx) *last_dx = dxh;
-        if (diverged) return MSM_ENOCONV;                     // message set above
-        if (max_iter > 0 && !(dxh <= tol)) return fail_msg(MSM_ENOCONV, "parareal: max |dx| = %g after %d iterations", dxh, done);
-        return MSM_OK;
-    };
-    rc = body();
-    cleanup();
-    return rc;
+    return MSM_OK;
+}
+
+extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F, double dtF,
+                            int32_t stepsF, const msm_system *state0, int32_t n_slices, int32_t max_iter, double tol,
+                            double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx, void *stream)
+{
+    TRY(parareal_args(G, dtG, stepsG, F, dtF, stepsF, state0, n_slices, max_iter, tol, slices_x, slices_v));
+    PararealRun P{G, F, dtG, dtF, stepsG, stepsF, state0, n_slices, n_slices, max_iter, false, tol,
+                  slices_x, slices_v, iters_done, last_dx};
+    return parareal_impl(P, (cudaStream_t)stream);
+}
+
+extern "C" int parareal_run_window(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F,
+                                   double dtF, int32_t stepsF, const msm_system *state0, int32_t n_slices,
+                                   int32_t window, int32_t max_iter, double tol, double *slices_x, double *slices_v,
+                                   int32_t *iters_done, double *last_dx, void *stream)
+{
+    TRY(parareal_args(G, dtG, stepsG, F, dtF, stepsF, state0, n_slices, max_iter, tol, slices_x, slices_v));
+    if (window < 1) return fail_msg(MSM_EINVAL, "window must be >= 1");
+    PararealRun P{G, F, dtG, dtF, stepsG, stepsF, state0, n_slices, std::min(window, n_slices), max_iter, true, tol,
+                  slices_x, slices_v, iters_done, last_dx};
+    return parareal_impl(P, (cudaStream_t)stream);
 }
 
 // -------------------------------------------------------------- inspection
@@ -1745,6 +1933,7 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
 extern "C" int msm_grid_shape(msm_handle *h, int32_t level, int64_t shape[3], int64_t lo[3])
 {
     if (!h || !h->have_geom) return fail_msg(MSM_EINVAL, "no evaluation yet");
+    if (!has_grids(h->p)) return fail_msg(MSM_EINVAL, "the cutoff methods have no grids");
     if (level < 0 || level >= h->gg.levels) return fail_msg(MSM_EINVAL, "level out of range");
     for (int d = 0; d < 3; d++) {
         if (shape) shape[d] = h->gg.L[level].n[d];
@@ -1756,6 +1945,7 @@ extern "C" int msm_grid_shape(msm_handle *h, int32_t level, int64_t shape[3], in
 extern "C" int msm_stage_grid(msm_handle *h, int32_t level, int32_t which, double *out, int64_t count)
 {
     if (!h || !h->have_geom || !out) return fail_msg(MSM_EINVAL, "no evaluation yet");
+    if (!has_grids(h->p)) return fail_msg(MSM_EINVAL, "the cutoff methods have no grids");
     const int l = h->gg.levels;
     if (level < 0 || level >= l || which < 0 || which > 2 || (which == 1 && level == l - 1))
         return fail_msg(MSM_EINVAL, "no such grid");

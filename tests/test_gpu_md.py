@@ -103,21 +103,26 @@ def test_md_host_buffers_equal_device_buffers(api, torch, small_water):
     assert np.array_equal(hs.pos, d.pos.cpu().numpy()) and np.array_equal(hs.vel, d.vel.cpu().numpy())
 
 
-def test_nve_energy_is_conserved(api, torch):
+def test_nve_energy_error_is_second_order(api, torch):
+    """Velocity Verlet's energy error is second order in dt (Sec. 2's integrator):
+    over the same 50 fs from the same state, halving dt cuts the largest total-energy
+    deviation about four-fold, in FP64 and in FP32; and the FP32 path's deviation at
+    the smaller step stays that of the FP64 path (its arithmetic adds no visible
+    error of its own)."""
     s = inputs.water_box(3000, 3.1, margin=1.0)
     out = {}
     for prec in ("fp64", "fp32"):
-        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water")
-        d = _dev_sys(torch, s)
-        uk = m.md_run(d, dt=0.002, n_steps=100).cpu().numpy()
-        e = uk.sum(1)
-        out[prec] = (np.abs(e - e[0]).max(), uk[:, 1].mean())
-        assert np.all(np.isfinite(uk))
-    # velocity Verlet at 2 fs: energy fluctuations stay a small fraction of the kinetic energy,
-    # and FP32 arithmetic does not add visible drift on top of the FP64 run
-    for prec in out:
-        assert out[prec][0] < 0.05 * out[prec][1]
-    assert out["fp32"][0] < 2.0 * out["fp64"][0] + 1e-3 * out["fp64"][1]
+        fl = []
+        for dt, n in ((0.002, 25), (0.001, 50)):
+            m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water", wall_k=1e4, wall_width=0.8)
+            d = _dev_sys(torch, s)
+            uk = m.md_run(d, dt=dt, n_steps=n).cpu().numpy()
+            assert np.all(np.isfinite(uk))
+            e = uk.sum(1)
+            fl.append(np.abs(e - e[0]).max())
+        out[prec] = fl
+        assert fl[1] < fl[0] / 2.5, (prec, fl)
+    assert abs(out["fp32"][1] - out["fp64"][1]) < 0.1 * out["fp64"][1], out
 
 
 # ------------------------------------------------------------------ parareal
@@ -188,3 +193,37 @@ def test_verlet_lists_equal_cell_search(api, torch, prec, tol):
         out[skin] = (d.pos.cpu().numpy(), uk)
     assert np.abs(out[0.0][0] - out[0.1][0]).max() <= tol
     assert np.abs(out[0.0][1] - out[0.1][1]).max() <= 10 * tol * np.abs(out[0.0][1]).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_windowed_parareal_invariants(api, torch, pr_sys, prec):
+    """The sliding window (Sec. 4's computational window): a full window with
+    tol = 0 gives parareal_run's iterates bit for bit; a one-slice window is the
+    serial fine run (one iteration per slice); a two-slice window iterated to the
+    end gives every slice exactly."""
+    s = pr_sys
+    n_slices = 5
+    fx, fv = _serial(api, torch, s, FINE, prec, n_slices)
+    for k in (1, 2):
+        a = api.parareal_run(COARSE, FINE, s, n_slices, k, 0.0, precision=prec)
+        b = api.parareal_run(COARSE, FINE, s, n_slices, k, 0.0, precision=prec, window=n_slices)
+        assert a[2] == b[2] == k
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, n_slices, 50, 0.0, precision=prec, window=1)
+    assert conv and it == n_slices
+    assert np.array_equal(xs, fx) and np.array_equal(vs, fv)
+    xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, n_slices, 50, 0.0, precision=prec, window=2)
+    assert conv and np.array_equal(xs, fx) and np.array_equal(vs, fv)
+
+
+def test_windowed_parareal_matches_oracle(api, torch, pr_sys):
+    s = pr_sys
+    for window, iters in ((2, 3), (3, 2)):
+        oxs, ovs, oit, odx, orc = oracle.parareal_window(s, COARSE, FINE, n_slices=5, window=window,
+                                                         max_iter=iters, tol=0.0)
+        xs, vs, it, dx, conv = api.parareal_run(COARSE, FINE, s, 5, iters, 0.0, precision="fp64", window=window)
+        assert it == oit == iters and not conv
+        reached = np.any(oxs != 0, axis=(1, 2))
+        assert np.array_equal(np.any(xs != 0, axis=(1, 2)), reached)
+        assert np.abs(xs[reached] - oxs[reached]).max() < 1e-9
+        assert np.abs(vs[reached] - ovs[reached]).max() < 1e-6

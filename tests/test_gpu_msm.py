@@ -7,10 +7,16 @@ Bars:
     relative energy <= 1e-12;
   * FP32 path: relative force RMS <= 1e-4 and relative potential RMS <= 1e-4,
     relative energy <= 1e-6.
+Per atom, besides the RMS bars: max_i |F_i - F_i^ref| <= MAX_F * F_rms and
+max_i |phi_i - phi_i^ref| <= MAX_F * phi_rms (FP32: 2e-3, FP64: 1e-10), so a few
+atoms wrong by a fraction of a percent cannot hide inside an RMS over thousands.
 The FP32 energy bar follows from the arithmetic: U = 1/2 sum q_i phi_i is
-accumulated in FP64 from per-atom FP32 potentials whose relative error is
-~1e-6; the errors are independent across atoms, so the sum's relative error
-is far below 1e-6 unless U cancels strongly.
+accumulated in FP64 from per-atom potentials whose FP32 parts (short-range sum,
+grid potential) have independent relative errors of ~1e-6, while the large terms
+that cancel inside U -- every atom's self term and, in the water model, the
+excluded pairs' smooth terms -- are formed in FP64.  The one exception is a
+single atom, whose U is nothing but the cancelled self energy: there the bar is
+relative to that self energy.
 """
 import numpy as np
 import pytest
@@ -21,13 +27,28 @@ from paper_1309_1889_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 A, H = 1.2, 0.25
-TOL = {"fp64": dict(f=1e-12, p=1e-12, e=1e-12), "fp32": dict(f=1e-4, p=1e-4, e=1e-6)}
+TOL = {"fp64": dict(f=1e-12, p=1e-12, e=1e-12, fmax=1e-10, vir=1e-12),
+       "fp32": dict(f=1e-4, p=1e-4, e=1e-6, fmax=2e-3, vir=1e-6)}
 
 
 def rel_rms(x, ref):
     x = np.asarray(x, dtype=np.float64); ref = np.asarray(ref, dtype=np.float64)
     den = np.sqrt((ref ** 2).sum())
     return float(np.sqrt(((x - ref) ** 2).sum()) / (den if den > 0 else 1.0))
+
+
+def max_rel(x, ref):
+    """Largest per-atom error over the RMS magnitude of the reference (vectors by norm)."""
+    x = np.asarray(x, dtype=np.float64); ref = np.asarray(ref, dtype=np.float64)
+    if ref.ndim == 1:
+        x, ref = x[:, None], ref[:, None]
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    return float(np.linalg.norm(x - ref, axis=1).max() / (rms if rms > 0 else 1.0))
+
+
+def check_atoms(f, p, ref_f, ref_p, t):
+    assert rel_rms(f, ref_f) <= t["f"] and max_rel(f, ref_f) <= t["fmax"]
+    assert rel_rms(p, ref_p) <= t["p"] and max_rel(p, ref_p) <= t["fmax"]
 
 
 @pytest.fixture(scope="module")
@@ -105,10 +126,10 @@ def test_msm_matches_oracle_on_water(api, torch, water3k, water3k_ref, prec):
     ref = water3k_ref
     t = TOL[prec]
     assert abs(float(e) - ref["energy"]) <= t["e"] * abs(ref["energy"])
-    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
-    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+    check_atoms(f.cpu().numpy(), p.cpu().numpy(), ref["forces"], ref["pot"], t)
+    # virial sum_i r_i . F_i, against the oracle's forces, relative to sum_i |r_i . F_i|
     vir_ref = (s.pos * ref["forces"]).sum()
-    assert abs(float(vir) - vir_ref) <= 1e-3 * np.abs(s.pos * ref["forces"]).sum()
+    assert abs(float(vir) - vir_ref) <= t["vir"] * np.abs((s.pos * ref["forces"]).sum(1)).sum()
 
 
 # ragged sizes, non-cubic boxes, every level count, empty-ish systems
@@ -126,14 +147,14 @@ def test_msm_matches_oracle_on_clouds(api, torch, n, L, levels, prec):
     m = api.MSM(a=A, h=H, levels=levels, precision=prec)
     e, f, p = m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box)
     t = TOL[prec]
-    # U = 1/2 sum q_i phi_i minus the self energy 1/2 k_e sum q_i^2 gamma(0)/a: rounding scales
-    # with those terms, so the bar is relative to their magnitude (|U| alone is ill-conditioned
-    # for one or two atoms, where U is almost entirely cancelled self energy)
-    scale = abs(ref["energy"]) + 0.5 * oracle.KE * (s.q ** 2).sum() * 15.0 / (8.0 * A)
+    # a single atom's U is its grid self energy minus the exact self term, nothing else:
+    # the bar is relative to that self energy 1/2 k_e q^2 gamma(0)/a there
+    scale = abs(ref["energy"]) if n > 1 else 0.5 * oracle.KE * (s.q ** 2).sum() * 15.0 / (8.0 * A)
     assert abs(float(e) - ref["energy"]) <= t["e"] * scale
     if n > 1:
-        assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
-    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+        check_atoms(f.cpu().numpy(), p.cpu().numpy(), ref["forces"], ref["pot"], t)
+    else:
+        assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
 
 
 def test_host_and_device_inputs_give_identical_bits(api, torch, water3k):
@@ -195,14 +216,6 @@ def test_batched_uneven_systems_equal_single_evaluations(api, torch):
         assert torch.equal(f[offs[k]:offs[k + 1]], f1) and torch.equal(p[offs[k]:offs[k + 1]], p1)
 
 
-def _excluded_pair_energy(s):
-    x = s.pos[: 3 * s.n_mol].reshape(-1, 3, 3); q = s.q[: 3 * s.n_mol].reshape(-1, 3)
-    tot = 0.0
-    for a, b in ((0, 1), (0, 2), (1, 2)):
-        tot += np.abs(oracle.KE * q[:, a] * q[:, b] / np.linalg.norm(x[:, a] - x[:, b], axis=1)).sum()
-    return tot
-
-
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_water_model_matches_oracle(api, torch, prec):
     # atoms within 0.6 nm of a face feel the flat-bottom wall (margin 0.5 nm)
@@ -213,13 +226,21 @@ def test_water_model_matches_oracle(api, torch, prec):
                        n_mol=s.n_mol, lj=torch.tensor(s.lj, device="cuda"))
     e, f, p = m.system_forces(sd)
     t = TOL[prec]
-    # The oracle forms U by subtracting the excluded pairs' exact Coulomb energy (~2.5e5 kJ/mol
-    # here) from the all-pairs MSM energy, so its own rounding scales with those terms: the
-    # energy bar is relative to |U| plus that magnitude.
-    scale = abs(ref["energy"]) + _excluded_pair_energy(s)
+    # FP64: the oracle forms U by subtracting the excluded pairs' full Coulomb energy (~1.4e2 x |U|
+    # here) from its all-pairs MSM energy, the GPU path by skipping those pairs' g* and subtracting
+    # their smooth part; the two FP64 roundings differ by ~1e-16 of that energy, which exceeds
+    # 1e-12 |U|.  The FP32 bar is 1e-6 |U| itself (the FP32 rounding is far above the oracle's).
+    scale = abs(ref["energy"]) + (_excluded_pair_energy(s) if prec == "fp64" else 0.0)
     assert abs(float(e) - ref["energy"]) <= t["e"] * scale
-    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
-    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+    check_atoms(f.cpu().numpy(), p.cpu().numpy(), ref["forces"], ref["pot"], t)
+
+
+def _excluded_pair_energy(s):
+    x = s.pos[: 3 * s.n_mol].reshape(-1, 3, 3); q = s.q[: 3 * s.n_mol].reshape(-1, 3)
+    tot = 0.0
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        tot += np.abs(oracle.KE * q[:, a] * q[:, b] / np.linalg.norm(x[:, a] - x[:, b], axis=1)).sum()
+    return tot
 
 
 def test_fp32_and_fp64_paths_agree_at_full_size(api, torch):
@@ -233,7 +254,7 @@ def test_fp32_and_fp64_paths_agree_at_full_size(api, torch):
     e32, f32, p32 = m32.energy_forces(pos, q, s.box)
     e64, f64, p64 = m64.energy_forces(pos, q, s.box)
     assert abs(float(e32) - float(e64)) <= 1e-6 * abs(float(e64))
-    assert rel_rms(f32.cpu().numpy(), f64.cpu().numpy()) <= 1e-4
+    check_atoms(f32.cpu().numpy(), p32.cpu().numpy(), f64.cpu().numpy(), p64.cpu().numpy(), TOL["fp32"])
     rng = np.random.default_rng(0)
     tg = rng.choice(s.n, 512, replace=False)
     ophi, of = oracle.short_range(s.pos, s.q, A, s.box, targets=tg)
@@ -281,7 +302,63 @@ def test_long_cutoff_takes_the_row_list_in_segments(api, torch, prec):
     ophi, of = oracle.short_range(s.pos, s.q, a, s.box)
     assert rel_rms(phi, ophi) <= t["f"] and rel_rms(fs, of) <= t["f"]
     ref = oracle.msm(s.pos, s.q, s.box, a, h, 1)
-    scale = abs(ref["energy"]) + 0.5 * oracle.KE * (s.q ** 2).sum() * 15.0 / (8.0 * a)
-    assert abs(float(e) - ref["energy"]) <= t["e"] * scale
-    assert rel_rms(f.cpu().numpy(), ref["forces"]) <= t["f"]
-    assert rel_rms(p.cpu().numpy(), ref["pot"]) <= t["p"]
+    assert abs(float(e) - ref["energy"]) <= t["e"] * abs(ref["energy"])
+    check_atoms(f.cpu().numpy(), p.cpu().numpy(), ref["forces"], ref["pot"], t)
+
+
+def _water1m_device(torch, s, with_vel=False):
+    t = lambda x: _dev(torch, x)
+    return inputs.System(pos=t(s.pos), q=t(s.q), mass=t(s.mass), box=s.box, vel=t(s.vel) if with_vel else None,
+                         n_mol=s.n_mol, lj=torch.tensor(s.lj, device="cuda"))
+
+
+def _fp32_fp64_pair(api, sd, levels):
+    out = {}
+    for prec in ("fp64", "fp32"):
+        m = api.MSM(a=A, h=H, levels=levels, precision=prec, model="water", wall_k=1e4, wall_width=0.8)
+        e, f, p = m.system_forces(sd)
+        out[prec] = (float(e), f.cpu().numpy(), p.cpu().numpy())
+        m.close()
+    return out["fp64"], out["fp32"]
+
+
+def test_water_model_fp32_energy_at_full_size(api, torch):
+    """The 1,000,000-atom water model (exclusions, LJ, wall) on the jittered-lattice
+    start: FP32 forces within the FP32 bars, per atom too, and the FP32 energy within
+    1e-6 of the energy's own scale, sum_i |q_i phi_i| / 2.  On this start the random
+    orientations leave |U| at ~0.3 % of that scale (0.6 kJ/mol per molecule), and the
+    FP32 pair sum carries a bias proportional to N (~3e-6 kJ/mol per atom: the rsqrt
+    approximation's mean error times the intermolecular 1/r energy inside the cutoff
+    spheres, ~+6e7 kJ/mol here, and the FP32 rounding of the gamma coefficients),
+    which is 1.4e-5 of |U| there.  The relaxed state below holds 1e-6 of |U| itself."""
+    cfg = inputs.WORKLOADS["water1M"]
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=1.0, with_velocities=False)
+    (e64, f64, p64), (e32, f32, p32) = _fp32_fp64_pair(api, _water1m_device(torch, s), cfg["levels"])
+    scale = 0.5 * float(np.abs(s.q * p64).sum())
+    print(f"lattice start: U64 {e64:.6f}, |dU| {abs(e32 - e64):.4f} kJ/mol = {abs(e32 - e64) / abs(e64):.2e} of |U|, "
+          f"{abs(e32 - e64) / scale:.2e} of sum|q phi|/2 = {scale:.4e}")
+    assert abs(e32 - e64) <= 1e-6 * scale
+    check_atoms(f32, p32, f64, p64, TOL["fp32"])
+
+
+def test_water_model_fp32_energy_relaxed_full_size(api, torch):
+    """The same 1,000,000-atom box after 2 ps of its own FP32 dynamics with the
+    velocities rescaled to 300 K every 0.1 ps (a liquid-like state: hydrogen-bonded
+    orientations, |U| tens of kJ/mol per molecule): the FP32 energy within 1e-6 of
+    |U| of the FP64 path's, forces within the FP32 bars.  The comparison is of the
+    two GPU paths on one input; the FP64 path matches the oracle to 1e-12 elsewhere."""
+    cfg = inputs.WORKLOADS["water1M"]
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=1.0, seed=0, vel_seed=1)
+    d = _water1m_device(torch, s, with_vel=True)
+    dof = 6 * s.n_mol + 3 * (s.n - 3 * s.n_mol)
+    kb = 0.0083144626
+    m = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", wall_k=1e4, wall_width=0.8)
+    for _ in range(20):
+        uk = m.md_run(d, 0.002, 50)
+        d.vel.mul_(float(np.sqrt(0.5 * dof * kb * 300.0 / float(uk[-1, 1]))))
+    m.close()
+    torch.cuda.synchronize()
+    (e64, f64, p64), (e32, f32, p32) = _fp32_fp64_pair(api, d, cfg["levels"])
+    print(f"relaxed: U64 {e64:.6f}, |dU| {abs(e32 - e64):.4f} kJ/mol = {abs(e32 - e64) / abs(e64):.2e} of |U|")
+    assert abs(e32 - e64) <= 1e-6 * abs(e64)
+    check_atoms(f32, p32, f64, p64, TOL["fp32"])

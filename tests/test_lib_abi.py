@@ -74,3 +74,44 @@ def test_flag_values_match_the_header():
 def test_library_is_built_for_sm_103a():
     from paper_1309_1889_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_method_values_and_validation(L):
+    from paper_1309_1889_gb300 import api
+    hdr = (ROOT / "include" / "msm.h").read_text()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define MSM_METHOD_(\w+)\s+(\d+)", hdr)}
+    assert defs == {"MSM": 0, "CUTOFF": 1, "WOLF": 2}
+    assert {k.upper(): v for k, v in api.METHODS.items()} == defs
+    p = api.Params()
+    L.msm_default_params(C.byref(p))
+    assert p.method == 0 and p.wolf_alpha == 0.0
+    h = C.c_void_p()
+    bad = api.make_params(method=3)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"unknown method" in L.msm_last_error()
+    bad = api.make_params(method="wolf", wolf_alpha=-1.0)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"wolf_alpha" in L.msm_last_error()
+    bad = api.make_params(method="wolf", wolf_alpha=2.0, list_skin=0.1)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"Verlet lists" in L.msm_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and field offsets of msm_params and msm_system as a C compiler lays them
+    out from include/msm.h, against the ctypes structures of the binding."""
+    from paper_1309_1889_gb300 import api
+    src = tmp_path / "layout.c"
+    fields_p = [f[0] for f in api.Params._fields_]
+    fields_s = [f[0] for f in api.SystemC._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT / "include" / "msm.h"}"', 'int main(void){',
+            'printf("%zu\\n", sizeof(msm_params));']
+    body += [f'printf("%zu\\n", offsetof(msm_params, {f}));' for f in fields_p]
+    body += ['printf("%zu\\n", sizeof(msm_system));']
+    body += [f'printf("%zu\\n", offsetof(msm_system, {f}));' for f in fields_s]
+    body += ['return 0;}']
+    src.write_text("\n".join(body))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [C.sizeof(api.Params)] + [getattr(api.Params, f).offset for f in fields_p]
+    want += [C.sizeof(api.SystemC)] + [getattr(api.SystemC, f).offset for f in fields_s]
+    assert got == want

@@ -236,3 +236,16 @@ def test_model_potentials_are_charge_derivatives():
         up = oracle.model_forces(dataclasses.replace(s, q=qp), A, H, 3)["energy"]
         um = oracle.model_forces(dataclasses.replace(s, q=qm), A, H, 3)["energy"]
         assert ref["pot"][atom] == pytest.approx((up - um) / (2 * d), rel=1e-7, abs=1e-7)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    s = inputs.water_box(300, 1.5, margin=0.5, seed=4, with_velocities=False)
+    k = oracle.num_threads()
+    try:
+        oracle.set_num_threads(1)
+        one = oracle.model_forces(s, A, H, 3)
+    finally:
+        oracle.set_num_threads(k)
+    many = oracle.model_forces(s, A, H, 3)
+    assert one["energy"] == many["energy"]
+    assert np.array_equal(one["forces"], many["forces"]) and np.array_equal(one["pot"], many["pot"])
