@@ -328,9 +328,10 @@ def test_water_model_fp32_energy_at_full_size(api, torch):
     1e-6 of the energy's own scale, sum_i |q_i phi_i| / 2.  On this start the random
     orientations leave |U| at ~0.3 % of that scale (0.6 kJ/mol per molecule), and the
     FP32 pair sum carries a bias proportional to N (~3e-6 kJ/mol per atom: the rsqrt
-    approximation's mean error times the intermolecular 1/r energy inside the cutoff
-    spheres, ~+6e7 kJ/mol here, and the FP32 rounding of the gamma coefficients),
-    which is 1.4e-5 of |U| there.  The relaxed state below holds 1e-6 of |U| itself."""
+    approximation's ulp errors, weighted by the charge products of the pairs, and the
+    FP32 rounding of the gamma coefficients, both amplified by the intermolecular 1/r
+    energy inside the cutoff spheres, ~+6e7 kJ/mol here), which is 1.4e-5 of |U|
+    there.  The relaxed state below holds 1e-6 of |U| itself."""
     cfg = inputs.WORKLOADS["water1M"]
     s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=1.0, with_velocities=False)
     (e64, f64, p64), (e32, f32, p32) = _fp32_fp64_pair(api, _water1m_device(torch, s), cfg["levels"])
