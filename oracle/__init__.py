@@ -74,6 +74,8 @@ def lib():
         L.orc_cutoff.restype = i; L.orc_cutoff.argtypes = [i, d, d, d, i64, i64, p, p, p, p, p]
         L.orc_model_forces.restype = i
         L.orc_model_forces.argtypes = [p, i, i64, i64, p, p, p, p, p, p, p]
+        L.orc_model_forces_split.restype = i
+        L.orc_model_forces_split.argtypes = [p, i, i64, i64, p, p, p, p, p, p, p, p]
         L.orc_md_run.restype = i
         L.orc_md_run.argtypes = [p, i, i64, i64, p, p, p, p, p, p, d, i, p]
         L.orc_parareal.restype = i
@@ -298,11 +300,12 @@ LJ_EPSILON = 0.6364    # kJ/mol
 
 
 def model_params(a, h, ke=KE, sigma=LJ_SIGMA, eps=LJ_EPSILON, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
-                 method="msm", wolf_alpha=0.0):
+                 method="msm", wolf_alpha=0.0, mts=0):
+    """mts: fast steps per slow step of md_run's multiple time stepping (<= 1: plain velocity Verlet)."""
     if d_hh is None:
         import math
         d_hh = 2.0 * d_oh * math.sin(math.radians(104.52) / 2.0)
-    return _f64([a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_width, METHODS[method], wolf_alpha])
+    return _f64([a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_width, METHODS[method], wolf_alpha, mts])
 
 
 def model_forces(sys, a, h, levels, ke=KE, pos=None, **kw):
@@ -316,8 +319,23 @@ def model_forces(sys, a, h, levels, ke=KE, pos=None, **kw):
     return dict(energy=float(e[0]), forces=f, pot=p)
 
 
+def model_forces_split(sys, a, h, levels, ke=KE, pos=None, **kw):
+    """The model's forces split for multiple time stepping: fast (short-range g*
+    over non-excluded pairs, Lennard-Jones, wall) and slow (grid part minus the
+    excluded pairs' smooth part); energy and its slow part."""
+    x = _f64(sys.pos if pos is None else pos)
+    mdp = model_params(a, h, ke, **kw)
+    n = x.shape[0]
+    e = np.zeros(1); es = np.zeros(1); ff = np.zeros((n, 3)); fs = np.zeros((n, 3))
+    lj = np.ascontiguousarray(sys.lj, dtype=np.uint8)
+    _check(lib().orc_model_forces_split(_ptr(mdp), int(levels), n, int(sys.n_mol), _ptr(x), _ptr(_f64(sys.q)),
+                                        _ptr(lj), _ptr(_f64(sys.box)), _ptr(e), _ptr(es), _ptr(ff), _ptr(fs)))
+    return dict(energy=float(e[0]), energy_slow=float(es[0]), f_fast=ff, f_slow=fs)
+
+
 def md_run(sys, a, h, levels, dt, n_steps, ke=KE, x=None, v=None, **kw):
-    """Velocity Verlet + SHAKE/RATTLE.  Returns (x, v, uk (n_steps+1, 2))."""
+    """Velocity Verlet + SHAKE/RATTLE (with mts=k > 1: the multiple-time-step
+    impulse method, the grid part every k steps).  Returns (x, v, uk (n_steps+1, 2))."""
     x = _f64(sys.pos if x is None else x).copy()
     v = _f64(sys.vel if v is None else v).copy()
     mdp = model_params(a, h, ke, **kw)
@@ -342,7 +360,7 @@ def project_rigid(x, v, mass, n_mol, d_oh=0.09572, d_hh=None):
 
 def _pack(p, ke):
     mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0),
-                       method=p.get("method", "msm"), wolf_alpha=p.get("wolf_alpha", 0.0))
+                       method=p.get("method", "msm"), wolf_alpha=p.get("wolf_alpha", 0.0), mts=p.get("mts", 0))
     return _f64(list(mdp) + [p["dt"], p["steps"], p["levels"]])
 
 
@@ -368,9 +386,7 @@ def parareal(sys, G: dict, F: dict, n_slices, max_iter, tol, ke=KE):
     n = sys.n
 
     def pack(p):
-        mdp = model_params(p["a"], p["h"], ke, wall_k=p.get("wall_k", 0.0), wall_width=p.get("wall_width", 0.0),
-                           method=p.get("method", "msm"), wolf_alpha=p.get("wolf_alpha", 0.0))
-        return _f64(list(mdp) + [p["dt"], p["steps"], p["levels"]])
+        return _pack(p, ke)
 
     xs = np.zeros((n_slices + 1, n, 3)); vs = np.zeros((n_slices + 1, n, 3))
     xs[0] = sys.pos; vs[0] = sys.vel

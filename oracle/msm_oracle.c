@@ -29,7 +29,10 @@
  *   orc_cutoff .............. Sec. 5, the coarse propagator's electrostatics:
  *                             simple cutoff (Coulomb's law for pairs within a)
  *                             or Wolf summation (damped, shifted, neutralised)
- *   orc_md_run .............. Sec. 2, F = -dU/dr and velocity Verlet
+ *   orc_md_run .............. Sec. 2, F = -dU/dr and velocity Verlet; with
+ *                             mts > 1 the multiple-time-step impulse method
+ *                             (Sec. 3: the MSM suits one), grid part as the
+ *                             slow force (orc_model_forces_split)
  *   orc_parareal ............ Sec. 4, lambda^{k+1}_{n+1} = G(lambda^{k+1}_n)
  *                                       + F(lambda^k_n) - G(lambda^k_n)
  *   orc_parareal_window ..... Sec. 4, the same recurrence over a sliding
@@ -671,10 +674,12 @@ int orc_cutoff(int method, double a, double alpha, double ke, int64_t n, int64_t
  * of the cutoff methods of orc_cutoff (1 simple cutoff, 2 Wolf summation with
  * damping wolf_alpha), which skip the intramolecular pairs instead of
  * subtracting them.
- * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh, wall_k, wall_w, method, wolf_alpha}. */
+ * mdp = {a, h, k_e, lj_sigma, lj_epsilon, d_oh, d_hh, wall_k, wall_w, method, wolf_alpha, mts}
+ * (mts: the multiple-time-step factor of md_steps). */
 typedef struct {
     double a, h, ke, sigma, eps, d_oh, d_hh, wall_k, wall_w, alpha;
     int method;
+    int mts;            /* fast steps per slow step (<= 1: plain velocity Verlet) */
     int l;
     int64_t n, n_mol;
     const double *q, *m;
@@ -687,48 +692,16 @@ static void model_from(orc_model *md, const double *mdp, int l, int64_t n, int64
 {
     md->a = mdp[0]; md->h = mdp[1]; md->ke = mdp[2]; md->sigma = mdp[3]; md->eps = mdp[4];
     md->d_oh = mdp[5]; md->d_hh = mdp[6]; md->wall_k = mdp[7]; md->wall_w = mdp[8];
-    md->method = (int)mdp[9]; md->alpha = mdp[10];
+    md->method = (int)mdp[9]; md->alpha = mdp[10]; md->mts = (int)mdp[11];
     md->l = l; md->n = n; md->n_mol = n_mol;
     md->q = q; md->m = m; md->lj = lj; md->box = box;
 }
 
-static int model_forces(const orc_model *md, const double *x, double *U, double *F, double *pot)
+/* The water completion's Lennard-Jones and wall terms, added to *dU_out and F. */
+static int add_lj_wall(const orc_model *md, const double *x, double *dU_out, double *F)
 {
-    double prm[3] = {md->a, md->h, md->ke};
     int64_t n = md->n;
-    double *phi = pot ? pot : malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    if (!phi) return ORC_ENOMEM;
-    int rc;
-    if (md->method == ORC_METHOD_MSM) {
-        rc = orc_msm(prm, md->l, n, x, md->q, md->box, U, F, phi, NULL);
-    } else {
-        /* the cutoff methods need no grid, but atoms must still lie in the open
-         * domain (the binning contract, the same for every method) */
-        int64_t *key = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-        if (!key) { if (!pot) free(phi); return ORC_ENOMEM; }
-        rc = orc_bin(n, x, md->box, md->h, NULL, key, NULL, NULL);
-        free(key);
-        if (rc == ORC_OK) rc = orc_cutoff(md->method, md->a, md->alpha, md->ke, n, md->n_mol, x, md->q, U, F, phi);
-    }
-    if (rc) { if (!pot) free(phi); return rc; }
-    double dU = 0;
-    /* intramolecular exclusions (MSM only: the cutoff methods skipped these pairs):
-     * subtract k_e q_i q_j / r for (O,H1), (O,H2), (H1,H2) */
-    for (int64_t mo = 0; md->method == ORC_METHOD_MSM && mo < md->n_mol; mo++) {
-        static const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
-        for (int c = 0; c < 3; c++) {
-            int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
-            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
-            double r = sqrt(dx * dx + dy * dy + dz * dz);
-            double e = md->ke * md->q[i] * md->q[j] / r;
-            dU -= e;
-            phi[i] -= md->ke * md->q[j] / r;
-            phi[j] -= md->ke * md->q[i] / r;
-            double s = e / (r * r);
-            F[3 * i] -= s * dx; F[3 * i + 1] -= s * dy; F[3 * i + 2] -= s * dz;
-            F[3 * j] += s * dx; F[3 * j + 1] += s * dy; F[3 * j + 2] += s * dz;
-        }
-    }
+    double dU = *dU_out;            /* continues the caller's sum in its order */
     /* Lennard-Jones between flagged sites within a (all pairs of flagged sites) */
     if (md->lj && md->eps != 0.0) {
         double s2 = md->sigma * md->sigma, a2 = md->a * md->a;
@@ -738,7 +711,7 @@ static int model_forces(const orc_model *md, const double *x, double *U, double 
         int64_t *idx = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
         double *fl = calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
         double *el = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
-        if (!idx || !fl || !el) { free(idx); free(fl); free(el); if (!pot) free(phi); return ORC_ENOMEM; }
+        if (!idx || !fl || !el) { free(idx); free(fl); free(el); return ORC_ENOMEM; }
         for (int64_t i = 0; i < n; i++) if (md->lj[i]) idx[nl++] = i;
 #pragma omp parallel for schedule(dynamic, 16)
         for (int64_t u = 0; u < nl; u++) {
@@ -782,9 +755,123 @@ static int model_forces(const orc_model *md, const double *x, double *U, double 
                 }
             }
     }
+    *dU_out = dU;
+    return ORC_OK;
+}
+
+static int model_forces(const orc_model *md, const double *x, double *U, double *F, double *pot)
+{
+    double prm[3] = {md->a, md->h, md->ke};
+    int64_t n = md->n;
+    double *phi = pot ? pot : malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!phi) return ORC_ENOMEM;
+    int rc;
+    if (md->method == ORC_METHOD_MSM) {
+        rc = orc_msm(prm, md->l, n, x, md->q, md->box, U, F, phi, NULL);
+    } else {
+        /* the cutoff methods need no grid, but atoms must still lie in the open
+         * domain (the binning contract, the same for every method) */
+        int64_t *key = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        if (!key) { if (!pot) free(phi); return ORC_ENOMEM; }
+        rc = orc_bin(n, x, md->box, md->h, NULL, key, NULL, NULL);
+        free(key);
+        if (rc == ORC_OK) rc = orc_cutoff(md->method, md->a, md->alpha, md->ke, n, md->n_mol, x, md->q, U, F, phi);
+    }
+    if (rc) { if (!pot) free(phi); return rc; }
+    double dU = 0;
+    /* intramolecular exclusions (MSM only: the cutoff methods skipped these pairs):
+     * subtract k_e q_i q_j / r for (O,H1), (O,H2), (H1,H2) */
+    for (int64_t mo = 0; md->method == ORC_METHOD_MSM && mo < md->n_mol; mo++) {
+        static const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+        for (int c = 0; c < 3; c++) {
+            int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
+            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double e = md->ke * md->q[i] * md->q[j] / r;
+            dU -= e;
+            phi[i] -= md->ke * md->q[j] / r;
+            phi[j] -= md->ke * md->q[i] / r;
+            double s = e / (r * r);
+            F[3 * i] -= s * dx; F[3 * i + 1] -= s * dy; F[3 * i + 2] -= s * dz;
+            F[3 * j] += s * dx; F[3 * j + 1] += s * dy; F[3 * j + 2] += s * dz;
+        }
+    }
+    rc = add_lj_wall(md, x, &dU, F);
+    if (rc) { if (!pot) free(phi); return rc; }
     *U += dU;
     if (!pot) free(phi);
     return ORC_OK;
+}
+
+/* The forces of the model split for multiple time stepping.  Sec. 3 notes that
+ * the MSM uses a multiple-time-step integrator well: its short-range part g*
+ * changes on the time scale of the atoms' collisions, its grid part is smooth
+ * and changes slowly.  Reading: the fast part Ff is the short-range g* sum over
+ * the non-excluded pairs, the Lennard-Jones term and the wall; the slow part Fs
+ * is the grid part -k_e q_i grad u^long(r_i) minus the smooth part
+ * k_e q_i q_j gamma(r/a)/a of each excluded pair (which the grids carry and the
+ * exclusion removes).  U is the whole energy, as model_forces gives it, and Us
+ * its slow part 1/2 sum_i q_i k_e (u_i^long - q_i gamma(0)/a) minus the
+ * excluded pairs' smooth energies.  MSM method only. */
+static int model_forces_split(const orc_model *md, const double *x, double *U, double *Us, double *Ff, double *Fs)
+{
+    int64_t n = md->n;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double prm[3] = {md->a, md->h, md->ke};
+    double ke = md->ke, a = md->a;
+    double *ps = malloc(sizeof(double) * nn), *fs = malloc(sizeof(double) * 3 * nn);
+    double *pl = malloc(sizeof(double) * nn), *gl = malloc(sizeof(double) * 3 * nn);
+    if (!ps || !fs || !pl || !gl) { free(ps); free(fs); free(pl); free(gl); return ORC_ENOMEM; }
+    orc_stage_out st = {ps, fs, pl, gl, NULL, NULL, NULL};
+    int rc = orc_msm(prm, md->l, n, x, md->q, md->box, NULL, NULL, NULL, &st);
+    if (rc) { free(ps); free(fs); free(pl); free(gl); return rc; }
+    double self = orc_gamma(0.0) / a, u = 0, us = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double qi = md->q[i];
+        u += qi * (ke * (ps[i] + pl[i] - qi * self));
+        us += qi * (ke * (pl[i] - qi * self));
+        for (int d = 0; d < 3; d++) {
+            Ff[3 * i + d] = ke * fs[3 * i + d];
+            Fs[3 * i + d] = -ke * qi * gl[3 * i + d];
+        }
+    }
+    double dU = 0.5 * u, dUs = 0.5 * us;
+    /* exclusions: 1/r = g*(r) + gamma(r/a)/a; the g* part leaves the fast
+     * forces, the smooth part the slow ones, the whole 1/r the energy */
+    for (int64_t mo = 0; mo < md->n_mol; mo++) {
+        static const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+        for (int c = 0; c < 3; c++) {
+            int64_t i = 3 * mo + pi[c], j = 3 * mo + pj[c];
+            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double qq = ke * md->q[i] * md->q[j];
+            dU -= qq / r;
+            dUs -= qq * orc_gamma(r / a) / a;
+            /* removing energy e(r) adds e'(r) (r_i - r_j)/r to F_i */
+            double sf = qq * orc_dgstar(r, a) / r, ss = qq * orc_dgamma(r / a) / (a * a) / r;
+            Ff[3 * i] += sf * dx; Ff[3 * i + 1] += sf * dy; Ff[3 * i + 2] += sf * dz;
+            Ff[3 * j] -= sf * dx; Ff[3 * j + 1] -= sf * dy; Ff[3 * j + 2] -= sf * dz;
+            Fs[3 * i] += ss * dx; Fs[3 * i + 1] += ss * dy; Fs[3 * i + 2] += ss * dz;
+            Fs[3 * j] -= ss * dx; Fs[3 * j + 1] -= ss * dy; Fs[3 * j + 2] -= ss * dz;
+        }
+    }
+    free(ps); free(fs); free(pl); free(gl);
+    rc = add_lj_wall(md, x, &dU, Ff);
+    if (rc) return rc;
+    *U = dU;
+    *Us = dUs;
+    return ORC_OK;
+}
+
+/* The split forces of the model (see model_forces_split): U, Us, Ff, Fs. */
+int orc_model_forces_split(const double *mdp, int l, int64_t n, int64_t n_mol, const double *x, const double *q,
+                           const unsigned char *lj, const double *box, double *energy, double *energy_slow,
+                           double *f_fast, double *f_slow)
+{
+    orc_model md;
+    model_from(&md, mdp, l, n, n_mol, q, NULL, lj, box);
+    if (md.method != ORC_METHOD_MSM) return ORC_EINVAL;
+    return model_forces_split(&md, x, energy, energy_slow, f_fast, f_slow);
 }
 
 /* Energy and forces of the water model (MSM + exclusions + LJ). */
@@ -870,8 +957,11 @@ static double kinetic(int64_t n, const double *m, const double *v)
     return K;
 }
 
+static int md_steps_mts(const orc_model *md, double *x, double *v, double dt, int n_steps, double *uk);
+
 static int md_steps(const orc_model *md, double *x, double *v, double dt, int n_steps, double *uk)
 {
+    if (md->mts > 1) return md_steps_mts(md, x, v, dt, n_steps, uk);
     int64_t n = md->n;
     double *F = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *xo = malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -902,6 +992,61 @@ out:
     return rc;
 }
 
+/* Multiple time stepping (Sec. 3: the MSM suits a multiple-time-step
+ * integrator), as the impulse method (Grubmueller et al. 1991; Tuckerman,
+ * Berne & Martyna 1992, "r-RESPA") restated with SHAKE/RATTLE: an outer step
+ * of k = mts fast steps of dt.  The slow force Fs acts as two impulses of
+ * k dt/2, at the start and the end of the outer step, each folded into the
+ * adjacent half kick of the fast velocity Verlet step, which then uses
+ * Ff + k Fs (a RATTLE half step with that force); the inner half kicks use Ff
+ * alone.  Fs is evaluated at the end of each outer step only.  n_steps must
+ * be a multiple of k.  uk records (U, K) after every step, U being the fast
+ * energy at the current positions plus the slow energy of the last slow
+ * evaluation (at the ends of outer steps: the whole energy). */
+static int md_steps_mts(const orc_model *md, double *x, double *v, double dt, int n_steps, double *uk)
+{
+    int64_t n = md->n;
+    const int k = md->mts;
+    if (md->method != ORC_METHOD_MSM || n_steps % k != 0) return ORC_EINVAL;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *Ff = malloc(sizeof(double) * 3 * nn), *Fs = malloc(sizeof(double) * 3 * nn);
+    double *Gs = malloc(sizeof(double) * 3 * nn), *xo = malloc(sizeof(double) * 3 * nn);
+    if (!Ff || !Fs || !Gs || !xo) { free(Ff); free(Fs); free(Gs); free(xo); return ORC_ENOMEM; }
+    double U, Us, Ut, Ust;
+    int rc = model_forces_split(md, x, &U, &Us, Ff, Fs);
+    if (rc) goto out;
+    if (uk) { uk[0] = U; uk[1] = kinetic(n, md->m, v); }
+    for (int s = 0; s < n_steps; s++) {
+        const int first = s % k == 0, last = s % k == k - 1;
+        memcpy(xo, x, sizeof(double) * 3 * (size_t)n);
+        for (int64_t i = 0; i < n; i++)                       /* half kick (+ slow impulse), drift */
+            for (int d = 0; d < 3; d++) {
+                double f = first ? Ff[3 * i + d] + (double)k * Fs[3 * i + d] : Ff[3 * i + d];
+                v[3 * i + d] += 0.5 * dt * f / md->m[i];
+                x[3 * i + d] += dt * v[3 * i + d];
+            }
+        rc = shake(md, xo, x, v, dt);
+        if (rc) goto out;
+        /* the oracle evaluates both parts every step and keeps the slow one only at
+         * the ends of outer steps */
+        rc = model_forces_split(md, x, &Ut, &Ust, Ff, Gs);
+        if (rc) goto out;
+        if (last) { memcpy(Fs, Gs, sizeof(double) * 3 * (size_t)n); U = Ut; Us = Ust; }
+        else U = (Ut - Ust) + Us;
+        for (int64_t i = 0; i < n; i++)                        /* second half kick (+ slow impulse) */
+            for (int d = 0; d < 3; d++) {
+                double f = last ? Ff[3 * i + d] + (double)k * Fs[3 * i + d] : Ff[3 * i + d];
+                v[3 * i + d] += 0.5 * dt * f / md->m[i];
+            }
+        rc = rattle_v(md, x, v);
+        if (rc) goto out;
+        if (uk) { uk[2 * (s + 1)] = U; uk[2 * (s + 1) + 1] = kinetic(n, md->m, v); }
+    }
+out:
+    free(Ff); free(Fs); free(Gs); free(xo);
+    return rc;
+}
+
 /* Velocity Verlet (Sec. 2: forces F = -dU/dr, then move the atoms) with
  * SHAKE/RATTLE for the rigid triples.  x, v are updated in place.  uk, if
  * non-NULL, receives (U, K) before the first step and after each step. */
@@ -923,7 +1068,7 @@ int orc_md_run(const double *mdp, int l, int64_t n, int64_t n_mol, double *x, do
  *              bitwise the bracket is exactly 0 and slice n+1 equals F);
  *   stop when max_{n,i,d} |x^{k+1} - x^k| <= tol, or after max_iter iterations.
  * slices_x/v: (n_slices+1) * n * 3, slot 0 holds state0 on entry.
- * gp/fp: {mdp (11 values), dt, steps, levels}. */
+ * gp/fp: {mdp (12 values), dt, steps, levels}. */
 /* Parareal's correction F + (G_new - G_old) adds positions of rigid molecules
  * taken from different trajectories, so the corrected molecules need not have
  * the rigid bond lengths; a grossly distorted one would start the next coarse
@@ -1002,10 +1147,10 @@ int orc_parareal(const double *gp, const double *fp, int64_t n, int64_t n_mol,
                  int *iters_done, double *last_dx)
 {
     orc_model G, F;
-    model_from(&G, gp, (int)gp[13], n, n_mol, q, m, lj, box);
-    model_from(&F, fp, (int)fp[13], n, n_mol, q, m, lj, box);
-    double dtG = gp[11], dtF = fp[11];
-    int sG = (int)gp[12], sF = (int)fp[12];
+    model_from(&G, gp, (int)gp[14], n, n_mol, q, m, lj, box);
+    model_from(&F, fp, (int)fp[14], n, n_mol, q, m, lj, box);
+    double dtG = gp[12], dtF = fp[12];
+    int sG = (int)gp[13], sF = (int)fp[13];
     size_t sz = 3 * (size_t)n;
     int rc = ORC_OK;
     double *gold_x = malloc(sizeof(double) * sz * (size_t)n_slices), *gold_v = malloc(sizeof(double) * sz * (size_t)n_slices);
@@ -1081,10 +1226,10 @@ int orc_parareal_window(const double *gp, const double *fp, int64_t n, int64_t n
 {
     if (window < 1 || n_slices < 1) return ORC_EINVAL;
     orc_model G, F;
-    model_from(&G, gp, (int)gp[13], n, n_mol, q, m, lj, box);
-    model_from(&F, fp, (int)fp[13], n, n_mol, q, m, lj, box);
-    double dtG = gp[11], dtF = fp[11];
-    int sG = (int)gp[12], sF = (int)fp[12];
+    model_from(&G, gp, (int)gp[14], n, n_mol, q, m, lj, box);
+    model_from(&F, fp, (int)fp[14], n, n_mol, q, m, lj, box);
+    double dtG = gp[12], dtF = fp[12];
+    int sG = (int)gp[13], sF = (int)fp[13];
     const size_t sz = 3 * (size_t)n, ns = (size_t)n_slices;
     int rc = ORC_OK;
     /* per slice n: its coarse propagation of the current iterate (gold), its fine one (f) */
