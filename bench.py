@@ -67,6 +67,8 @@ def args_parse():
                         "velocities rescaled to 300 K after each (0: start from the lattice)")
     p.add_argument("--nve-steps", type=int, default=200, help="NVE leg: FP32 and FP64 energy drift side by side")
     p.add_argument("--list-skin", type=float, default=0.0, help="Verlet-list skin (nm) of the timed FP32 run")
+    p.add_argument("--mts-steps", type=int, default=200,
+                   help="timed steps of the multiple-time-stepping leg (grid part every 2 and 4 steps; 0: skip)")
     return p.parse_args()
 
 
@@ -327,6 +329,36 @@ def run_ours(a):
                          "temperature_k": float(2 * ukn[:, 1].mean() / (dof * KB))}
             del dn
 
+    # ---- multiple time stepping (grid part every k steps): step time and energy at outer steps
+    mts = None
+    if a.mts_steps > 0:
+        mts = {"note": "impulse method: short range, LJ and wall every 2 fs step, the grid part every k steps "
+                       "(Sec. 3); energy drift over the NVE leg's steps from the same relaxed state, total energy "
+                       "at the ends of outer steps"}
+        for k in (2, 4):
+            mk = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", mts=k, **WALL)
+            dk = dev_system(torch, s, dev)
+            mk.md_run(dk, DT, 2 * k, record=False)
+            torch.cuda.synchronize()
+            nst = (a.mts_steps // k) * k
+            e0.record(stream)
+            mk.md_run(dk, DT, nst, record=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tk = e0.elapsed_time(e1) / nst
+            entry = {"ms_per_step": tk, "value": n / (tk / 1e3), "unit": UNIT, "speedup_vs_every_step": t_ms / a.steps / tk}
+            if a.nve_steps > 0:
+                dn = dev_system(torch, s, dev)
+                ukn = mk.md_run(dn, DT, (a.nve_steps // k) * k, record=True).cpu().numpy()
+                et = ukn.sum(1)[::k]
+                entry.update({"energy_drift_kj_mol": float(et[-1] - et[0]),
+                              "max_abs_dev_kj_mol": float(np.abs(et - et[0]).max()),
+                              "temperature_k": float(2 * ukn[:, 1].mean() / (dof * KB))})
+                del dn
+            mts[f"k{k}"] = entry
+            mk.close()
+            del dk
+
     # ---- forces and energy at the start: FP32 and FP64 GPU paths against the FP64 oracle
     d0 = dev_system(torch, s, dev)
     u32, f32, _ = m32.system_forces(d0)
@@ -437,6 +469,7 @@ def run_ours(a):
                              "kinetic_kj_mol": float(uk[-1, 1]),
                              "temperature_k": float(2 * uk[:, 1].mean() / (dof * KB))},
         "nve": nve,
+        "mts": mts,
         "relax_s": t_relax,
         "stage_ms_per_launch": stage_ms,
         "stage_share_of_step": step_share,
@@ -517,10 +550,12 @@ def relaxed_state(api, inputs, s, steps=40, chunk=50, temp=300.0, levels=3, torc
 
 # coarse propagators of the parareal leg: the configured MSM G (shorter cutoff, coarser
 # grid, longer step: Sec. 5's "shorter cutoff" and "coarse grid") and the two cutoff
-# methods Sec. 5 keeps, the simple cutoff (its chosen G) and Wolf summation
+# methods Sec. 5 keeps, the simple cutoff (its chosen G; also at the fine propagator's
+# own cutoff, as in the paper's 12 A example) and Wolf summation
 COARSE = {
     "msm_a0.8_h0.5": dict(a=0.8, h=0.5, levels=2, method="msm"),
     "cutoff_a0.8": dict(a=0.8, h=0.5, levels=1, method="cutoff"),
+    "cutoff_a1.2": dict(a=1.2, h=0.5, levels=1, method="cutoff"),
     "wolf_a0.8": dict(a=0.8, h=0.5, levels=1, method="wolf", wolf_alpha=2.5),
 }
 

@@ -113,6 +113,19 @@ extern "C" {
  *              atom has moved more than list_skin/2 (0 = cell search every
  *              step; the default).  Exact either way: pairs are still tested against a.
  *   method     MSM_METHOD_* (default MSM_METHOD_MSM)
+ *   mts_steps  md_run, md_run_batched and the parareal propagators: multiple
+ *              time stepping (Sec. 3 notes that the MSM suits a multiple-
+ *              time-step integrator), the impulse method with SHAKE/RATTLE.
+ *              The grid part (k_e q_i times the interpolated long-range
+ *              gradient, minus the excluded pairs' smooth part) is the slow
+ *              force, evaluated once per outer step of mts_steps steps and
+ *              applied as two impulses of mts_steps*dt/2 folded into the
+ *              outer step's first and last half kicks; the short-range pair
+ *              sum, Lennard-Jones and wall are the fast force, every step.
+ *              n_steps must be a multiple of mts_steps; the recorded U of a
+ *              step inside an outer step is its fast energy plus the last slow
+ *              energy (the whole energy at the ends of outer steps).  0 or 1:
+ *              plain velocity Verlet (default 0); > 1 needs MSM_METHOD_MSM.
  *   wolf_alpha damping of MSM_METHOD_WOLF (1/nm, >= 0)  */
 typedef struct msm_params {
     double  a;
@@ -132,7 +145,7 @@ typedef struct msm_params {
     double  wall_width;
     double  list_skin;
     int32_t method;
-    int32_t reserved1;
+    int32_t mts_steps;
     double  wolf_alpha;
 } msm_params;
 

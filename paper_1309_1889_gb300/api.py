@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("model", C.c_int32), ("flags", C.c_int32), ("lj_sigma", C.c_double),
                 ("lj_epsilon", C.c_double), ("d_oh", C.c_double), ("d_hh", C.c_double),
                 ("wall_k", C.c_double), ("wall_width", C.c_double), ("list_skin", C.c_double),
-                ("method", C.c_int32), ("reserved1", C.c_int32), ("wolf_alpha", C.c_double)]
+                ("method", C.c_int32), ("mts_steps", C.c_int32), ("wolf_alpha", C.c_double)]
 
 
 class SystemC(C.Structure):
@@ -172,7 +172,8 @@ def _box(box):
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
                 lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
                 list_skin=0.0, graphs=True, autotune=True, scalar_pairs=False, method="msm",
-                wolf_alpha=0.0) -> Params:
+                wolf_alpha=0.0, mts=0) -> Params:
+    """mts: multiple time stepping of md_run (the grid part every `mts` steps; 0 or 1: off)."""
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -188,6 +189,7 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
                | (FLAG_SCALAR_PAIRS if scalar_pairs else 0))
     p.method = METHODS[method] if isinstance(method, str) else int(method)
     p.wolf_alpha = float(wolf_alpha)
+    p.mts_steps = int(mts)
     return p
 
 
@@ -446,7 +448,7 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
                            wall_k=P.get("wall_k", 0.0), wall_width=P.get("wall_width", 0.0),
                            list_skin=P.get("list_skin", 0.0), graphs=P.get("graphs", True),
                            autotune=P.get("autotune", True), method=P.get("method", "msm"),
-                           wolf_alpha=P.get("wolf_alpha", 0.0))
+                           wolf_alpha=P.get("wolf_alpha", 0.0), mts=P.get("mts", 0))
     pg, pf = params(G), params(F)
     s, keep = _system_struct(sys, need_v=True)
     n = int(s.n)

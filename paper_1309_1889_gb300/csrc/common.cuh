@@ -85,8 +85,10 @@ struct CellGeom {
 
 struct LevelGeom {
     int lo[3];          // index of the first point per axis
-    int n[3];           // points per axis
+    int n[3];           // points per axis (x: padded to a multiple of 4, see nx_log)
     int off;            // offset of this level in the concatenated grid buffer
+    int nx_log;         // points along x of the method's grid; the n[0] - nx_log points
+                        // after them carry zero charge (rows start on 16-byte boundaries)
 };
 
 struct GridGeom {

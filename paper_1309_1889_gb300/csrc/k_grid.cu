@@ -6,21 +6,26 @@
 //                  nu - 2mu in {-3,-1,0,1,3} with weights {-1,9,16,9,-1}/16
 //   k_stencil      u^{k,cut}_mu = sum_n 2^{-k} W[n] q^k_{mu+n}, W[n] = g^0(|n| h)
 //                  for |n| h < 2a (g^k(2^k r) = 2^{-k} g^0(r)): every level
-//                  0..l-2 in one launch; shared-memory tile with a halo of
-//                  rad points, 4 outputs per thread along x held in registers,
+//                  0..l-2 in one launch; the planes of a tile and its halo of
+//                  rad points come into shared memory by TMA (mbarrier-paced
+//                  double buffer), 8 x 2 outputs per thread held in registers,
 //                  rows of the tap sphere unrolled per half-width
 //   k_top          u^{l-1}_mu = sum_nu g^{l-1}(|r_mu - r_nu|) q_nu in FP64 over
 //                  a precomputed Toeplitz table (one warp per output point)
 //   k_prolong      u^k_mu = u^{k,cut}_mu + sum_nu Phi(mu/2 - nu)^{x3} u^{k+1}_nu
 //   k_interp       phi_i = k_e (u_i^short + sum_mu phi^0_mu(r_i) u^0_mu - q_i gamma(0)/a),
 //                  F_i = k_e (F_i^short - q_i sum_mu grad phi^0_mu(r_i) u^0_mu) [+ LJ],
-//                  scattered back to the caller's atom order
+//                  scattered back to the caller's atom order (for multiple time
+//                  stepping the two terms of F_i as fast and slow forces)
 //
 // Every kernel serves a batch of systems (one launch per stage for all of
 // them): blockIdx.y picks the system for the per-point and per-atom kernels,
 // and the persistent lattice-cutoff kernel takes tiles of every (system,
 // level) pair from one counter.
 #include <algorithm>
+#include <cstring>
+
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 
 #include "kernels.cuh"
 
@@ -202,20 +207,26 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
 // ST_RX outputs along x times ST_RZ along z in registers.  The ST_NT threads of
 // a CTA cover TGX = min(ceil(n_x / ST_RX), ST_MAXGX) groups along x times
 // TYR = ST_NT / TGX rows along y, so a tile spans whole grid rows of short
-// levels (the 98-point level-0 rows of a 23.5 nm box waste 6 % of the
+// levels (the 100-point level-0 rows of a 23.5 nm box waste 6 % of the
 // threads, fixed 32-point tiles 23 %).  The tile's input planes z' = z0-rad ..
-// z0+ST_RZ-1+rad pass through two shared-memory buffers filled by cp.async
-// (zero outside the grid), the next plane's copy in flight while the current
-// one is used.  The plane rows y + dy and y - dy (the weights depend on |dy|)
-// are added once in registers and applied to the ST_RZ output planes they
-// reach (dz = z' - z), walking the tap row (|dy|, |dz|) of the sphere with
-// compile-time offsets: half the multiply-adds of walking every row.  The weights
-// W[n] = g^0(|n| h) depend on |n| only, so one octant of the table sits in
-// shared memory; the level factor 2^{-k} is applied at the end.  CTAs take
-// tiles from a counter.  Each output sums its taps in a fixed order (planes,
-// row pairs, then x offsets), whatever the tile shape.
+// z0+ST_RZ-1+rad come into two shared-memory buffers by TMA: one thread
+// starts a cp.async.bulk.tensor copy of the plane's box (the tile's rows with
+// their halos; the hardware fills points outside the grid with zeros) on the
+// buffer's mbarrier, the next plane's copy in flight while the current one is
+// used.  The box starts on a 16-byte boundary in x (the halo is rounded up to
+// whole groups of 4 values) and its width is an odd number of 16-byte granules
+// (consecutive rows fall in different banks).  The plane rows y + dy and y - dy
+// (the weights depend on |dy|) are added once in registers and applied to the
+// ST_RZ output planes they reach (dz = z' - z), walking the tap row (|dy|, |dz|)
+// of the sphere with compile-time offsets: half the multiply-adds of walking
+// every row.  The weights W[n] = g^0(|n| h) depend on |n| only, so one octant of
+// the table sits in shared memory; the level factor 2^{-k} is applied at the
+// end.  CTAs take tiles from a counter.  Each output sums its taps in a fixed
+// order (planes, row pairs, then x offsets), whatever the tile shape.
 constexpr int ST_RX = 8, ST_RZ = 2, ST_NT = 128, ST_MAXGX = 16;
 constexpr int ST_MAXRAD = 12;
+constexpr int ST_MAXMAPS = 24;      // descriptors per launch (kernel parameter: 24 x 128 bytes)
+constexpr long ST_WAIT_POLLS = 1L << 22;
 
 struct StTile { int tgx, tyr, ntx, nty, ntz; };
 __host__ __device__ inline StTile st_tile(const LevelGeom &L)
@@ -230,20 +241,32 @@ __host__ __device__ inline StTile st_tile(const LevelGeom &L)
     return t;
 }
 
-// Plane rows and weight rows are padded to multiples of 4 values so that rows
-// start on 16-byte boundaries and are read four values per load.
+// Rows of values are handled in groups of 4 (16 bytes of FP32).
 __host__ __device__ constexpr int st_up4(int v) { return (v + 3) & ~3; }
 __host__ __device__ constexpr int st_r1p(int rad) { return st_up4(rad + 1); }
-__host__ __device__ inline int st_px(int tgx, int rad) { return st_up4(tgx * ST_RX + 2 * rad); }
-__host__ __device__ inline int st_py(int tgx, int rad) { return ST_NT / tgx + 2 * rad; }
+// x halo of a tile, rounded up to whole groups: the box starts on a 16-byte boundary
+__host__ __device__ constexpr int st_radp(int rad) { return st_up4(rad); }
+// box width: the tile's x range and both halos, an odd number of groups of 4 values
+__host__ __device__ inline int st_bx(int tgx, int rad)
+{
+    int g = (tgx * ST_RX + 2 * st_radp(rad)) / 4;
+    if (!(g & 1)) g++;
+    return 4 * g;
+}
+// box height: the tile's rows and both halos
+__host__ __device__ inline int st_by(int tgx, int rad) { return ST_NT / tgx + 2 * rad; }
 
-// Shared memory of one CTA: the weight octant W[|dz|][|dy|][|dx|] ((rad+1)^2
-// rows of st_r1p values), two plane buffers of `plane` values, and the
-// half-widths of the tap rows by (|dz|, |dy|).
+// Shared memory of one CTA: 128 bytes of alignment slack, the weight octant
+// W[|dz|][|dy|][|dx|] ((rad+1)^2 rows of st_r1p values) rounded up to 128
+// bytes, two plane buffers of `plane` values (a multiple of 32 values: both
+// buffers start on 128-byte boundaries), and the half-widths of the tap rows by
+// (|dz|, |dy|).
+__host__ __device__ inline size_t st_up128(size_t b) { return (b + 127) & ~(size_t)127; }
 template <typename T> size_t stencil_smem_bytes(int rad, int plane)
 {
     const size_t r1 = (size_t)rad + 1;
-    return sizeof(T) * (r1 * r1 * (size_t)st_r1p(rad) + 2 * (size_t)plane) + sizeof(int) * (r1 * r1 + 4);
+    return 128 + st_up128(sizeof(T) * r1 * r1 * (size_t)st_r1p(rad)) + sizeof(T) * 2 * (size_t)plane +
+           sizeof(int) * (r1 * r1 + 4);
 }
 template size_t stencil_smem_bytes<float>(int, int);
 template size_t stencil_smem_bytes<double>(int, int);
@@ -251,16 +274,17 @@ template size_t stencil_smem_bytes<double>(int, int);
 int stencil_plane_values(const LevelGeom &L, int rad)
 {
     const StTile t = st_tile(L);
-    return st_px(t.tgx, rad) * st_py(t.tgx, rad);
+    return (st_bx(t.tgx, rad) * st_by(t.tgx, rad) + 31) & ~31;
 }
 
-// Values of one plane row in registers: ST_RX + 2 RAD used, rounded up to 4.
-template <int RAD> struct StRow { static constexpr int N = st_up4(ST_RX + 2 * RAD); };
+// Values of one plane row in registers: ST_RX + 2 st_radp(RAD).
+template <int RAD> struct StRow { static constexpr int N = st_up4(ST_RX + 2 * st_radp(RAD)); };
 
+// acc[r] += sum_{|d| <= W} w[|d|] v[r + d + st_radp(RAD)]
 template <int W, int RAD, typename T>
 __device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T *__restrict__ wr, T (&acc)[ST_RX])
 {
-    constexpr int NW = st_up4(W + 1);
+    constexpr int NW = st_up4(W + 1), RP = st_radp(RAD);
     T w[NW];                                                   // octant row |dx| = 0..W (16-byte aligned)
     if (sizeof(T) == sizeof(float)) {
 #pragma unroll
@@ -275,7 +299,7 @@ __device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T
 #pragma unroll
     for (int d = -W; d <= W; d++) {
 #pragma unroll
-        for (int r = 0; r < ST_RX; r++) acc[r] = fma(w[d < 0 ? -d : d], v[r + d + RAD], acc[r]);
+        for (int r = 0; r < ST_RX; r++) acc[r] = fma(w[d < 0 ? -d : d], v[r + d + RP], acc[r]);
     }
 }
 
@@ -291,34 +315,60 @@ __device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<R
     }
 }
 
-// Asynchronous copy of one value of type T from global to shared memory; with
-// ok = false nothing is read and the destination is zero-filled.
-template <typename T>
-__device__ __forceinline__ void st_copy(T *dst, const T *src, bool ok)
+// The descriptors of one launch: entries e0 .. e0+ne-1 of the batch.
+struct StMaps {
+    CUtensorMap map[ST_MAXMAPS];
+    int e0, ne;
+};
+
+__device__ __forceinline__ uint32_t st_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Start the TMA copy of the box at (x, y, z) into dst; the barrier expects its bytes.
+__device__ __forceinline__ void st_tma_plane(const CUtensorMap *map, void *dst, uint64_t *bar, int x, int y, int z,
+                                             uint32_t bytes)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = ok ? (int)sizeof(T) : 0;
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    const uint32_t b = st_smem(bar), d = st_smem(dst);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+                 ::"r"(d), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(b)
+                 : "memory");
 }
-__device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void st_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void st_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Wait for the barrier phase with the given parity: at most ST_WAIT_POLLS polls.
+__device__ __forceinline__ bool st_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t b = st_smem(bar);
+    for (long i = 0; i < ST_WAIT_POLLS; i++) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 
 template <typename T, int RAD>
-__global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *__restrict__ counter)
+__global__ void __launch_bounds__(ST_NT) k_stencil(const __grid_constant__ StencilArgs<T> A,
+                                                   const __grid_constant__ StMaps M, int *__restrict__ counter)
 {
-    constexpr int WD = 2 * RAD + 1, R1 = RAD + 1, R1P = st_r1p(RAD);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WD = 2 * RAD + 1, R1 = RAD + 1, R1P = st_r1p(RAD), RP = st_radp(RAD);
+    extern __shared__ unsigned char smem_raw[];
     const int PLANE = A.sg.plane;
-    T *wt = reinterpret_cast<T *>(smem_raw);                 // R1 x R1 rows of R1P weights W[|dz|][|dy|][|dx|]
-    T *buf0 = wt + R1 * R1 * R1P;                            // two plane buffers
+    unsigned char *base = smem_raw + ((128 - (st_smem(smem_raw) & 127)) & 127);
+    T *wt = reinterpret_cast<T *>(base);                     // R1 x R1 rows of R1P weights W[|dz|][|dy|][|dx|]
+    T *buf0 = reinterpret_cast<T *>(base + st_up128(sizeof(T) * R1 * R1 * R1P));   // two plane buffers
     int *hw = reinterpret_cast<int *>(buf0 + 2 * PLANE);     // R1^2 half widths by (|dz|, |dy|) (-1: empty)
-    __shared__ int s_tile, s_ent;
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_tile, s_ent, s_err;
     if (failed(A.status)) return;
     const int t = threadIdx.x;
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(st_smem(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(st_smem(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_err = 0;
+    }
     for (int e = t; e < R1 * R1 * R1P; e += ST_NT) {
         const int ax = e % R1P, ay = (e / R1P) % R1, az = e / (R1P * R1);
         wt[e] = ax < R1 ? A.w[((az + RAD) * WD + (ay + RAD)) * WD + (ax + RAD)] : T(0);
@@ -329,13 +379,15 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *
         const int4 r = A.rows[e];
         if (r.x >= 0 && r.y >= 0) hw[r.y * R1 + r.x] = r.z;
     }
-    const int total = A.total_tiles, nent = A.bt.B * A.nlev;
+    uint32_t phase[2] = {0u, 0u};                            // the barriers' next phases (uniform)
+    const int e_end = M.e0 + M.ne;
+    const int first = A.blk_off[M.e0], total = A.blk_off[e_end];
     for (;;) {
         __syncthreads();
         if (t == 0) {
-            const int tile = atomicAdd(counter, 1);
+            const int tile = first + atomicAdd(counter, 1);
             // owner (system, level) of the tile: last entry whose first tile is <= tile
-            int lo_e = 0, hi_e = nent - 1;
+            int lo_e = M.e0, hi_e = e_end - 1;
             while (lo_e < hi_e) {
                 const int mid = (lo_e + hi_e + 1) >> 1;
                 if (A.blk_off[mid] <= tile) lo_e = mid; else hi_e = mid - 1;
@@ -350,40 +402,42 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *
         const SysDesc &D = A.bt.sd[ent / A.nlev];
         const LevelGeom &L = D.gg.L[lev];
         const StTile tg = st_tile(L);
-        const int PX = st_px(tg.tgx, RAD), PY = tg.tyr + 2 * RAD;
+        const int PX = st_bx(tg.tgx, RAD);
+        const uint32_t bytes = (uint32_t)(sizeof(T) * PX * st_by(tg.tgx, RAD));
+        const CUtensorMap *map = &M.map[ent - M.e0];
         const int b = tile - A.blk_off[ent];
         const int tx = b % tg.ntx, ty = (b / tg.ntx) % tg.nty, tz = b / (tg.ntx * tg.nty);
         const int x0 = tx * tg.tgx * ST_RX, y0 = ty * tg.tyr, z0 = tz * ST_RZ;
-        // consecutive lanes take consecutive rows: the plane pitch is an odd number of
+        // consecutive lanes take consecutive rows: the box width is an odd number of
         // 16-byte granules, so their row loads fall in different banks
         const int yr = t % tg.tyr, xg = t / tg.tyr;
         const bool active = xg < tg.tgx;
-        const T *__restrict__ q = A.q + D.grid_off + L.off;
-        const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+        const int ny = L.n[1], nz = L.n[2];
         // planes that exist: z' in [zb, ze)
         const int zb = max(z0 - RAD, 0), ze = min(z0 + ST_RZ + RAD, nz);
-        auto fill = [&](int zp, T *dst) {
-            int px = t % PX, py = t / PX;
-            for (int e = t; e < PX * PY; e += ST_NT) {
-                const int gx = x0 + px - RAD, gy = y0 + py - RAD;
-                const bool ok = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-                st_copy(dst + e, ok ? q + ((size_t)zp * ny + gy) * nx + gx : q, ok);
-                px += ST_NT;
-                while (px >= PX) { px -= PX; py++; }
-            }
-            st_commit();
-        };
         T acc[ST_RZ][ST_RX];
 #pragma unroll
         for (int s = 0; s < ST_RZ; s++)
 #pragma unroll
             for (int r = 0; r < ST_RX; r++) acc[s][r] = 0;
-        if (zb < ze) fill(zb, buf0);
+        if (t == 0 && zb < ze) st_tma_plane(map, buf0, &bars[0], x0 - RP, y0 - RAD, zb, bytes);
         for (int zp = zb; zp < ze; zp++) {
-            T *cur = buf0 + ((zp - zb) & 1) * PLANE;
-            if (zp + 1 < ze) { fill(zp + 1, buf0 + ((zp + 1 - zb) & 1) * PLANE); st_wait_prev(); }
-            else st_wait_all();
+            const int bi = (zp - zb) & 1;
+            T *cur = buf0 + bi * PLANE;
+            // the other buffer was last read in the previous plane, before its closing barrier
+            if (t == 0 && zp + 1 < ze)
+                st_tma_plane(map, buf0 + (bi ^ 1) * PLANE, &bars[bi ^ 1], x0 - RP, y0 - RAD, zp + 1, bytes);
+            if (!st_wait(&bars[bi], phase[bi])) s_err = 1;
             __syncthreads();
+            if (s_err) {
+                // a copy that did not arrive: report, give the copies in flight a bounded
+                // wait of their own, leave (every thread of the CTA takes this branch)
+                if (t == 0) set_status(const_cast<int *>(A.status), MSM_ETIMEOUT);
+                st_wait(&bars[bi], phase[bi]);
+                if (zp + 1 < ze) st_wait(&bars[bi ^ 1], phase[bi ^ 1]);
+                return;
+            }
+            phase[bi] ^= 1u;
             if (active) {
                 // W depends on |dy|: rows y + dy and y - dy are added once and share
                 // the tap row of (|dz|, |dy|) for both output planes
@@ -430,53 +484,101 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const StencilArgs<T> A, int *
             for (int s = 0; s < ST_RZ; s++) {
                 const int gz = z0 + s;
                 if (gz >= nz) continue;
-                T *out = A.ucut + D.grid_off + L.off + ((size_t)gz * ny + gy) * nx;
+                T *out = A.ucut + D.grid_off + L.off + ((size_t)gz * ny + gy) * L.n[0];
 #pragma unroll
                 for (int r = 0; r < ST_RX; r++) {
                     const int gx = x0 + xg * ST_RX + r;
-                    if (gx < nx) out[gx] = scale * acc[s][r];
+                    if (gx < L.n[0]) out[gx] = scale * acc[s][r];
                 }
             }
         }
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point lookup.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+template <typename T>
+int encode_stencil_maps(const SysDesc *sd, int B, int nlev, int rad, const T *q, CUtensorMap *maps)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail_msg(MSM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    for (int s = 0; s < B; s++)
+        for (int k = 0; k < nlev; k++) {
+            const SysDesc &D = sd[s];
+            const LevelGeom &L = D.gg.L[k];
+            const StTile tg = st_tile(L);
+            const T *base = q + D.grid_off + L.off;
+            if ((reinterpret_cast<uintptr_t>(base) & 15) || (L.n[0] * sizeof(T)) % 16)
+                return fail_msg(MSM_EINVAL, "lattice-cutoff grid rows are not 16-byte aligned");
+            const cuuint64_t dims[3] = {(cuuint64_t)L.n[0], (cuuint64_t)L.n[1], (cuuint64_t)L.n[2]};
+            const cuuint64_t strides[2] = {(cuuint64_t)L.n[0] * sizeof(T), (cuuint64_t)L.n[0] * L.n[1] * sizeof(T)};
+            const cuuint32_t box[3] = {(cuuint32_t)st_bx(tg.tgx, rad), (cuuint32_t)st_by(tg.tgx, rad), 1u};
+            const cuuint32_t estr[3] = {1u, 1u, 1u};
+            const CUresult r = enc(&maps[(size_t)s * nlev + k],
+                                   sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                   3, const_cast<T *>(base), dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail_msg(MSM_ECUDA, "cuTensorMapEncodeTiled failed (%d) for system %d, level %d", (int)r, s, k);
+        }
+    return MSM_OK;
+}
+template int encode_stencil_maps<float>(const SysDesc *, int, int, int, const float *, CUtensorMap *);
+template int encode_stencil_maps<double>(const SysDesc *, int, int, int, const double *, CUtensorMap *);
+
 template <typename T, int RAD>
-static int launch_stencil_rad(const StencilArgs<T> &a, int *counter, int sms, cudaStream_t st)
+static int launch_stencil_rad(const StencilArgs<T> &a, const CUtensorMap *maps, const int *blk, int *counter,
+                              int sms, cudaStream_t st)
 {
     const size_t smem = stencil_smem_bytes<T>(RAD, a.sg.plane);
     CUDA_TRY(cudaFuncSetAttribute(k_stencil<T, RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_NT, smem));
     if (per_sm < 1) return fail_msg(MSM_EINVAL, "lattice-cutoff tile does not fit (radius %d)", RAD);
-    const int grid = std::min(a.total_tiles, sms * per_sm);
-    k_stencil<T, RAD><<<grid, ST_NT, smem, st>>>(a, counter);
-    count_launch();
-    CUDA_TRY(cudaGetLastError());
+    const int nent = a.bt.B * a.nlev;
+    for (int e0 = 0; e0 < nent; e0 += ST_MAXMAPS) {
+        StMaps m;
+        m.e0 = e0;
+        m.ne = std::min(ST_MAXMAPS, nent - e0);
+        memcpy(m.map, maps + e0, sizeof(CUtensorMap) * (size_t)m.ne);
+        const int tiles = blk[e0 + m.ne] - blk[e0];
+        if (tiles <= 0) continue;
+        CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        const int grid = std::min(tiles, sms * per_sm);
+        k_stencil<T, RAD><<<grid, ST_NT, smem, st>>>(a, m, counter);
+        count_launch();
+        CUDA_TRY(cudaGetLastError());
+    }
     return MSM_OK;
 }
 
 template <typename T>
-int launch_stencil(const StencilArgs<T> &a, int *counter, cudaStream_t st)
+int launch_stencil(const StencilArgs<T> &a, const CUtensorMap *maps, const int *blk, int *counter, cudaStream_t st)
 {
     if (a.nlev <= 0 || a.total_tiles <= 0) return MSM_OK;
     int dev = 0, sms = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     switch (a.sg.rad) {
-    case 1: return launch_stencil_rad<T, 1>(a, counter, sms, st);
-    case 2: return launch_stencil_rad<T, 2>(a, counter, sms, st);
-    case 3: return launch_stencil_rad<T, 3>(a, counter, sms, st);
-    case 4: return launch_stencil_rad<T, 4>(a, counter, sms, st);
-    case 5: return launch_stencil_rad<T, 5>(a, counter, sms, st);
-    case 6: return launch_stencil_rad<T, 6>(a, counter, sms, st);
-    case 7: return launch_stencil_rad<T, 7>(a, counter, sms, st);
-    case 8: return launch_stencil_rad<T, 8>(a, counter, sms, st);
-    case 9: return launch_stencil_rad<T, 9>(a, counter, sms, st);
-    case 10: return launch_stencil_rad<T, 10>(a, counter, sms, st);
-    case 11: return launch_stencil_rad<T, 11>(a, counter, sms, st);
-    case 12: return launch_stencil_rad<T, 12>(a, counter, sms, st);
+#define ST_RADCASE(r) case r: return launch_stencil_rad<T, r>(a, maps, blk, counter, sms, st);
+    ST_RADCASE(1) ST_RADCASE(2) ST_RADCASE(3) ST_RADCASE(4) ST_RADCASE(5) ST_RADCASE(6)
+    ST_RADCASE(7) ST_RADCASE(8) ST_RADCASE(9) ST_RADCASE(10) ST_RADCASE(11) ST_RADCASE(12)
+#undef ST_RADCASE
     default: return fail_msg(MSM_EINVAL, "lattice-cutoff radius %d outside 1..%d", a.sg.rad, ST_MAXRAD);
     }
 }
@@ -685,7 +787,16 @@ __global__ void k_interp(const InterpArgs<T> A)
     const vec4<T> sr = A.sr[i];
     const T q = to_t<T>(A.q[i]);
     const T ke = to_t<T>(A.ke), ih = to_t<T>(D.inv_h);
-    T F[3] = {ke * (sr.x - q * gx * ih), ke * (sr.y - q * gy * ih), ke * (sr.z - q * gz * ih)};
+    // split evaluation (multiple time stepping): F holds the fast part, Fs the grid part
+    const bool split = A.fslow != nullptr;
+    T F[3], Fs[3] = {T(0), T(0), T(0)};
+    if (split) {
+        const T kq = ke * q * ih;
+        F[0] = ke * sr.x; F[1] = ke * sr.y; F[2] = ke * sr.z;
+        Fs[0] = -(kq * gx); Fs[1] = -(kq * gy); Fs[2] = -(kq * gz);
+    } else {
+        F[0] = ke * (sr.x - q * gx * ih); F[1] = ke * (sr.y - q * gy * ih); F[2] = ke * (sr.z - q * gz * ih);
+    }
     const double qd = A.q[i];
     const double phid = A.ke * ((to_d(sr.w) + to_d(p)) - qd * A.self);
     double ed = (0.5 * qd) * phid;
@@ -710,6 +821,13 @@ __global__ void k_interp(const InterpArgs<T> A)
     if (A.forces) { A.forces[3 * i] = Fd[0]; A.forces[3 * i + 1] = Fd[1]; A.forces[3 * i + 2] = Fd[2]; }
     if (A.pot) A.pot[i] = phid;
     A.eatom[i] = ed;
+    if (split) {
+        const double Fsd[3] = {to_d(Fs[0]), to_d(Fs[1]), to_d(Fs[2])};
+        A.fslow[3 * i] = Fsd[0]; A.fslow[3 * i + 1] = Fsd[1]; A.fslow[3 * i + 2] = Fsd[2];
+        A.eslow[i] = (0.5 * qd) * (A.ke * (to_d(p) - qd * A.self));
+#pragma unroll
+        for (int d = 0; d < 3; d++) Fd[d] += Fsd[d];
+    }
     A.vatom[i] = x[0] * Fd[0] + x[1] * Fd[1] + x[2] * Fd[2];
 }
 
@@ -729,8 +847,10 @@ template int launch_anterp<float>(const AnterpArgs<float> &, cudaStream_t);
 template int launch_anterp<double>(const AnterpArgs<double> &, cudaStream_t);
 template int launch_restrict<float>(const Batch &, int, int, float *, const int *, cudaStream_t);
 template int launch_restrict<double>(const Batch &, int, int, double *, const int *, cudaStream_t);
-template int launch_stencil<float>(const StencilArgs<float> &, int *, cudaStream_t);
-template int launch_stencil<double>(const StencilArgs<double> &, int *, cudaStream_t);
+template int launch_stencil<float>(const StencilArgs<float> &, const CUtensorMap *, const int *, int *,
+                                   cudaStream_t);
+template int launch_stencil<double>(const StencilArgs<double> &, const CUtensorMap *, const int *, int *,
+                                    cudaStream_t);
 template int launch_top<float>(const Batch &, int, const double *, const float *, double *, const int *, cudaStream_t);
 template int launch_top<double>(const Batch &, int, const double *, const double *, double *, const int *, cudaStream_t);
 template int launch_top_to_grid<float>(const Batch &, int, const double *, float *, const int *, cudaStream_t);

@@ -15,6 +15,7 @@
 //   k_record_uk    (U, K) of every system after a step, at a step index kept
 //                  on the device so that a replayed CUDA graph writes each
 //                  step's entry
+//   k_add          y += x (multiple time stepping: fast + slow forces)
 //
 // The per-system kernels take a batch: blockIdx.y is the system.
 #include "kernels.cuh"
@@ -77,6 +78,8 @@ __global__ void k_exclusions(const ExclArgs A)
         F[a][0] += s * dx; F[a][1] += s * dy; F[a][2] += s * dz;
         F[b][0] -= s * dx; F[b][1] -= s * dy; F[b][2] -= s * dz;
     }
+    // split evaluation (multiple time stepping): the correction is smooth, a part of the slow force
+    double *fout = A.fslow ? A.fslow : A.forces;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         const int i = i0 + a;
@@ -84,11 +87,12 @@ __global__ void k_exclusions(const ExclArgs A)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double fd = to_d(F[a][d]);
-            if (A.forces) A.forces[3 * i + d] += fd;
+            if (fout) fout[3 * i + d] += fd;
             v += A.x[3 * i + d] * fd;
         }
         if (A.pot) A.pot[i] += dphid[a];
         A.eatom[i] += 0.5 * qd[a] * dphid[a];          // each pair's -1/2 e to both atoms
+        if (A.eslow) A.eslow[i] += 0.5 * qd[a] * dphid[a];
         A.vatom[i] += v;
     }
 }
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(VV_T) k_vv_first(const VVArgs A)
         sx[e] = x;
         A.xo[g0 + e] = x;                                          // positions before the drift
         sv[e] = A.v[g0 + e];
-        sf[e] = A.f[g0 + e];
+        sf[e] = A.fs ? A.f[g0 + e] + A.ws * A.fs[g0 + e] : A.f[g0 + e];
     }
     __syncthreads();
     if (u < D.n_mol) {
@@ -286,7 +290,8 @@ __global__ void __launch_bounds__(VV_T) k_vv_first(const VVArgs A)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const double x = A.x[3 * i + d];
-            const double v = A.v[3 * i + d] + 0.5 * dt * A.f[3 * i + d] * im;
+            const double f = A.fs ? A.f[3 * i + d] + A.ws * A.fs[3 * i + d] : A.f[3 * i + d];
+            const double v = A.v[3 * i + d] + 0.5 * dt * f * im;
             A.xo[3 * i + d] = x;
             A.x[3 * i + d] = x + dt * v;
             A.v[3 * i + d] = v;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(VV_T) k_vv_second(const VVArgs A, double *__re
     for (int e = threadIdx.x; e < 9 * nmb; e += VV_T) {
         sx[e] = A.x[g0 + e];
         sv[e] = A.v[g0 + e];
-        sf[e] = A.f[g0 + e];
+        sf[e] = A.fs ? A.f[g0 + e] + A.ws * A.fs[g0 + e] : A.f[g0 + e];
     }
     __syncthreads();
     if (u < D.n_mol) {
@@ -397,7 +402,8 @@ __global__ void __launch_bounds__(VV_T) k_vv_second(const VVArgs A, double *__re
         double k2 = 0;
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double v = A.v[3 * i + d] + hdt * A.f[3 * i + d] * im;
+            const double f = A.fs ? A.f[3 * i + d] + A.ws * A.fs[3 * i + d] : A.f[3 * i + d];
+            const double v = A.v[3 * i + d] + hdt * f * im;
             A.v[3 * i + d] = v;
             k2 += v * v;
         }
@@ -461,12 +467,13 @@ int launch_kinetic(int n, const double *v, const double *m, double *kin_atom, cu
 
 // One thread per system: uk[s*uk_stride + 2*step + (0, 1)] = (U_s, K_s), step = *ctr.
 __global__ void k_record_uk(int B, const double *__restrict__ sums, int sums_stride, const double *__restrict__ kin,
-                            double *__restrict__ uk, int uk_stride, int *__restrict__ ctr)
+                            double *__restrict__ uk, int uk_stride, int *__restrict__ ctr, bool add_slow)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int step = *ctr;
     if (s < B) {
-        uk[(size_t)s * uk_stride + 2 * step] = sums[s * sums_stride];
+        uk[(size_t)s * uk_stride + 2 * step] = add_slow ? sums[s * sums_stride] + sums[s * sums_stride + 2]
+                                                        : sums[s * sums_stride];
         uk[(size_t)s * uk_stride + 2 * step + 1] = kin[s];
     }
     __syncthreads();
@@ -474,10 +481,25 @@ __global__ void k_record_uk(int B, const double *__restrict__ sums, int sums_str
 }
 
 int launch_record_uk(int B, const double *sums, int sums_stride, const double *kin, double *uk, int uk_stride,
-                     int *ctr, cudaStream_t st)
+                     int *ctr, bool add_slow, cudaStream_t st)
 {
     if (B > 1024) return fail_msg(MSM_EINVAL, "at most 1024 systems record energies");
-    k_record_uk<<<1, 1024, 0, st>>>(B, sums, sums_stride, kin, uk, uk_stride, ctr);
+    k_record_uk<<<1, 1024, 0, st>>>(B, sums, sums_stride, kin, uk, uk_stride, ctr, add_slow);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
+}
+
+__global__ void k_add(int64_t n, const double *__restrict__ x, double *__restrict__ y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+
+int launch_add(int64_t n, const double *x, double *y, cudaStream_t st)
+{
+    if (n <= 0) return MSM_OK;
+    k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;

@@ -2,6 +2,8 @@
 // libmsm_gb300.so (internal; the C ABI is include/msm.h).
 #pragma once
 
+#include <cuda.h>          // CUtensorMap: TMA descriptors of the lattice-cutoff planes
+
 #include "common.cuh"
 
 namespace msm {
@@ -151,7 +153,16 @@ template <typename T> struct StencilArgs {
     T *ucut;               // concatenated, levels < nlev
     const int *status;
 };
-template <typename T> int launch_stencil(const StencilArgs<T> &a, int *tile_counter, cudaStream_t st);
+// maps: one TMA descriptor per (system, level) entry of the batch (encode_stencil_maps);
+// blk: the host copy of blk_off.  Entries are launched in groups of at most
+// ST_MAXMAPS, each group's descriptors passed as a kernel parameter.
+template <typename T> int launch_stencil(const StencilArgs<T> &a, const CUtensorMap *maps, const int *blk,
+                                         int *tile_counter, cudaStream_t st);
+// Encode the descriptors of every (system s, level k < nlev) of a batch into
+// maps[s*nlev + k]: 3-D tiled maps of level k's grid inside q (rows of n[0], a
+// multiple of 4 values), box = one plane of a tile with its halos, zero fill.
+template <typename T> int encode_stencil_maps(const SysDesc *sd, int B, int nlev, int rad, const T *q,
+                                              CUtensorMap *maps);
 template <typename T> size_t stencil_smem_bytes(int rad, int plane);
 int stencil_tile_count(const LevelGeom &L);
 int stencil_plane_values(const LevelGeom &L, int rad);   // plane buffer a tile of level L needs
@@ -187,6 +198,10 @@ template <typename T> struct InterpArgs {
     double *pot;           // (nullable)
     double *eatom;         // 1/2 q_i phi_i + 1/2 E_lj,i
     double *vatom;         // r_i . F_i
+    // multiple time stepping, split evaluation (both NULL otherwise): forces then
+    // receives the fast part (pair sum, LJ, wall), fslow the grid part
+    // -k_e q_i grad u^long, eslow the slow energy 1/2 q_i k_e (u_i^long - q_i self)
+    double *fslow, *eslow;
     const int *status;
 };
 template <typename T> int launch_interp(const InterpArgs<T> &a, cudaStream_t st);
@@ -199,6 +214,8 @@ struct ExclArgs {
     const double *q;
     double ke, a, inv_a;   // k_e, a and 1/a (rounded once, FP64)
     double *forces, *pot, *eatom, *vatom;
+    double *fslow, *eslow; // split evaluation: the correction's forces go to fslow (not forces),
+                           // its energy to eslow as well (both NULL otherwise)
     const int *status;
 };
 template <typename T> int launch_exclusions(const ExclArgs &a, cudaStream_t st);
@@ -216,6 +233,8 @@ struct VVArgs {
     double *x, *v;
     double *xo;            // scratch: positions before the drift
     const double *f, *m;
+    const double *fs;      // multiple time stepping: the kicks use f + ws * fs (NULL: f alone)
+    double ws;
     const double *im;      // 1/m, computed once per md_run call
     double dt;
     double d_oh2, d_hh2;
@@ -230,9 +249,12 @@ template <typename T> int launch_vv_first(const VVArgs &a, cudaStream_t st);
 template <typename T> int launch_vv_second(const VVArgs &a, double *kin_atom, cudaStream_t st);
 int launch_kinetic(int n, const double *v, const double *m, double *kin_atom, cudaStream_t st);
 int launch_inverse(int n, const double *m, double *im, cudaStream_t st);
-// uk[s][step][2] <- (U_s, K_s) for every system; step from *ctr, then ++*ctr.
+// uk[s][step][2] <- (U_s, K_s) for every system; step from *ctr, then ++*ctr.  With add_slow
+// U_s = sums[s][0] + sums[s][2] (a fast-only evaluation plus the last slow energy).
 int launch_record_uk(int B, const double *sums, int sums_stride, const double *kin, double *uk, int uk_stride,
-                     int *ctr, cudaStream_t st);
+                     int *ctr, bool add_slow, cudaStream_t st);
+// y[i] += x[i], i < n (FP64)
+int launch_add(int64_t n, const double *x, double *y, cudaStream_t st);
 
 int launch_parareal_update(int count, const double *f, const double *gnew, const double *gold, double *out,
                            const double *prev, double *dx_partials, cudaStream_t st);

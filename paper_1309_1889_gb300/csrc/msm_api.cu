@@ -162,7 +162,7 @@ struct GraphKey {
     const void *x, *v, *f, *q, *m, *lj, *uk;
     long long uk_stride, geom_gen, alloc_gen;
     double dt;
-    int B, list_on;
+    int B, list_on, mts;
 };
 
 // Brick shape chosen by timing, per system geometry (atoms, cells per axis).
@@ -183,6 +183,7 @@ struct msm_handle {
     std::vector<SysIn> sys_key;
     std::vector<SysDesc> hsd;
     std::vector<int> h_blk;
+    std::vector<CUtensorMap> st_maps;                   // TMA descriptors of the lattice-cutoff planes
     long long geom_gen = 0;
     int N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, stiles = 0;
     int max_n = 0, max_mol = 0, max_units = 0, max_bricks = 0, max_atiles = 0, max_top = 0, max_lj_bricks = 0;
@@ -208,6 +209,7 @@ struct msm_handle {
     DevBuf eatom, vatom, kin, partials, sums, kin_s, status, ctr;
     DevBuf in_pos, in_q, in_lj, out_f, out_p;          // staging of host arrays
     DevBuf md_f, md_xo, md_x, md_v, md_q, md_m, md_lj, md_uk, md_im;
+    DevBuf md_fs, eslow;                                // multiple time stepping: slow forces and energies
     int *h_status = nullptr;
     double *h_scal = nullptr;
     double *h_e = nullptr;                              // pinned, per-system energies
@@ -298,6 +300,7 @@ extern "C" void msm_default_params(msm_params *p)
     p->wall_width = 0.0;
     p->list_skin = 0.0;
     p->method = MSM_METHOD_MSM;
+    p->mts_steps = 0;
     p->wolf_alpha = 0.0;
 }
 
@@ -322,6 +325,9 @@ static int check_params(const msm_params *p)
     if (!(p->wolf_alpha >= 0) || !std::isfinite(p->wolf_alpha)) return fail_msg(MSM_EINVAL, "wolf_alpha must be >= 0");
     if (p->method == MSM_METHOD_WOLF && p->list_skin > 0)
         return fail_msg(MSM_EINVAL, "Verlet lists serve the MSM and the simple cutoff only");
+    if (p->mts_steps < 0) return fail_msg(MSM_EINVAL, "mts_steps must be >= 0");
+    if (p->mts_steps > 1 && p->method != MSM_METHOD_MSM)
+        return fail_msg(MSM_EINVAL, "multiple time stepping needs the MSM (the cutoff methods have no slow part)");
     if (p->method != MSM_METHOD_MSM) return MSM_OK;          // no grids: n_levels is not used
     int rad = 0;
     while ((double)(rad + 1) * p->h < 2.0 * p->a) rad++;
@@ -363,6 +369,7 @@ extern "C" void msm_destroy(msm_handle *h)
                      &h->kin_s, &h->status, &h->ctr, &h->sd_buf, &h->blk_buf,
                      &h->in_pos, &h->in_q, &h->in_lj, &h->out_f, &h->out_p, &h->md_f, &h->md_xo,
                      &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk, &h->md_im,
+                     &h->md_fs, &h->eslow,
                      &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->vl_rtab, &h->vl_rtn,
                      &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_nbr_lj, &h->vl_ctl};
     for (DevBuf *b : all) release(*b);
@@ -502,17 +509,32 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             D.wall_hi[k] = (int)floor((S.box[3 + k] - h->p.wall_width) * D.inv_h) - 2;
         }
         D.gg.levels = l;
-        int64_t lo[3], hi[3], tot = 0;
+        // Level ranges: level 0 spans [-1, floor(L/h) + 2], level k+1 [ceil((lo-3)/2),
+        // floor((hi+3)/2)] of level k.  Each level's x range is then extended to a
+        // multiple of 4 points (hi_x grows by up to 3, and the next level's range
+        // derives from the extended one): rows start on 16-byte boundaries, as the
+        // TMA copies of the lattice cutoff need.  The added points
+        // carry zero charge at every level (a point gets charge only from points
+        // within its restriction taps, all inside the unextended range), and no
+        // point of the unextended range reads a potential outside it, so the
+        // extension changes no result.
+        int64_t lo[3], hi[3], hi_log = 0, tot = 0;
         for (int k = 0; k < 3; k++) { lo[k] = -1; hi[k] = (int64_t)floor(S.box[3 + k] / hh) + 2; }
+        hi_log = hi[0];
         for (int k = 0; k < l; k++) {
-            if (k > 0)
+            if (k > 0) {
                 for (int e = 0; e < 3; e++) { lo[e] = -floordiv64(-(lo[e] - 3), 2); hi[e] = floordiv64(hi[e] + 3, 2); }
+                hi_log = floordiv64(hi_log + 3, 2);
+            }
+            const int64_t nx_log = hi_log - lo[0] + 1, nx_ext = hi[0] - lo[0] + 1;
+            hi[0] = lo[0] + ((nx_ext + 3) / 4) * 4 - 1;
             int64_t sz = 1;
             for (int e = 0; e < 3; e++) {
                 D.gg.L[k].lo[e] = (int)lo[e];
                 D.gg.L[k].n[e] = (int)(hi[e] - lo[e] + 1);
                 sz *= D.gg.L[k].n[e];
             }
+            D.gg.L[k].nx_log = (int)nx_log;
             D.gg.L[k].off = (int)tot;
             tot += sz;
         }
@@ -623,6 +645,16 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     for (const SysDesc &D : d)
         for (int k = 0; k + 1 < l; k++) h->sg.plane = std::max(h->sg.plane, stencil_plane_values(D.gg.L[k], h->sg.rad));
     h->hsd.swap(d);
+    if (grids && l > 1) {
+        // descriptors of every (system, level) plane source: the grid buffer and the
+        // geometry are fixed until the next change of batch
+        h->st_maps.resize((size_t)B * (l - 1));
+        if (h->precision == MSM_FP32)
+            TRY(encode_stencil_maps<float>(h->hsd.data(), B, l - 1, h->sg.rad, h->qgrid.as<float>(), h->st_maps.data()));
+        else
+            TRY(encode_stencil_maps<double>(h->hsd.data(), B, l - 1, h->sg.rad, h->qgrid.as<double>(),
+                                            h->st_maps.data()));
+    }
     CUDA_TRY(cudaMemcpyAsync(h->sd_buf.p, h->hsd.data(), sizeof(SysDesc) * (size_t)B, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(h->blk_buf.p, h->h_blk.data(), sizeof(int) * h->h_blk.size(), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));          // the host copies may change with the next batch
@@ -681,6 +713,7 @@ static int ensure_atoms(msm_handle *h, int64_t n)
     TRY(ensure(h->eatom, sizeof(double) * nn));
     TRY(ensure(h->vatom, sizeof(double) * nn));
     TRY(ensure(h->kin, sizeof(double) * nn));
+    if (h->p.mts_steps > 1) TRY(ensure(h->eslow, sizeof(double) * nn));
     return MSM_OK;
 }
 
@@ -837,10 +870,16 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
 // eatom/vatom get per-atom energy and virial; sums[4 s + 0] = U_s,
 // sums[4 s + 1] = virial_s.  No host synchronisation (except the autotuner's,
 // once per geometry).
+// Evaluation modes (multiple time stepping): the whole force into forces; the
+// split into fast (forces) and slow (fslow) parts; or the fast part alone.
+enum EvalMode { EVAL_FULL = 0, EVAL_SPLIT = 1, EVAL_FAST = 2 };
+
 struct EvalIO {
     const double *pos, *q;
     const uint8_t *lj;       // nullable (device)
     double *forces, *pot;    // device, nullable
+    double *fslow = nullptr; // EVAL_SPLIT: slow forces (device)
+    int mode = EVAL_FULL;
 };
 
 template <typename T>
@@ -866,7 +905,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     // forked here and joined before interpolation: its small, latency-bound launches
     // (the lattice cutoff keeps about four CTAs per SM busy) fill the SMs beside the
     // issue-bound pair kernels.
-    const bool grids = has_grids(h->p);
+    const bool grids = has_grids(h->p) && io.mode != EVAL_FAST;
+    const bool split = grids && io.mode == EVAL_SPLIT;
     const bool fork = grids && !h->prof.on && !h->list_on;
     cudaStream_t gs = st;
     if (fork) {
@@ -902,7 +942,7 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             sa.bt = bt; sa.nlev = l - 1; sa.blk_off = h->blk_buf.as<int>(); sa.total_tiles = h->stiles; sa.sg = h->sg;
             sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
             PROF(ST_STENCIL);
-            TRY(launch_stencil<T>(sa, h->status.as<int>() + 2, st));
+            TRY(launch_stencil<T>(sa, h->st_maps.data(), h->h_blk.data(), h->status.as<int>() + 2, st));
         }
         // step 5: top level in FP64
         { PROF(ST_TOP); TRY(launch_top<T>(bt, h->max_top, h->ttop.as<double>(), qg, h->utop.as<double>(), status, st)); }
@@ -981,10 +1021,13 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     ia.u = grids ? ug : nullptr; ia.pos = io.pos; ia.q = io.q; ia.ke = h->p.coulomb_k;
     // self coefficient: phi_i -= q_i self (the MSM's gamma(0)/a; Wolf's neutralisation term)
     const double al = h->p.wolf_alpha, a_ = h->p.a;
-    ia.self = h->p.method == MSM_METHOD_MSM ? GAMMA_C0 / a_
+    // (a fast-only evaluation has no self term: it belongs to the slow, grid part)
+    ia.self = io.mode == EVAL_FAST ? 0.0
+            : h->p.method == MSM_METHOD_MSM ? GAMMA_C0 / a_
             : h->p.method == MSM_METHOD_WOLF ? erfc(al * a_) / a_ + 2.0 * al / sqrt(M_PI) : 0.0;
     ia.wall_k = model ? h->p.wall_k : 0.0; ia.wall_w = h->p.wall_width;
     ia.forces = io.forces; ia.pot = io.pot; ia.eatom = h->eatom.as<double>(); ia.vatom = h->vatom.as<double>();
+    ia.fslow = split ? io.fslow : nullptr; ia.eslow = split ? h->eslow.as<double>() : nullptr;
     ia.status = status;
     { PROF(ST_INTERP); TRY(launch_interp<T>(ia, st)); }
     PROF(ST_SUMS);
@@ -993,11 +1036,15 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         ex.bt = bt; ex.max_mol = h->max_mol; ex.x = io.pos; ex.q = io.q; ex.ke = h->p.coulomb_k; ex.a = h->p.a;
         ex.inv_a = 1.0 / h->p.a;
         ex.forces = io.forces; ex.pot = io.pot; ex.eatom = h->eatom.as<double>(); ex.vatom = h->vatom.as<double>();
+        ex.fslow = ia.fslow; ex.eslow = ia.eslow;
         ex.status = status;
         TRY(launch_exclusions<T>(ex, st));
     }
-    const double *cols[2] = {h->eatom.as<double>(), h->vatom.as<double>()};
-    TRY(launch_sum(bt, h->max_n, h->PB, 2, cols, h->partials.as<double>(), h->sums.as<double>(), 4, status, st));
+    // sums[s][0] energy, [1] virial, [2] slow energy (split evaluations only: a
+    // fast-only evaluation leaves the last one in place)
+    const double *cols[3] = {h->eatom.as<double>(), h->vatom.as<double>(), h->eslow.as<double>()};
+    TRY(launch_sum(bt, h->max_n, h->PB, split ? 3 : 2, cols, h->partials.as<double>(), h->sums.as<double>(), 4,
+                   status, st));
     return MSM_OK;
 }
 
@@ -1220,32 +1267,55 @@ template <typename T> static double rattle_tol() { return sizeof(T) == 4 ? 2e-6 
 // kin_ready: the per-atom kinetic energies are already in h->kin (written by
 // the second half kick).
 static int record_uk(msm_handle *h, const RunSys &s, double *uk, int64_t uk_stride, cudaStream_t st,
-                     bool kin_ready = false)
+                     bool kin_ready = false, bool add_slow = false)
 {
     if (!kin_ready) TRY(launch_kinetic(h->N, s.v, s.m, h->kin.as<double>(), st));
     const double *cols[1] = {h->kin.as<double>()};
     TRY(launch_sum(batch_of(h), h->max_n, h->PB, 1, cols, h->partials.as<double>(), h->kin_s.as<double>(), 1,
                    h->status.as<int>(), st));
     return launch_record_uk(h->B, h->sums.as<double>(), 4, h->kin_s.as<double>(), uk, (int)uk_stride,
-                            h->ctr.as<int>(), st);
+                            h->ctr.as<int>(), add_slow, st);
 }
 
+// Fast steps per slow step (1: plain velocity Verlet).
+static int mts_of(const msm_handle *h) { return h->p.mts_steps > 1 ? h->p.mts_steps : 1; }
+
 // One velocity Verlet step of the batch: half kick + drift + SHAKE, forces,
-// half kick + RATTLE (+ the energies when recorded).
+// half kick + RATTLE (+ the energies when recorded).  With multiple time
+// stepping, one outer step: k fast steps whose first and last half kicks add
+// the slow force's impulse k dt/2 (io.fslow, weight k), fast-only evaluations
+// inside, and a split evaluation (fast and slow parts) at the end.
 template <typename T>
 static int md_step(msm_handle *h, const RunSys &s, const EvalIO &io, const VVArgs &va, double *uk,
                    int64_t uk_stride, cudaStream_t st)
 {
-    { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
-    TRY(evaluate_t<T>(h, io, st));
-    { PROF(ST_VV2); TRY(launch_vv_second<T>(va, uk ? h->kin.as<double>() : nullptr, st)); }
-    if (uk) TRY(record_uk(h, s, uk, uk_stride, st, true));
+    const int k = mts_of(h);
+    if (k == 1) {
+        { PROF(ST_VV1); TRY(launch_vv_first<T>(va, st)); }
+        TRY(evaluate_t<T>(h, io, st));
+        { PROF(ST_VV2); TRY(launch_vv_second<T>(va, uk ? h->kin.as<double>() : nullptr, st)); }
+        if (uk) TRY(record_uk(h, s, uk, uk_stride, st, true));
+        return MSM_OK;
+    }
+    for (int j = 0; j < k; j++) {
+        const bool first = j == 0, last = j == k - 1;
+        VVArgs v1 = va;
+        v1.fs = first ? io.fslow : nullptr; v1.ws = (double)k;
+        { PROF(ST_VV1); TRY(launch_vv_first<T>(v1, st)); }
+        EvalIO e = io;
+        e.mode = last ? EVAL_SPLIT : EVAL_FAST;
+        TRY(evaluate_t<T>(h, e, st));
+        VVArgs v2 = va;
+        v2.fs = last ? io.fslow : nullptr; v2.ws = (double)k;
+        { PROF(ST_VV2); TRY(launch_vv_second<T>(v2, uk ? h->kin.as<double>() : nullptr, st)); }
+        if (uk) TRY(record_uk(h, s, uk, uk_stride, st, true, !last));
+    }
     return MSM_OK;
 }
 
-// Capture one md step into a CUDA graph on the handle's own stream (capture
-// records the launches; nothing runs), or reuse the graph captured for the
-// same arrays, geometry and buffers.
+// Capture one md step (an outer step with multiple time stepping) into a CUDA
+// graph on the handle's own stream (capture records the launches; nothing
+// runs), or reuse the graph captured for the same arrays, geometry and buffers.
 static GraphKey graph_key(const msm_handle *h, const RunSys &s, const EvalIO &io, double dt, double *uk,
                           int64_t uk_stride)
 {
@@ -1253,7 +1323,7 @@ static GraphKey graph_key(const msm_handle *h, const RunSys &s, const EvalIO &io
     memset(&k, 0, sizeof k);
     k.x = s.x; k.v = s.v; k.f = io.forces; k.q = s.q; k.m = s.m; k.lj = s.lj; k.uk = uk;
     k.uk_stride = uk_stride; k.geom_gen = h->geom_gen; k.alloc_gen = g_alloc_gen.load(); k.dt = dt;
-    k.B = s.B; k.list_on = h->list_on ? 1 : 0;
+    k.B = s.B; k.list_on = h->list_on ? 1 : 0; k.mts = mts_of(h);
     return k;
 }
 
@@ -1294,25 +1364,31 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
     int64_t n = 0;
     for (int b = 0; b < s.B; b++) n += s.sys[b].n;
     const size_t nn = (size_t)(n > 0 ? n : 1);
+    const int k = mts_of(h);                            // fast steps per slow step
+    if (n_steps % k) return fail_msg(MSM_EINVAL, "n_steps (%d) must be a multiple of mts_steps (%d)", n_steps, k);
     TRY(ensure(h->md_xo, sizeof(double) * 3 * nn));
     TRY(ensure(h->md_im, sizeof(double) * nn));
     if (!s.f) TRY(ensure(h->md_f, sizeof(double) * 3 * nn));
+    if (k > 1) TRY(ensure(h->md_fs, sizeof(double) * 3 * nn));
     h->list_on = false;
     TRY(set_batch(h, s.B, s.sys, st));
     EvalIO io;
     io.pos = s.x; io.q = s.q; io.lj = s.lj;
-    io.forces = s.f ? s.f : h->md_f.as<double>();
+    io.forces = s.f ? s.f : h->md_f.as<double>();      // with k > 1: the fast part during the run
     io.pot = nullptr;
+    if (k > 1) { io.fslow = h->md_fs.as<double>(); io.mode = EVAL_SPLIT; }
     TRY(launch_inverse((int)n, s.m, h->md_im.as<double>(), st));
     VVArgs va;
     va.bt = batch_of(h); va.max_units = h->max_units;
     va.x = s.x; va.v = s.v; va.xo = h->md_xo.as<double>();
     va.f = io.forces; va.m = s.m; va.im = h->md_im.as<double>(); va.dt = dt;
+    va.fs = nullptr; va.ws = 0.0;
     va.d_oh2 = h->p.d_oh * h->p.d_oh; va.d_hh2 = h->p.d_hh * h->p.d_hh;
     va.tol = shake_tol<T>(); va.tol_v = rattle_tol<T>(); va.max_iter = sizeof(T) == 4 ? 200 : 1000;
     va.status = h->status.as<int>();
-    if (s.f && s.f_valid && !h->tune_pending) {
-        // forces and energies of the start positions come with the systems
+    if (s.f && s.f_valid && !h->tune_pending && k == 1) {
+        // forces and energies of the start positions come with the systems (whole
+        // forces: multiple time stepping needs them split, so it evaluates)
         CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int) * 4, st));
         for (int b = 0; b < s.B; b++) h->h_e[b] = s.e0[b];
         CUDA_TRY(cudaMemcpy2DAsync(h->sums.p, 4 * sizeof(double), h->h_e, sizeof(double), sizeof(double),
@@ -1334,7 +1410,8 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
     const bool warm = graphs && !h->tune_pending && h->gexec &&
                       [&] { const GraphKey k = graph_key(h, s, io, dt, uk, uk_stride);
                             return memcmp(&k, &h->gkey, sizeof k) == 0; }();
-    for (int step = 0; step < n_steps && rc == MSM_OK; step++) {
+    // one md_step is one step, or one outer step of k steps (multiple time stepping)
+    for (int step = 0; step < n_steps / k && rc == MSM_OK; step++) {
         if (!graphs || (step == 0 && !warm) || h->tune_pending) {
             rc = md_step<T>(h, s, io, va, uk, uk_stride, st);
             continue;
@@ -1350,6 +1427,9 @@ static int run_md_t(msm_handle *h, const RunSys &s, double dt, int n_steps, doub
         }
     }
     h->list_on = false;
+    // the caller's forces are the whole forces at the end positions (the last
+    // evaluation of an outer step is a split one)
+    if (rc == MSM_OK && k > 1 && s.f) rc = launch_add(3 * n, h->md_fs.as<double>(), s.f, st);
     return rc;
 }
 
@@ -1936,7 +2016,7 @@ extern "C" int msm_grid_shape(msm_handle *h, int32_t level, int64_t shape[3], in
     if (!has_grids(h->p)) return fail_msg(MSM_EINVAL, "the cutoff methods have no grids");
     if (level < 0 || level >= h->gg.levels) return fail_msg(MSM_EINVAL, "level out of range");
     for (int d = 0; d < 3; d++) {
-        if (shape) shape[d] = h->gg.L[level].n[d];
+        if (shape) shape[d] = d ? h->gg.L[level].n[d] : h->gg.L[level].nx_log;
         if (lo) lo[d] = h->gg.L[level].lo[d];
     }
     return MSM_OK;
@@ -1950,19 +2030,23 @@ extern "C" int msm_stage_grid(msm_handle *h, int32_t level, int32_t which, doubl
     if (level < 0 || level >= l || which < 0 || which > 2 || (which == 1 && level == l - 1))
         return fail_msg(MSM_EINVAL, "no such grid");
     const LevelGeom &L = h->gg.L[level];
-    const int64_t m = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    // the method's points: nx_log of every stored row of n[0]
+    const int64_t rows = (int64_t)L.n[1] * L.n[2], m = (int64_t)L.nx_log * rows;
     if (count < m) return fail_msg(MSM_EINVAL, "output too small");
     CUDA_TRY(cudaDeviceSynchronize());
     if (which == 2 && level == l - 1) {
-        CUDA_TRY(cudaMemcpy(out, h->utop.p, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * L.nx_log, h->utop.p, sizeof(double) * L.n[0],
+                              sizeof(double) * L.nx_log, (size_t)rows, cudaMemcpyDeviceToHost));
         return MSM_OK;
     }
     const DevBuf &b = which == 0 ? h->qgrid : (which == 1 ? h->ucut : h->ugrid);
     if (h->precision == MSM_FP64) {
-        CUDA_TRY(cudaMemcpy(out, b.as<double>() + L.off, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy2D(out, sizeof(double) * L.nx_log, b.as<double>() + L.off, sizeof(double) * L.n[0],
+                              sizeof(double) * L.nx_log, (size_t)rows, cudaMemcpyDeviceToHost));
     } else {
         std::vector<float> tmp((size_t)m);
-        CUDA_TRY(cudaMemcpy(tmp.data(), b.as<float>() + L.off, sizeof(float) * m, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy2D(tmp.data(), sizeof(float) * L.nx_log, b.as<float>() + L.off, sizeof(float) * L.n[0],
+                              sizeof(float) * L.nx_log, (size_t)rows, cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < m; i++) out[i] = tmp[(size_t)i];
     }
     return MSM_OK;

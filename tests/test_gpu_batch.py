@@ -199,3 +199,23 @@ def test_batch_with_more_cells_than_one_scan_pass_holds(api, torch):
         o0, o1 = offsets[b], offsets[b + 1]
         assert e[b] == es
         assert np.array_equal(f[o0:o1], fs) and np.array_equal(p[o0:o1], ps)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_beyond_one_group_of_plane_descriptors(api, torch, prec):
+    """13 systems of 3 levels have 26 (system, level) lattice cutoffs, more than the
+    24 TMA descriptors one launch carries: the lattice cutoff runs as two launches,
+    and every system still gets exactly the bits it gets alone."""
+    systems = [inputs.random_cloud(300 + 37 * k, 1.6 + 0.05 * k, seed=60 + k, neutral=True, margin=0.3)
+               for k in range(13)]
+    m = api.MSM(a=A, h=H, levels=3, precision=prec)
+    singles = [m.energy_forces(s.pos, s.q, s.box) for s in systems]
+    offsets = np.cumsum([0] + [len(s.q) for s in systems])
+    pos = np.concatenate([s.pos for s in systems]); q = np.concatenate([s.q for s in systems])
+    boxes = np.stack([np.asarray(s.box, dtype=np.float64) for s in systems])
+    mb = api.MSM(a=A, h=H, levels=3, precision=prec)
+    e, f, p = mb.energy_forces_batched(offsets, pos, q, boxes)
+    for b, (es, fs, ps) in enumerate(singles):
+        o0, o1 = offsets[b], offsets[b + 1]
+        assert e[b] == es
+        assert np.array_equal(f[o0:o1], fs) and np.array_equal(p[o0:o1], ps)

@@ -94,6 +94,20 @@ def test_method_values_and_validation(L):
     assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"Verlet lists" in L.msm_last_error()
 
 
+def test_multiple_time_stepping_validation(L):
+    """mts_steps defaults to 0 (plain velocity Verlet), must be >= 0, and above 1
+    needs the MSM: the cutoff methods have no grid part to put on the slow clock."""
+    from paper_1309_1889_gb300 import api
+    p = api.Params()
+    L.msm_default_params(C.byref(p))
+    assert p.mts_steps == 0
+    h = C.c_void_p()
+    bad = api.make_params(mts=-1)
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"mts_steps" in L.msm_last_error()
+    bad = api.make_params(mts=2, method="cutoff")
+    assert L.msm_create(C.byref(bad), C.byref(h)) == -1 and b"multiple time stepping" in L.msm_last_error()
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """sizeof and field offsets of msm_params and msm_system as a C compiler lays them
     out from include/msm.h, against the ctypes structures of the binding."""
