@@ -274,6 +274,22 @@ MSM_API int  parareal_run(const msm_params *G, double dtG, int32_t stepsG,
                   double *slices_x, double *slices_v, int32_t *iters_done, double *last_dx,
                   void *stream);
 
+/* Resume parareal (Sec. 4) from a checkpoint: slices_x/v hold the iterate
+ * lambda^k (n_slices + 1 states, slot 0 = state0's x, v) that parareal_run or
+ * parareal_resume wrote after k = iters_before iterations (for instance a run
+ * stopped by its max_iter, or a saved copy of one).  The coarse propagations
+ * G(lambda^k_n) the next correction needs are recomputed from those states (a
+ * G sweep), then at most max_iter more iterations run; the iterates equal
+ * those of one uninterrupted parareal_run bit for bit.  *iters_done counts
+ * all iterations, k included.  state0 supplies q, m, lj, box and the atom
+ * counts (its x, v must equal slot 0).  Other arguments, outputs and errors
+ * as parareal_run; iters_before < 0 is MSM_EINVAL. */
+MSM_API int  parareal_resume(const msm_params *G, double dtG, int32_t stepsG,
+                  const msm_params *F, double dtF, int32_t stepsF,
+                  const msm_system *state0, int32_t n_slices, int32_t iters_before, int32_t max_iter,
+                  double tol, double *slices_x, double *slices_v, int32_t *iters_done,
+                  double *last_dx, void *stream);
+
 /* Parareal over a sliding computational window (Sec. 4: the iteration runs on
  * a window of time points).  At most `window` slices [b, e) are iterated at
  * once: each iteration runs F on every window slice as one batch and the
@@ -297,6 +313,17 @@ MSM_API int  parareal_run_window(const msm_params *G, double dtG, int32_t stepsG
                   const msm_system *state0, int32_t n_slices, int32_t window, int32_t max_iter,
                   double tol, double *slices_x, double *slices_v, int32_t *iters_done,
                   double *last_dx, void *stream);
+
+/* Budget for the device memory the library allocates: the scratch and staging
+ * buffers of every handle in the process (callers' arrays are not counted, nor
+ * the static array of msm_cell_list_noalloc).  bytes <= 0 removes the budget
+ * (the default).  An allocation that would take the library's holdings past
+ * the budget fails as a failed cudaMalloc does: the call that needed it
+ * returns MSM_ENOMEM, and the handle stays usable (a later call with room
+ * allocates again).  Returns the bytes held when called.  No counterpart in
+ * the paper: it lets a caller that shares the GPU with other allocators cap
+ * the library's share. */
+MSM_API int64_t msm_set_device_budget(int64_t bytes);
 
 /* Inspection of the last evaluation on h (host outputs, synchronous).
  * msm_grid_shape: level k's point counts (nx, ny, nz) and index origin

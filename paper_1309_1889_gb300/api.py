@@ -53,7 +53,8 @@ EXPORTS = ("msm_default_params", "msm_create", "msm_destroy", "msm_energy_forces
            "msm_system_forces", "md_run", "parareal_run", "msm_grid_shape", "msm_stage_grid", "msm_cell_list",
            "msm_stage_atoms", "msm_kernel_launches", "msm_last_error", "msm_profile_enable", "msm_profile_read",
            "msm_stage_name", "msm_count_pairs", "msm_cell_list_noalloc", "msm_list_stats",
-           "msm_system_forces_batched", "md_run_batched", "msm_diag_convert", "parareal_run_window")
+           "msm_system_forces_batched", "md_run_batched", "msm_diag_convert", "parareal_run_window",
+           "parareal_resume", "msm_set_device_budget")
 
 
 def lib():
@@ -82,6 +83,10 @@ def lib():
         L.parareal_run_window.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, i32, d, p, p,
                                           P(i32), P(d), p]
         L.parareal_run_window.restype = C.c_int
+        L.parareal_resume.argtypes = [P(Params), d, i32, P(Params), d, i32, P(SystemC), i32, i32, i32, d, p, p,
+                                      P(i32), P(d), p]
+        L.parareal_resume.restype = C.c_int
+        L.msm_set_device_budget.argtypes = [i64]; L.msm_set_device_budget.restype = i64
         L.msm_grid_shape.argtypes = [p, i32, p, p]; L.msm_grid_shape.restype = C.c_int
         L.msm_stage_grid.argtypes = [p, i32, i32, p, i64]; L.msm_stage_grid.restype = C.c_int
         L.msm_cell_list.argtypes = [p, p, p, p]; L.msm_cell_list.restype = C.c_int
@@ -435,12 +440,14 @@ def _system_struct(sys, need_v=False):
 
 
 def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float, model="water",
-                 precision="fp32", stream=None, window=None):
+                 precision="fp32", stream=None, window=None, resume=None):
     """Parareal over md_run: G and F are dict(a, h, levels, dt, steps[, method, wolf_alpha,
     wall_k, wall_width, ...]); method "cutoff" or "wolf" makes a cutoff coarse propagator.
 
     window: None runs parareal_run (every slice iterated); an integer runs
     parareal_run_window with at most that many slices per iteration.
+    resume: (xs, vs, k) -- continue, through parareal_resume, from the iterate that
+    an earlier call returned after k iterations (at most max_iter more).
 
     Returns (xs (n_slices+1, n, 3), vs, iterations, last max |dx|, converged)."""
     def params(P):
@@ -456,7 +463,13 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
     it = C.c_int32(0); dx = C.c_double(0)
     xs[0] = np.asarray(sys.pos.cpu() if _is_tensor(sys.pos) else sys.pos)
     vs[0] = np.asarray(sys.vel.cpu() if _is_tensor(sys.vel) else sys.vel)
-    if window is None:
+    if resume is not None:
+        rx, rv, rk = resume
+        xs[:] = np.asarray(rx); vs[:] = np.asarray(rv)
+        rc = lib().parareal_resume(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
+                                   int(F["steps"]), C.byref(s), int(n_slices), int(rk), int(max_iter), float(tol),
+                                   _ptr(xs), _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
+    elif window is None:
         rc = lib().parareal_run(C.byref(pg), float(G["dt"]), int(G["steps"]), C.byref(pf), float(F["dt"]),
                                 int(F["steps"]), C.byref(s), int(n_slices), int(max_iter), float(tol), _ptr(xs),
                                 _ptr(vs), C.byref(it), C.byref(dx), _stream(stream))
@@ -467,6 +480,11 @@ def parareal_run(G: dict, F: dict, sys, n_slices: int, max_iter: int, tol: float
     if rc != 0 and not (rc == -6 and lib().msm_last_error().decode().startswith("parareal:")):
         _check(rc)                     # a propagator failed (not merely a slow convergence)
     return xs, vs, it.value, dx.value, rc == 0
+
+
+def set_device_budget(nbytes: int) -> int:
+    """Cap the device memory the library allocates (0: no cap); returns the bytes it holds."""
+    return int(lib().msm_set_device_budget(int(nbytes)))
 
 
 # ----------------------------------------------------------------- autograd

@@ -68,14 +68,21 @@ struct DevBuf {
     template <typename X> X *as() const { return static_cast<X *>(p); }
 };
 
+// Device bytes the library holds (every handle's buffers) and the caller's budget for them
+static std::atomic<long long> g_held_bytes{0}, g_budget_bytes{0};
+
 static int ensure(DevBuf &b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return MSM_OK;
-    if (b.p) cudaFree(b.p);
+    if (b.p) { cudaFree(b.p); g_held_bytes.fetch_sub((long long)b.cap); }
     b.p = nullptr;
     b.cap = 0;
     g_alloc_gen.fetch_add(1);
+    const long long budget = g_budget_bytes.load();
+    if (budget > 0 && g_held_bytes.load() + (long long)bytes > budget)
+        return fail_msg(MSM_ENOMEM, "device memory budget of %lld bytes exceeded (%lld held, %zu more needed)",
+                        budget, g_held_bytes.load(), bytes);
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -83,14 +90,21 @@ static int ensure(DevBuf &b, size_t bytes)
         return fail_msg(MSM_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     b.cap = bytes;
+    g_held_bytes.fetch_add((long long)bytes);
     return MSM_OK;
 }
 
 static void release(DevBuf &b)
 {
-    if (b.p) cudaFree(b.p);
+    if (b.p) { cudaFree(b.p); g_held_bytes.fetch_sub((long long)b.cap); }
     b.p = nullptr;
     b.cap = 0;
+}
+
+extern "C" int64_t msm_set_device_budget(int64_t bytes)
+{
+    g_budget_bytes.store(bytes > 0 ? (long long)bytes : 0);
+    return (int64_t)g_held_bytes.load();
 }
 
 // Device memory of the current device, or managed memory: used in place.
@@ -477,6 +491,10 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         same = sys[s].n == h->sys_key[s].n && sys[s].n_mol == h->sys_key[s].n_mol &&
                memcmp(sys[s].box, h->sys_key[s].box, sizeof sys[s].box) == 0;
     if (same) return MSM_OK;
+    // until this rebuild completes the handle describes no batch: a failure below (an
+    // allocation beyond the budget, say) must not leave a later call reusing buffers
+    // that were freed on the way
+    h->have_geom = false;
 
     const double hh = h->p.h;
     const bool grids = has_grids(h->p);
@@ -1712,6 +1730,7 @@ struct PararealRun {
     double *slices_x, *slices_v;
     int *iters_done;
     double *last_dx;
+    int resume_k = -1;     // plain mode: continue from the iterate lambda^k held in slices_x/v (-1: start)
 };
 
 static int parareal_impl(const PararealRun &P, cudaStream_t st)
@@ -1854,8 +1873,26 @@ static int parareal_impl(const PararealRun &P, cudaStream_t st)
         };
         CUDA_TRY(cudaMemsetAsync(gst.p, 0, sizeof(int) * 4, st));
         int b = 0, e = std::min(W, ns);
-        TRY(fill(0, e));
-        int done = 0;
+        const int k_start = P.resume_k >= 0 ? P.resume_k : 0;
+        if (P.resume_k >= 0) {
+            // resume: lambda^k_n from the caller (n = 0 .. n_slices), and G(lambda^k_n) of every
+            // slice, which the sweep of iteration k-1 left behind -- recomputed by the same
+            // propagation on the same states, so the iterates continue bit for bit
+            for (int n = 1; n <= ns; n++) {
+                CUDA_TRY(cudaMemcpyAsync(LX(n), P.slices_x + (size_t)n * n3, sizeof(double) * n3, cudaMemcpyDefault, st));
+                CUDA_TRY(cudaMemcpyAsync(LV(n), P.slices_v + (size_t)n * n3, sizeof(double) * n3, cudaMemcpyDefault, st));
+            }
+            for (int n = 0; n < ns; n++) {
+                CUDA_TRY(D2D(tmp_x.as<double>(), LX(n)));
+                CUDA_TRY(D2D(tmp_v.as<double>(), LV(n)));
+                TRY(runG(n));
+                CUDA_TRY(D2D(GX(n), tmp_x.as<double>()));
+                CUDA_TRY(D2D(GV(n), tmp_v.as<double>()));
+            }
+        } else {
+            TRY(fill(0, e));
+        }
+        int done = k_start;
         double dxh = INFINITY;
         bool diverged = false;
         {
@@ -1865,7 +1902,7 @@ static int parareal_impl(const PararealRun &P, cudaStream_t st)
                                     status_text(gs));
         }
         if (P.sliding) for (int n = 1; n <= e; n++) TRY(publish(n));
-        for (int it = 0; it < P.max_iter && b < ns; it++) {
+        for (int it = k_start; it < k_start + P.max_iter && b < ns; it++) {
             if (P.sliding) {
                 // refill the window: first iterates of the slices entering it, by G in order
                 const int e2 = std::min(b + W, ns);
@@ -1993,6 +2030,19 @@ extern "C" int parareal_run(const msm_params *G, double dtG, int32_t stepsG, con
     TRY(parareal_args(G, dtG, stepsG, F, dtF, stepsF, state0, n_slices, max_iter, tol, slices_x, slices_v));
     PararealRun P{G, F, dtG, dtF, stepsG, stepsF, state0, n_slices, n_slices, max_iter, false, tol,
                   slices_x, slices_v, iters_done, last_dx};
+    return parareal_impl(P, (cudaStream_t)stream);
+}
+
+extern "C" int parareal_resume(const msm_params *G, double dtG, int32_t stepsG, const msm_params *F, double dtF,
+                               int32_t stepsF, const msm_system *state0, int32_t n_slices, int32_t iters_before,
+                               int32_t max_iter, double tol, double *slices_x, double *slices_v, int32_t *iters_done,
+                               double *last_dx, void *stream)
+{
+    TRY(parareal_args(G, dtG, stepsG, F, dtF, stepsF, state0, n_slices, max_iter, tol, slices_x, slices_v));
+    if (iters_before < 0) return fail_msg(MSM_EINVAL, "iters_before must be >= 0");
+    PararealRun P{G, F, dtG, dtF, stepsG, stepsF, state0, n_slices, n_slices, max_iter, false, tol,
+                  slices_x, slices_v, iters_done, last_dx};
+    P.resume_k = iters_before;
     return parareal_impl(P, (cudaStream_t)stream);
 }
 

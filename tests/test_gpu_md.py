@@ -227,3 +227,28 @@ def test_windowed_parareal_matches_oracle(api, torch, pr_sys):
         assert np.array_equal(np.any(xs != 0, axis=(1, 2)), reached)
         assert np.abs(xs[reached] - oxs[reached]).max() < 1e-9
         assert np.abs(vs[reached] - ovs[reached]).max() < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parareal_resumes_from_a_checkpoint_bit_for_bit(api, torch, pr_sys, prec):
+    """Checkpoint and resume: the iterate after k iterations (what parareal_run
+    returns when max_iter stops it), fed back with k, continues to exactly the
+    iterates of one uninterrupted run; so does a second resume, and a resume of a
+    finished run changes nothing."""
+    s = pr_sys
+    n_slices = 5
+    whole = api.parareal_run(COARSE, FINE, s, n_slices, 4, 0.0, precision=prec)
+    part = api.parareal_run(COARSE, FINE, s, n_slices, 2, 0.0, precision=prec)
+    assert part[2] == 2
+    xs, vs = part[0].copy(), part[1].copy()                   # the checkpoint, as a caller would keep it
+    r1 = api.parareal_run(COARSE, FINE, s, n_slices, 1, 0.0, precision=prec, resume=(xs, vs, 2))
+    assert r1[2] == 3
+    r2 = api.parareal_run(COARSE, FINE, s, n_slices, 1, 0.0, precision=prec, resume=(r1[0], r1[1], 3))
+    assert r2[2] == 4
+    assert np.array_equal(r2[0], whole[0]) and np.array_equal(r2[1], whole[1])
+    assert r2[3] == whole[3]
+    done = api.parareal_run(COARSE, FINE, s, n_slices, n_slices, 0.0, precision=prec)
+    again = api.parareal_run(COARSE, FINE, s, n_slices, 3, 0.0, precision=prec,
+                             resume=(done[0], done[1], n_slices))
+    assert again[2] == n_slices + 1 and again[4]
+    assert np.array_equal(again[0], done[0]) and np.array_equal(again[1], done[1])

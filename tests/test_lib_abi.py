@@ -129,3 +129,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     want = [C.sizeof(api.Params)] + [getattr(api.Params, f).offset for f in fields_p]
     want += [C.sizeof(api.SystemC)] + [getattr(api.SystemC, f).offset for f in fields_s]
     assert got == want
+
+
+def test_device_budget_round_trip(L):
+    """The budget call needs no GPU: it sets or clears the cap and reports the bytes held."""
+    assert L.msm_set_device_budget(1 << 20) == 0
+    assert L.msm_set_device_budget(0) == 0
