@@ -451,6 +451,7 @@ def run_ours(a):
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                                     "(max SM clock from MEASURED_PEAKS.json)",
                      "work": f"{pairs} ordered pairs within a per launch x {FLOPS_PER_PAIR} flops",
+                     "pairs_per_s": pairs / sr_avg_s, "unique_pairs_per_s": 0.5 * pairs / sr_avg_s,
                      "duration": f"{sr_avg_s * 1e3:.4f} ms average of {sr_n} launches (CUDA events on the "
                                  f"launching stream, {a.profile_steps} eager steps continuing the timed run)"},
         "roofline_lattice_cutoff": {"bound": "alu", "achieved": st_achieved, "peak": peak_tflops, "unit": "TFLOP/s",

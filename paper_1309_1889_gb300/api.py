@@ -490,8 +490,18 @@ def set_device_budget(nbytes: int) -> int:
 # ----------------------------------------------------------------- autograd
 
 def msm_energy(pos, q, box, msm: MSM):
-    """U(pos, q) as a differentiable torch scalar; backward gives dU/dpos = -F and dU/dq = phi."""
+    """U(pos, q) as a differentiable torch scalar; backward gives dU/dpos = -F and dU/dq = phi.
+    The forward asks the library only for what the backward will need: forces if pos
+    requires a gradient, potentials if q does."""
     return _MSMEnergy.apply(pos, q, box, msm)
+
+
+def msm_energy_batched(offsets, pos, q, boxes, msm: MSM):
+    """Energies of independent systems of uneven sizes from one batched evaluation
+    (systems b = offsets[b] .. offsets[b+1] of pos (N, 3) and q (N,), box b = boxes[b]),
+    as a differentiable torch tensor (B,); backward gives each system's dU_b/dpos = -F
+    and dU_b/dq = phi, scaled by that system's incoming gradient."""
+    return _MSMEnergyBatched.apply(pos, q, offsets, boxes, msm)
 
 
 def _make_function():
@@ -509,16 +519,42 @@ def _make_function():
 
         @staticmethod
         def forward(ctx, pos, q, box, msm):
-            e, f, p = msm.energy_forces(pos.detach().contiguous(), q.detach().contiguous(), box)
-            ctx.save_for_backward(f, p)
+            need_f, need_p = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+            e, f, p = msm.energy_forces(pos.detach().contiguous(), q.detach().contiguous(), box,
+                                        forces=need_f, potentials=need_p)
+            ctx.save_for_backward(f if need_f else None, p if need_p else None)
             return e.reshape(())
 
         @staticmethod
         def backward(ctx, g):
             f, p = ctx.saved_tensors
-            return -g * f, g * p, None, None
+            return (-g * f if f is not None else None), (g * p if p is not None else None), None, None
 
     return MSMEnergyFn
+
+
+def _make_batched_function():
+    torch = _torch()
+
+    class MSMEnergyBatchedFn(torch.autograd.Function):
+        """Forward: one batched evaluation of B independent systems (energies (B,)).
+        Backward: system b's atoms get -g_b F_i (pos) and g_b phi_i (q)."""
+
+        @staticmethod
+        def forward(ctx, pos, q, offsets, boxes, msm):
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            e, f, p = msm.energy_forces_batched(off, pos.detach().contiguous(), q.detach().contiguous(), boxes)
+            counts = torch.as_tensor(np.diff(off), device=pos.device)
+            ctx.save_for_backward(f, p, counts)
+            return e
+
+        @staticmethod
+        def backward(ctx, g):
+            f, p, counts = ctx.saved_tensors
+            ga = torch.repeat_interleave(g, counts)               # each atom: its system's gradient
+            return -ga[:, None] * f, ga * p, None, None, None
+
+    return MSMEnergyBatchedFn
 
 
 class _Lazy:
@@ -531,3 +567,15 @@ class _Lazy:
 
 
 _MSMEnergy = _Lazy()
+
+
+class _LazyBatched:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyBatched._fn is None:
+            _LazyBatched._fn = _make_batched_function()
+        return _LazyBatched._fn.apply(*args)
+
+
+_MSMEnergyBatched = _LazyBatched()

@@ -87,3 +87,43 @@ def test_gradients_match_finite_differences_and_oracle(api, torch, water100k):
     # dU/dq against the oracle's potentials
     dq = q.grad.cpu().numpy()
     assert np.sqrt(((dq - ref["pot"]) ** 2).sum() / (ref["pot"] ** 2).sum()) < 1e-4
+
+
+def test_forward_computes_only_what_backward_needs(api, torch):
+    """Only positions need a gradient: the energy is the same bits, pos.grad is -F and
+    q gets no gradient; only charges: q.grad is phi."""
+    s = inputs.water_box(900, 2.0, margin=0.5, with_velocities=False)
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    e, f, p = m.energy_forces(torch.tensor(s.pos, device="cuda"), torch.tensor(s.q, device="cuda"), s.box)
+    pos = torch.tensor(s.pos, device="cuda", requires_grad=True)
+    q = torch.tensor(s.q, device="cuda")
+    U = api.msm_energy(pos, q, s.box, m)
+    U.backward()
+    assert float(U.detach()) == float(e) and torch.equal(pos.grad, -f) and q.grad is None
+    pos = torch.tensor(s.pos, device="cuda")
+    q = torch.tensor(s.q, device="cuda", requires_grad=True)
+    U = api.msm_energy(pos, q, s.box, m)
+    U.backward()
+    assert float(U.detach()) == float(e) and torch.equal(q.grad, p)
+
+
+def test_batched_energies_differentiate_per_system(api, torch):
+    """Three uneven systems in one batched evaluation: energies (B,) equal single
+    evaluations bit for bit, and a weighted sum sum_b w_b U_b gives each system's
+    atoms -w_b F and w_b phi."""
+    systems = [inputs.random_cloud(n, L, seed=70 + k, neutral=True, margin=0.3)
+               for k, (n, L) in enumerate(((500, 2.2), (1300, 3.0), (800, 2.6)))]
+    m = api.MSM(a=A, h=H, levels=3, precision="fp32")
+    offsets = np.cumsum([0] + [s.n for s in systems])
+    pos = torch.tensor(np.concatenate([s.pos for s in systems]), device="cuda", requires_grad=True)
+    q = torch.tensor(np.concatenate([s.q for s in systems]), device="cuda", requires_grad=True)
+    boxes = np.stack([np.asarray(s.box, dtype=np.float64) for s in systems])
+    U = api.msm_energy_batched(offsets, pos, q, boxes, m)
+    w = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64, device="cuda")
+    (w * U).sum().backward()
+    for b, s in enumerate(systems):
+        e, f, p = api.MSM(a=A, h=H, levels=3, precision="fp32").energy_forces(
+            torch.tensor(s.pos, device="cuda"), torch.tensor(s.q, device="cuda"), s.box)
+        o0, o1 = offsets[b], offsets[b + 1]
+        assert float(U[b].detach()) == float(e)
+        assert torch.equal(pos.grad[o0:o1], -w[b] * f) and torch.equal(q.grad[o0:o1], w[b] * p)
