@@ -121,3 +121,38 @@ def test_mts_needs_whole_outer_steps_and_the_msm(api, torch, small_water):
         m.md_run(d, dt=0.002, n_steps=5)
     with pytest.raises(api.MSMError):
         api.MSM(a=A, h=H, levels=1, precision="fp32", model="water", mts=2, method="cutoff")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_mts_with_verlet_lists_equals_cell_search(api, torch, prec, tol):
+    """The fast steps' short-range sum from Verlet lists (skin 0.1 nm) follows the
+    every-step cell search to rounding under multiple time stepping too."""
+    s = inputs.water_box(3000, 3.1, margin=1.0, seed=7, vel_seed=8)
+    out = {}
+    for skin in (0.0, 0.1):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water", mts=3, list_skin=skin,
+                    wall_k=1e4, wall_width=0.8)
+        d = _dev_sys(torch, s)
+        uk = m.md_run(d, dt=0.002, n_steps=30).cpu().numpy()
+        out[skin] = (d.pos.cpu().numpy(), uk)
+    assert np.abs(out[0.0][0] - out[0.1][0]).max() <= tol
+    assert np.abs(out[0.0][1] - out[0.1][1]).max() <= 10 * tol * np.abs(out[0.0][1]).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parareal_with_a_multiple_time_step_fine_propagator(api, torch, prec):
+    """Parareal (Sec. 4) around a fine propagator that itself steps the grid part every
+    second step: after as many iterations as slices the result is the serial
+    multiple-time-step run, bit for bit."""
+    s = inputs.water_box(45, 0.8, margin=0.5, seed=5, vel_seed=6)
+    fine = dict(a=1.2, h=0.25, levels=2, dt=0.002, steps=4, mts=2)
+    coarse = dict(a=0.8, h=0.5, levels=2, dt=0.004, steps=2)
+    n_slices = 3
+    m = api.MSM(a=1.2, h=0.25, levels=2, precision=prec, model="water", mts=2)
+    d = _dev_sys(torch, s)
+    xs_ref = [d.pos.cpu().numpy().copy()]
+    for _ in range(n_slices):
+        m.md_run(d, dt=0.002, n_steps=4, record=False)
+        xs_ref.append(d.pos.cpu().numpy().copy())
+    xs, vs, it, dx, conv = api.parareal_run(coarse, fine, s, n_slices, n_slices, 0.0, precision=prec)
+    assert np.array_equal(xs, np.array(xs_ref))
