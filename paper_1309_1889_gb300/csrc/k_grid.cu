@@ -280,22 +280,14 @@ int stencil_plane_values(const LevelGeom &L, int rad)
 // Values of one plane row in registers: ST_RX + 2 st_radp(RAD).
 template <int RAD> struct StRow { static constexpr int N = st_up4(ST_RX + 2 * st_radp(RAD)); };
 
-// acc[r] += sum_{|d| <= W} w[|d|] v[r + d + st_radp(RAD)]
+// acc[r] += sum_{|d| <= W} w[|d|] v[r + d + st_radp(RAD)]; w: the octant row |dx| = 0..RAD of
+// the tap row, already in registers (loaded with the plane rows, before the switch on W)
+template <int RAD> struct StW { static constexpr int N = st_r1p(RAD); };
+
 template <int W, int RAD, typename T>
-__device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T *__restrict__ wr, T (&acc)[ST_RX])
+__device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T (&w)[StW<RAD>::N], T (&acc)[ST_RX])
 {
-    constexpr int NW = st_up4(W + 1), RP = st_radp(RAD);
-    T w[NW];                                                   // octant row |dx| = 0..W (16-byte aligned)
-    if (sizeof(T) == sizeof(float)) {
-#pragma unroll
-        for (int k = 0; k < NW; k += 4) {
-            const float4 f = *reinterpret_cast<const float4 *>(wr + k);
-            w[k] = f.x; w[k + 1] = f.y; w[k + 2] = f.z; w[k + 3] = f.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k <= W; k++) w[k] = wr[k];
-    }
+    constexpr int RP = st_radp(RAD);
 #pragma unroll
     for (int d = -W; d <= W; d++) {
 #pragma unroll
@@ -304,7 +296,8 @@ __device__ __forceinline__ void stencil_row(const T (&v)[StRow<RAD>::N], const T
 }
 
 template <int RAD, typename T>
-__device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<RAD>::N], const T *wr, T (&acc)[ST_RX])
+__device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<RAD>::N], const T (&wr)[StW<RAD>::N],
+                                                     T (&acc)[ST_RX])
 {
     switch (w) {
 #define ST_CASE(k) case k: if (k <= RAD) stencil_row<(k <= RAD ? k : 0), RAD>(v, wr, acc); break;
@@ -312,6 +305,22 @@ __device__ __forceinline__ void stencil_row_dispatch(int w, const T (&v)[StRow<R
     ST_CASE(7) ST_CASE(8) ST_CASE(9) ST_CASE(10) ST_CASE(11) ST_CASE(12)
 #undef ST_CASE
     default: break;
+    }
+}
+
+// A weight row (st_r1p values, 16-byte aligned) from shared memory into registers.
+template <int RAD, typename T>
+__device__ __forceinline__ void st_load_w(const T *__restrict__ wr, T (&w)[StW<RAD>::N])
+{
+    if (sizeof(T) == sizeof(float)) {
+#pragma unroll
+        for (int k = 0; k < StW<RAD>::N; k += 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(wr + k);
+            w[k] = f.x; w[k + 1] = f.y; w[k + 2] = f.z; w[k + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < StW<RAD>::N; k++) w[k] = wr[k];
     }
 }
 
@@ -440,10 +449,27 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const __grid_constant__ Stenc
             phase[bi] ^= 1u;
             if (active) {
                 // W depends on |dy|: rows y + dy and y - dy are added once and share
-                // the tap row of (|dz|, |dy|) for both output planes
+                // the tap row of (|dz|, |dy|) for both output planes.  Every shared-memory
+                // read of an iteration (the two half-widths, the two weight rows, the two
+                // plane rows) is issued before the first multiply-add needs one of them.
+                int adz_s[ST_RZ];
+                bool on_s[ST_RZ];
+#pragma unroll
+                for (int s = 0; s < ST_RZ; s++) {
+                    const int dz = zp - (z0 + s);
+                    on_s[s] = dz >= -RAD && dz <= RAD;
+                    adz_s[s] = on_s[s] ? (dz < 0 ? -dz : dz) : 0;
+                }
 #pragma unroll 1
                 for (int ady = 0; ady <= RAD; ady++) {
                     constexpr int NV = StRow<RAD>::N;
+                    int wsel[ST_RZ];
+                    T wrow[ST_RZ][StW<RAD>::N];
+#pragma unroll
+                    for (int s = 0; s < ST_RZ; s++) {
+                        wsel[s] = on_s[s] ? hw[adz_s[s] * R1 + ady] : -1;
+                        st_load_w<RAD>(wt + (adz_s[s] * R1 + ady) * R1P, wrow[s]);
+                    }
                     T v[NV];
                     const T *row = cur + (yr + RAD + ady) * PX + xg * ST_RX;      // 16-byte aligned
                     const T *mir = cur + (yr + RAD - ady) * PX + xg * ST_RX;
@@ -465,14 +491,8 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const __grid_constant__ Stenc
                         for (int i = 0; i < NV; i++) v[i] = ady > 0 ? row[i] + mir[i] : row[i];
                     }
 #pragma unroll
-                    for (int s = 0; s < ST_RZ; s++) {
-                        const int dz = zp - (z0 + s);
-                        if (dz < -RAD || dz > RAD) continue;
-                        const int adz = dz < 0 ? -dz : dz;
-                        const int w = hw[adz * R1 + ady];
-                        if (w < 0) continue;
-                        stencil_row_dispatch<RAD>(w, v, wt + (adz * R1 + ady) * R1P, acc[s]);
-                    }
+                    for (int s = 0; s < ST_RZ; s++)
+                        if (wsel[s] >= 0) stencil_row_dispatch<RAD>(wsel[s], v, wrow[s], acc[s]);
                 }
             }
             __syncthreads();                          // the buffer is refilled two planes on
