@@ -221,9 +221,15 @@ int launch_stencil_table(double a, double h, int rad, double *wd, cudaStream_t s
 // of the sphere with compile-time offsets: half the multiply-adds of walking
 // every row.  The weights W[n] = g^0(|n| h) depend on |n| only, so one octant of
 // the table sits in shared memory; the level factor 2^{-k} is applied at the
-// end.  CTAs take tiles from a counter.  Each output sums its taps in a fixed
-// order (planes, row pairs, then x offsets), whatever the tile shape.
+// end.  A tile's input planes are split in two halves (the first rad + ST_RZ/2
+// planes and the rest), taken by two CTAs: twice the warps per SM to hide the
+// shared-load latency, with no extra plane traffic.  Each half adds its scaled
+// partial sum into the zeroed output by an atomic add; with exactly two addends
+// onto zero the result does not depend on which lands first (IEEE addition
+// commutes).  CTAs take tile halves from a counter.  Each half sums its taps in
+// a fixed order (planes, row pairs, then x offsets), whatever the tile shape.
 constexpr int ST_RX = 8, ST_RZ = 2, ST_NT = 128, ST_MAXGX = 16;
+constexpr int ST_SPLIT = 2;         // plane halves per tile (two addends: order-free)
 constexpr int ST_MAXRAD = 12;
 constexpr int ST_MAXMAPS = 24;      // descriptors per launch (kernel parameter: 24 x 128 bytes)
 constexpr long ST_WAIT_POLLS = 1L << 22;
@@ -414,16 +420,33 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const __grid_constant__ Stenc
         const int PX = st_bx(tg.tgx, RAD);
         const uint32_t bytes = (uint32_t)(sizeof(T) * PX * st_by(tg.tgx, RAD));
         const CUtensorMap *map = &M.map[ent - M.e0];
-        const int b = tile - A.blk_off[ent];
+        const int part = (tile - A.blk_off[ent]) % ST_SPLIT, b = (tile - A.blk_off[ent]) / ST_SPLIT;
         const int tx = b % tg.ntx, ty = (b / tg.ntx) % tg.nty, tz = b / (tg.ntx * tg.nty);
         const int x0 = tx * tg.tgx * ST_RX, y0 = ty * tg.tyr, z0 = tz * ST_RZ;
-        // consecutive lanes take consecutive rows: the box width is an odd number of
-        // 16-byte granules, so their row loads fall in different banks
-        const int yr = t % tg.tyr, xg = t / tg.tyr;
+        // A 16-byte shared load of a warp is served eight lanes at a time.  Eight
+        // consecutive lanes take eight consecutive rows of one x group: the box
+        // width is an odd number of 16-byte granules, so their row loads fall in
+        // different banks.  The tyr % 8 rows left over per x group come last, two
+        // rows of four x groups per eight lanes when two are left (distinct banks
+        // again).  Which thread owns an output changes nothing in its sum.
+        const int full = tg.tyr & ~7, rem = tg.tyr - full, nblk = (full >> 3) * tg.tgx;
+        int yr, xg;
+        if (t < 8 * nblk) {
+            xg = (t >> 3) % tg.tgx;
+            yr = ((t >> 3) / tg.tgx) * 8 + (t & 7);
+        } else if (rem > 0) {
+            xg = (t - 8 * nblk) / rem;
+            yr = full + (t - 8 * nblk) % rem;
+        } else {
+            xg = tg.tgx;
+            yr = 0;
+        }
         const bool active = xg < tg.tgx;
         const int ny = L.n[1], nz = L.n[2];
-        // planes that exist: z' in [zb, ze)
-        const int zb = max(z0 - RAD, 0), ze = min(z0 + ST_RZ + RAD, nz);
+        // this half's planes that exist: z' in [zb, ze)
+        constexpr int ZH = RAD + ST_RZ / 2;
+        const int zlo = z0 - RAD + part * ZH, zhi = part == ST_SPLIT - 1 ? z0 + ST_RZ + RAD : zlo + ZH;
+        const int zb = max(zlo, 0), ze = min(zhi, nz);
         T acc[ST_RZ][ST_RX];
 #pragma unroll
         for (int s = 0; s < ST_RZ; s++)
@@ -508,7 +531,7 @@ __global__ void __launch_bounds__(ST_NT) k_stencil(const __grid_constant__ Stenc
 #pragma unroll
                 for (int r = 0; r < ST_RX; r++) {
                     const int gx = x0 + xg * ST_RX + r;
-                    if (gx < L.n[0]) out[gx] = scale * acc[s][r];
+                    if (gx < L.n[0]) atomicAdd(out + gx, scale * acc[s][r]);
                 }
             }
         }
@@ -571,6 +594,7 @@ static int launch_stencil_rad(const StencilArgs<T> &a, const CUtensorMap *maps, 
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil<T, RAD>, ST_NT, smem));
     if (per_sm < 1) return fail_msg(MSM_EINVAL, "lattice-cutoff tile does not fit (radius %d)", RAD);
     const int nent = a.bt.B * a.nlev;
+    CUDA_TRY(cudaMemsetAsync(a.ucut, 0, sizeof(T) * a.ucut_len, st));
     for (int e0 = 0; e0 < nent; e0 += ST_MAXMAPS) {
         StMaps m;
         m.e0 = e0;
@@ -606,7 +630,7 @@ int launch_stencil(const StencilArgs<T> &a, const CUtensorMap *maps, const int *
 int stencil_tile_count(const LevelGeom &L)
 {
     const StTile t = st_tile(L);
-    return t.ntx * t.nty * t.ntz;
+    return t.ntx * t.nty * t.ntz * ST_SPLIT;
 }
 
 // ------------------------------------------------------------------ top level

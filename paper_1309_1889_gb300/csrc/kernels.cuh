@@ -151,6 +151,7 @@ template <typename T> struct StencilArgs {
     const int4 *rows;      // (dy, dz, half-width, 0) of each non-empty row
     const T *q;            // concatenated grids
     T *ucut;               // concatenated, levels < nlev
+    size_t ucut_len;       // values of ucut zeroed before the two plane halves of each tile add into it
     const int *status;
 };
 // maps: one TMA descriptor per (system, level) entry of the batch (encode_stencil_maps);

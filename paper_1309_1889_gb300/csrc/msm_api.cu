@@ -958,7 +958,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         if (l > 1) {
             StencilArgs<T> sa;
             sa.bt = bt; sa.nlev = l - 1; sa.blk_off = h->blk_buf.as<int>(); sa.total_tiles = h->stiles; sa.sg = h->sg;
-            sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.status = status;
+            sa.w = h->wst_t.as<T>(); sa.rows = h->rows.as<int4>(); sa.q = qg; sa.ucut = uc; sa.ucut_len = (size_t)h->G;
+            sa.status = status;
             PROF(ST_STENCIL);
             TRY(launch_stencil<T>(sa, h->st_maps.data(), h->h_blk.data(), h->status.as<int>() + 2, st));
         }
