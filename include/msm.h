@@ -85,6 +85,12 @@ extern "C" {
                                 passes take their queued neighbours one at a time instead
                                 of two per packed FP32x2 step; the same bits, slower (off
                                 by default)                                                */
+#define MSM_FLAG_CLUSTER_PAIRS 8  /* FP32, MSM or simple cutoff: the short-range Coulomb pass
+                                on cluster pairs (8 i atoms x 4 j atoms from columns of
+                                2 x 2 cells, clusters culled by bounding box) instead of
+                                cell bricks; the same sums in another order: agrees with
+                                the brick pass to rounding, not bitwise; ignored for FP64,
+                                Wolf summation and MSM_FLAG_SCALAR_PAIRS                    */
 
 /* Method parameters (Sec. 3).
  *   a          cutoff of the short-range part g* (nm); the level-k lattice

@@ -114,6 +114,9 @@ struct SysDesc {
     int cell_off;       // global id of its first cell (cell_start index)
     int bd[3], nb[3], nbricks;   // short-range bricks: edge in cells, count per axis
     int lj_bd[3], lj_nb[3], lj_nbricks;   // bricks of the LJ-site pass (water completion)
+    int cp_nc[2];       // cluster-pair columns of 2 x 2 cells per axis (x, y)
+    int col_off;        // global index of its first column
+    int zc_off;         // first entry of its columns' layer-prefix tables (nc[2] + 1 per column)
     int grid_off;       // first point of its grids in the concatenated grid buffers
     int top_off;        // first point of its top level in the FP64 top buffer
     int ttab_off;       // first entry of its top-level Toeplitz table

@@ -88,6 +88,38 @@ template <typename T> int launch_lj_compact(int m_total, const int *start, const
                                             int *lj_perm, const int *status, cudaStream_t st);
 template <typename T> int launch_count_pairs(const ShortArgs<T> &a, cudaStream_t st);
 
+// ---- cluster pairs (k_cluster.cu, FP32) -------------------------------------
+// Columns of 2 x 2 finest cells per system (SysDesc::cp_nc, col_off, zc_off);
+// clusters of 4 atoms in column order, two per i cluster of 8.
+struct ClusterArgs {
+    Batch bt;
+    int max_cols;          // columns of the largest system
+    int n_cols;            // columns over all systems
+    int max_icl;           // bound on the i clusters of the largest system (n/8 + columns)
+    const int *start;      // global cell_start
+    const vec4<float> *apos;
+    const int *aflag;
+    const int *perm;
+    int *col_n;            // n_cols: clusters of 4 per column (even)
+    int *col_cl;           // n_cols + 1: first cluster of 4 of each column (scan of col_n)
+    int *bsum;             // scan scratch (scan_scratch_ints(n_cols))
+    int *zc;               // per column, nz + 1 entries: atoms of the column below cell layer z
+    vec4<float> *cpos;     // 4 per cluster: (x, y, z, q), padding (-1000, -1000, -1000, 0)
+    int *cmol;             // 4 per cluster: molecule id (water model), padding -2
+    int *cslot;            // 4 per cluster: sorted slot, padding -1
+    vec4<float> *cbox;     // 2 per cluster: low and high corner of its atoms
+    float a, a2, a_sel;
+    float c0, c1, c2, d0, d1;   // as ShortArgs
+    vec4<float> *sr;       // by atom: (F_x, F_y, F_z, phi) of the g* sum, before k_e
+    vec4<float> *lj;       // water model: zeroed for atoms that are not LJ sites
+    const int *vl_ctl;
+    const int *status;
+};
+// k_cp_count, the scan of the column counts, k_cp_fill
+int launch_cluster_build(const ClusterArgs &a, bool model, cudaStream_t st);
+// the Coulomb pass on cluster pairs (model: rigid-water exclusions, as launch_short)
+int launch_cluster_short(const ClusterArgs &a, bool model, cudaStream_t st);
+
 // ---- Verlet lists (k_list.cu, single systems) -----------------------------
 constexpr int VL_ROWS = 512;       // candidate rows per brick (9 bits of an entry)
 constexpr int VL_OFFS = 128;       // atoms per row segment (7 bits of an entry)

@@ -237,6 +237,10 @@ struct msm_handle {
     long long g_kernels = 0;                            // kernels per replayed step
     // Verlet lists (md_run with list_skin > 0, single systems)
     bool list_on = false;
+    // cluster pairs (MSM_FLAG_CLUSTER_PAIRS)
+    bool cp_on = false;
+    int cp_cols = 0, cp_max_cols = 0, cp_max_icl = 0;
+    DevBuf cp_coln, cp_colcl, cp_bsum, cp_zc, cp_pos, cp_mol, cp_slot, cp_box;
     DevBuf vl_perm, vl_start, vl_xref, vl_pos, vl_rtab, vl_rtn, vl_cnt, vl_cntlj, vl_nbr, vl_nbr_lj, vl_ctl;
     int vl_cap = 0, vl_cap_lj = 0, vl_nbricks = 0;
     int64_t vl_key_n = -1, vl_key_nmol = -1;
@@ -330,7 +334,7 @@ static int check_params(const msm_params *p)
     if (p->precision != MSM_FP32 && p->precision != MSM_FP64) return fail_msg(MSM_EINVAL, "unknown precision");
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
-    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE | MSM_FLAG_SCALAR_PAIRS))
+    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE | MSM_FLAG_SCALAR_PAIRS | MSM_FLAG_CLUSTER_PAIRS))
         return fail_msg(MSM_EINVAL, "unknown flags");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
@@ -385,7 +389,9 @@ extern "C" void msm_destroy(msm_handle *h)
                      &h->md_x, &h->md_v, &h->md_q, &h->md_m, &h->md_lj, &h->md_uk, &h->md_im,
                      &h->md_fs, &h->eslow,
                      &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->vl_rtab, &h->vl_rtn,
-                     &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_nbr_lj, &h->vl_ctl};
+                     &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_nbr_lj, &h->vl_ctl,
+                     &h->cp_coln, &h->cp_colcl, &h->cp_bsum, &h->cp_zc, &h->cp_pos, &h->cp_mol, &h->cp_slot,
+                     &h->cp_box};
     for (DevBuf *b : all) release(*b);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -502,6 +508,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     std::vector<SysDesc> d((size_t)B);
     std::vector<std::array<int, 4>> tops;          // (nx, ny, nz, table offset)
     int64_t N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, ST = 0;
+    int64_t CC = 0, CZ = 0, CK = 0, CI = 0, CMAX = 0;    // cluster pairs: columns, layer tables, clusters of 4
     bool pending = false;
     h->h_blk.clear();
     for (int s = 0; s < B; s++) {
@@ -564,6 +571,18 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         N += S.n;
         D.cell_off = (int)M;
         M += ncells;
+        D.cp_nc[0] = (D.g.nc[0] + 1) / 2;
+        D.cp_nc[1] = (D.g.nc[1] + 1) / 2;
+        {
+            const int64_t nco = (int64_t)D.cp_nc[0] * D.cp_nc[1], n = (int64_t)S.n;
+            D.col_off = (int)CC;
+            D.zc_off = (int)CZ;
+            CC += nco;
+            CZ += nco * (D.g.nc[2] + 1);
+            CK += n / 4 + 2 * nco;                         // clusters of 4: at most n/4 + 2 per column
+            CI = std::max(CI, n / 8 + nco);                 // i clusters: at most n/8 + 1 per column
+            CMAX = std::max(CMAX, nco);
+        }
         const Tuned *t = (h->p.flags & MSM_FLAG_AUTOTUNE) ? find_tuned(h, S.n, D.g) : nullptr;
         if (t) set_bricks(D, t->bd);
         else {
@@ -599,7 +618,8 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     }
     h->h_blk.push_back((int)ST);
     const int64_t lim = ((int64_t)1 << 31) - 1;
-    if (N > ((int64_t)1 << 30) || M >= lim || G >= lim || UT >= lim || TT >= lim || ST >= lim)
+    if (N > ((int64_t)1 << 30) || M >= lim || G >= lim || UT >= lim || TT >= lim || ST >= lim || CZ >= lim ||
+        4 * CK >= lim)
         return fail_msg(MSM_EINVAL, "batch too large for 32-bit offsets");
 
     const size_t ts = h->precision == MSM_FP32 ? sizeof(float) : sizeof(double);
@@ -610,6 +630,18 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         TRY(ensure(h->lj_start, sizeof(int) * (size_t)(M + 1)));
     }
     TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints((int)M)));
+    h->cp_on = (h->p.flags & MSM_FLAG_CLUSTER_PAIRS) && h->precision == MSM_FP32 &&
+               h->p.method != MSM_METHOD_WOLF && !(h->p.flags & MSM_FLAG_SCALAR_PAIRS);
+    if (h->cp_on) {
+        TRY(ensure(h->cp_coln, sizeof(int) * (size_t)(CC + 1)));
+        TRY(ensure(h->cp_colcl, sizeof(int) * (size_t)(CC + 1)));
+        TRY(ensure(h->cp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)CC)));
+        TRY(ensure(h->cp_zc, sizeof(int) * (size_t)CZ));
+        TRY(ensure(h->cp_pos, sizeof(float) * 16 * (size_t)CK));
+        TRY(ensure(h->cp_mol, sizeof(int) * 4 * (size_t)CK));
+        TRY(ensure(h->cp_slot, sizeof(int) * 4 * (size_t)CK));
+        TRY(ensure(h->cp_box, sizeof(float) * 8 * (size_t)CK));
+    }
     TRY(ensure(h->qgrid, ts * (size_t)G));
     TRY(ensure(h->ucut, ts * (size_t)G));
     TRY(ensure(h->ugrid, ts * (size_t)G));
@@ -680,6 +712,9 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     h->B = B;
     h->N = (int)N; h->M = (int)M; h->G = (int)G; h->UT = (int)UT; h->TT = (int)TT; h->PB = (int)PB;
     h->stiles = (int)ST;
+    h->cp_cols = (int)CC;
+    h->cp_max_cols = (int)CMAX;
+    h->cp_max_icl = (int)CI;
     h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = h->max_lj_bricks = 0;
     for (int k = 0; k < MSM_MAX_LEVELS; k++) h->max_lev[k] = 0;
     for (const SysDesc &D : h->hsd) {
@@ -768,6 +803,23 @@ static ShortArgs<T> short_args(msm_handle *h)
     s.status = h->status.as<int>();
     s.scalar_pairs = (h->p.flags & MSM_FLAG_SCALAR_PAIRS) != 0;
     return s;
+}
+
+// Arguments of the cluster-pair kernels: the short-range constants and outputs of s.
+static ClusterArgs cluster_args(msm_handle *h, const ShortArgs<float> &s)
+{
+    ClusterArgs c;
+    c.bt = s.bt;
+    c.max_cols = h->cp_max_cols; c.n_cols = h->cp_cols; c.max_icl = h->cp_max_icl;
+    c.start = s.start; c.apos = s.apos; c.aflag = s.aflag; c.perm = s.perm;
+    c.col_n = h->cp_coln.as<int>(); c.col_cl = h->cp_colcl.as<int>(); c.bsum = h->cp_bsum.as<int>();
+    c.zc = h->cp_zc.as<int>();
+    c.cpos = h->cp_pos.as<vec4<float>>(); c.cmol = h->cp_mol.as<int>(); c.cslot = h->cp_slot.as<int>();
+    c.cbox = h->cp_box.as<vec4<float>>();
+    c.a = s.a; c.a2 = s.a2; c.a_sel = s.a_sel;
+    c.c0 = s.c0; c.c1 = s.c1; c.c2 = s.c2; c.d0 = s.d0; c.d1 = s.d1;
+    c.sr = s.sr; c.lj = s.lj; c.vl_ctl = s.vl_ctl; c.status = s.status;
+    return c;
 }
 
 // The brick autotuner: on the first evaluation of a geometry, time the
@@ -1010,7 +1062,17 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
         {
             PROF(ST_SHORT);
             if (h->list_on) TRY(launch_list_force<T>(la, st));
-            TRY(launch_short<T>(s, model, st));
+            if constexpr (sizeof(T) == sizeof(float)) {
+                if (h->cp_on) {
+                    const ClusterArgs ca = cluster_args(h, s);
+                    TRY(launch_cluster_build(ca, model, st));
+                    TRY(launch_cluster_short(ca, model, st));
+                } else {
+                    TRY(launch_short<T>(s, model, st));
+                }
+            } else {
+                TRY(launch_short<T>(s, model, st));
+            }
         }
         if (model) {
             PROF(ST_LJ);
