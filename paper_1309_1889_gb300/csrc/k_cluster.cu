@@ -20,8 +20,9 @@
 // lies within a of its box, and for each the run of clusters covering the cell
 // layers within reach (one candidate column per lane, runs compacted by
 // ballot), then walks the runs 32 clusters at a time, one per lane: a cluster
-// whose box lies at least a from the i cluster's box is dropped, the rest enter
-// a 64-cluster FIFO in shared memory, drained 8 at a time.  In a drain, lane
+// whose box lies at least a from the i cluster's box is dropped, the atoms of
+// the rest are loaded by groups of four lanes (eight clusters per load) into a
+// 64-cluster FIFO in shared memory, drained 8 at a time.  In a drain, lane
 // (i, js) takes atom js of each queued cluster, two clusters per packed FP32x2
 // step (the operations of k_short's packed pair step).  Pairs beyond a, the
 // pair j = i and pairs inside one rigid molecule get charge zero, never a
@@ -147,6 +148,7 @@ struct CpSmem {
     // bank offsets, so the 32 lanes storing 32 consecutive clusters hit 32 banks.
     float sp[32 * CP_SP];
     int sf[32 * CP_SF];
+    int kj[32];                     // this round's kept clusters, in order
 };
 
 // npair pair blocks from P (stride CP_SP floats) and F (stride CP_SF ints) for
@@ -275,23 +277,18 @@ __global__ void __launch_bounds__(32, 32) k_cp_short(const ClusterArgs A)
             r_next += 32;
         }
         __syncwarp();
-        // ---- the segment's clusters 32 at a time, one per lane: its box and its four
-        // atoms are loaded together (no dependent round trip), the box test decides
-        // whether the cluster is queued
+        // ---- the segment's clusters 32 at a time, one per lane for the box test; the
+        // atoms of the kept clusters are then loaded by groups of four lanes, eight
+        // clusters per load instruction (runs are contiguous: few cache lines per load)
         int rc = 0;
         for (int cb = 0; cb < total; cb += 32) {
             const int want = cb + lane;
             bool keep = false;
-            float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0, p2 = p0, p3 = p0;
-            int4 f4 = make_int4(0, 0, 0, 0);
-            int row = rc;
+            int J = 0, row = rc;
             if (want < total) {
                 while (S.rend[row] <= want) row++;
-                const int J = S.rs0[row] + (want - (row ? S.rend[row - 1] : 0));
-                const float4 *P = reinterpret_cast<const float4 *>(A.cpos + 4 * (size_t)J);
+                J = S.rs0[row] + (want - (row ? S.rend[row - 1] : 0));
                 const vec4<float> jl = A.cbox[2 * (size_t)J], jh = A.cbox[2 * (size_t)J + 1];
-                p0 = P[0]; p1 = P[1]; p2 = P[2]; p3 = P[3];
-                if (MODEL) f4 = *reinterpret_cast<const int4 *>(A.cmol + 4 * (size_t)J);
                 const float ex = fmaxf(0.f, fmaxf(jl.x - hi[0], lo[0] - jh.x));
                 const float ey = fmaxf(0.f, fmaxf(jl.y - hi[1], lo[1] - jh.y));
                 const float ez = fmaxf(0.f, fmaxf(jl.z - hi[2], lo[2] - jh.z));
@@ -300,22 +297,36 @@ __global__ void __launch_bounds__(32, 32) k_cp_short(const ClusterArgs A)
             rc = __shfl_sync(0xffffffffu, row, 31);             // run of cluster cb + 31
             if (rc < nruns - 1 && S.rend[rc] <= cb + 32) rc++;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int q = (head + npend + __popc(m & lt)) & 63;
-                float *e = &S.sp[CP_SP * (q >> 1) + (q & 1)];
-                e[0] = p0.x; e[2] = p0.y; e[4] = p0.z; e[6] = p0.w;
-                e[8] = p1.x; e[10] = p1.y; e[12] = p1.z; e[14] = p1.w;
-                e[16] = p2.x; e[18] = p2.y; e[20] = p2.z; e[22] = p2.w;
-                e[24] = p3.x; e[26] = p3.y; e[28] = p3.z; e[30] = p3.w;
-                if (MODEL) {
-                    int *g = &S.sf[CP_SF * (q >> 1) + (q & 1)];
-                    g[0] = f4.x; g[2] = f4.y; g[4] = f4.z; g[6] = f4.w;
+            const int nk = __popc(m);
+            if (keep) S.kj[__popc(m & lt)] = J;
+            __syncwarp();
+            // kept cluster r = 8 t + lane / 4, atom lane % 4, for t = 0..3: all loads first
+            float4 pj[4];
+            int fj[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int r = 8 * t + (lane >> 2);
+                if (r < nk) {
+                    const size_t e = 4 * (size_t)S.kj[r] + (lane & 3);
+                    pj[t] = *reinterpret_cast<const float4 *>(A.cpos + e);
+                    fj[t] = MODEL ? A.cmol[e] : 0;
                 }
             }
-            npend += __popc(m);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int r = 8 * t + (lane >> 2);
+                if (r < nk) {
+                    const int q = (head + npend + r) & 63, k = lane & 3;
+                    float *e = &S.sp[CP_SP * (q >> 1) + 8 * k + (q & 1)];
+                    e[0] = pj[t].x; e[2] = pj[t].y; e[4] = pj[t].z; e[6] = pj[t].w;
+                    if (MODEL) S.sf[CP_SF * (q >> 1) + 2 * k + (q & 1)] = fj[t];
+                }
+            }
+            npend += nk;
             __syncwarp();
             while (npend >= 8) {                                 // uniform
-                cp_steps<MODEL>(&S.sp[CP_SP * (head >> 1) + 8 * js], &S.sf[CP_SF * (head >> 1) + 2 * js], 4, pi, mi, A, phi, ax, ay, az);
+                cp_steps<MODEL>(&S.sp[CP_SP * (head >> 1) + 8 * js], &S.sf[CP_SF * (head >> 1) + 2 * js], 4, pi, mi,
+                                A, phi, ax, ay, az);
                 head = (head + 8) & 63;
                 npend -= 8;
             }
