@@ -68,6 +68,7 @@ def args_parse():
     p.add_argument("--nve-steps", type=int, default=200, help="NVE leg: FP32 and FP64 energy drift side by side")
     p.add_argument("--list-skin", type=float, default=0.0, help="Verlet-list skin (nm) of the timed FP32 run")
     p.add_argument("--cluster-pairs", type=int, default=0, help="short-range Coulomb pass of the timed FP32 run on cluster pairs")
+    p.add_argument("--bricks", type=int, default=0, help="pair passes of the timed FP32 run on bricks of cells instead of 32-atom groups")
     p.add_argument("--mts-steps", type=int, default=200,
                    help="timed steps of the multiple-time-stepping leg (grid part every 2 and 4 steps; 0: skip)")
     return p.parse_args()
@@ -261,7 +262,7 @@ def run_ours(a):
 
     # ---- FP32 path: the timed run
     m32 = api.MSM(a=A, h=H, levels=cfg["levels"], precision="fp32", model="water", list_skin=a.list_skin,
-                  cluster_pairs=bool(a.cluster_pairs), **WALL)
+                  cluster_pairs=bool(a.cluster_pairs), bricks=bool(a.bricks), **WALL)
     d = dev_system(torch, s, dev)
     m32.md_run(d, DT, a.warmup, record=False)
     torch.cuda.synchronize()

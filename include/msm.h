@@ -91,6 +91,9 @@ extern "C" {
                                 cell bricks; the same sums in another order: agrees with
                                 the brick pass to rounding, not bitwise; ignored for FP64,
                                 Wolf summation and MSM_FLAG_SCALAR_PAIRS                    */
+#define MSM_FLAG_BRICKS 16  /* diagnostic: the short-range and LJ passes give each warp a brick
+                                of cells (~20 atoms) instead of a group of 32 atoms cut from a
+                                column of cells; the same bits, slower (off by default)      */
 
 /* Method parameters (Sec. 3).
  *   a          cutoff of the short-range part g* (nm); the level-k lattice

@@ -21,7 +21,7 @@ LIB_PATH = PKG / "libmsm_gb300.so"
 KE = 138.935458
 FP64, FP32 = 0, 1
 MODEL_CHARGES, MODEL_WATER = 0, 1
-FLAG_GRAPHS, FLAG_AUTOTUNE, FLAG_SCALAR_PAIRS, FLAG_CLUSTER_PAIRS = 1, 2, 4, 8
+FLAG_GRAPHS, FLAG_AUTOTUNE, FLAG_SCALAR_PAIRS, FLAG_CLUSTER_PAIRS, FLAG_BRICKS = 1, 2, 4, 8, 16
 METHODS = {"msm": 0, "cutoff": 1, "wolf": 2}
 CODES = {-1: "EINVAL", -2: "ERANGE", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOCONV"}
 
@@ -177,9 +177,10 @@ def _box(box):
 def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=KE, lj_sigma=0.315061,
                 lj_epsilon=0.6364, d_oh=0.09572, d_hh=None, wall_k=0.0, wall_width=0.0,
                 list_skin=0.0, graphs=True, autotune=True, scalar_pairs=False, method="msm",
-                wolf_alpha=0.0, mts=0, cluster_pairs=False) -> Params:
+                wolf_alpha=0.0, mts=0, cluster_pairs=False, bricks=False) -> Params:
     """mts: multiple time stepping of md_run (the grid part every `mts` steps; 0 or 1: off).
-    cluster_pairs: the FP32 short-range Coulomb pass on cluster pairs instead of cell bricks."""
+    cluster_pairs: the FP32 short-range Coulomb pass on cluster pairs.
+    bricks: the pair passes on bricks of cells instead of 32-atom groups (diagnostic: same bits)."""
     p = Params()
     p.a, p.h, p.n_levels = float(a), float(h), int(levels)
     p.precision = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}[precision]
@@ -192,7 +193,8 @@ def make_params(a=1.2, h=0.25, levels=3, precision="fp32", model="charges", ke=K
     p.wall_k, p.wall_width = float(wall_k), float(wall_width)
     p.list_skin = float(list_skin)
     p.flags = ((FLAG_GRAPHS if graphs else 0) | (FLAG_AUTOTUNE if autotune else 0)
-               | (FLAG_SCALAR_PAIRS if scalar_pairs else 0) | (FLAG_CLUSTER_PAIRS if cluster_pairs else 0))
+               | (FLAG_SCALAR_PAIRS if scalar_pairs else 0) | (FLAG_CLUSTER_PAIRS if cluster_pairs else 0)
+               | (FLAG_BRICKS if bricks else 0))
     p.method = METHODS[method] if isinstance(method, str) else int(method)
     p.wolf_alpha = float(wolf_alpha)
     p.mts_steps = int(mts)

@@ -115,6 +115,9 @@ struct SysDesc {
     int bd[3], nb[3], nbricks;   // short-range bricks: edge in cells, count per axis
     int lj_bd[3], lj_nb[3], lj_nbricks;   // bricks of the LJ-site pass (water completion)
     int cp_nc[2];       // cluster-pair columns of 2 x 2 cells per axis (x, y)
+    int gp_cw, gp_nc[2], gp_col_off;      // i groups of the short-range pass: columns of gp_cw x gp_cw
+                                          // cells, count per axis, global index of the first column
+    int lgp_cw, lgp_nc[2], lgp_col_off;   // the same for the LJ-site pass
     int col_off;        // global index of its first column
     int zc_off;         // first entry of its columns' layer-prefix tables (nc[2] + 1 per column)
     int grid_off;       // first point of its grids in the concatenated grid buffers

@@ -7,9 +7,14 @@
 // summation (g = erfc(alpha r)/r - erfc(alpha a)/a, the WOLF instance).
 //
 // Layout: atoms sorted by finest-grid cell (x fastest), so a run of cells
-// along x is one contiguous slot range.  One warp owns one brick of
-// bd[0] x bd[1] x bd[2] cells (about 24 atoms: one i atom per lane).  The
-// warp's j candidates are whole cell rows (fixed y, z) whose distance to the
+// along x is one contiguous slot range.  One warp owns one group of 32 i atoms
+// (one per lane): the cells are grouped into columns of cw x cw cells (cw^3
+// cells hold ~32 atoms at the mean density), and each column's atoms, in
+// cell-sort order, are cut into runs of 32 (k_grp_count, k_grp_fill).  Every
+// lane has an atom, and the groups' bounding boxes are compact: ~2.7 candidate
+// evaluations per pair within a on water, against ~3.3 for bricks.  With
+// MSM_FLAG_BRICKS the warp owns a brick of bd[0] x bd[1] x bd[2] cells instead
+// (about 20 atoms, taken 32 at a time).  The warp's j candidates are whole cell rows (fixed y, z) whose distance to the
 // bounding box of its i atoms is below a, each trimmed in x to the cells that
 // can still lie within a: every row is one contiguous slot range.
 //
@@ -198,7 +203,12 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
     const SysDesc &D = A.bt.sd[blockIdx.y];
     const int *BD = LJP ? D.lj_bd : D.bd, *NB = LJP ? D.lj_nb : D.nb;
     const int brick = blockIdx.x * SR_WARPS + wid;
-    if (brick >= (LJP ? D.lj_nbricks : D.nbricks) || failed(A.status)) return;
+    // i groups: warp `brick` takes group g0 + brick of this system, 32 slots
+    const int *gc = A.gcol ? A.gcol + (LJP ? D.lgp_col_off : D.gp_col_off) : nullptr;
+    const int g0 = gc ? gc[0] : 0;
+    const int n_units = gc ? gc[LJP ? D.lgp_nc[0] * D.lgp_nc[1] : D.gp_nc[0] * D.gp_nc[1]] - g0
+                           : (LJP ? D.lj_nbricks : D.nbricks);
+    if (brick >= n_units || failed(A.status)) return;
     if (A.vl_ctl && A.vl_ctl[1] == 0 && A.vl_ctl[2] == 0) return;     // the Verlet-list path ran
     constexpr bool PK = PACKED && sizeof(T) == 4 && !COUNT;
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
@@ -210,18 +220,24 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
     const unsigned lt = (1u << lane) - 1u;
 
     int n_i = 0;
-    for (int cz = cz0; cz < cz1; cz++)
-        for (int cy = cy0; cy < cy1; cy++) {
-            const int rb = (cz * ny + cy) * nx;
-            n_i += start[rb + cx1] - start[rb + cx0];
-        }
+    if (gc) {
+        n_i = 32;                                  // one pass over the group's (up to) 32 atoms
+    } else {
+        for (int cz = cz0; cz < cz1; cz++)
+            for (int cy = cy0; cy < cy1; cy++) {
+                const int rb = (cz * ny + cy) * nx;
+                n_i += start[rb + cx1] - start[rb + cx0];
+            }
+    }
     const T h = (T)D.g.h, inv_h = T(1) / h;
     const T a_sel2 = A.a_sel * A.a_sel;
 
     for (int base = 0; base < n_i; base += 32) {
-        // ---- this lane's i atom: the (base + lane)-th atom of the brick
+        // ---- this lane's i atom: slot lane of the group, or the (base + lane)-th atom of the brick
         int slot = -1;
-        {
+        if (gc) {
+            slot = A.gslot[32 * (size_t)(g0 + brick) + lane];
+        } else {
             int want = base + lane, acc = 0;
             for (int cz = cz0; cz < cz1; cz++)
                 for (int cy = cy0; cy < cy1; cy++) {
@@ -414,6 +430,95 @@ __global__ void __launch_bounds__(SR_WARPS * 32, sizeof(T) == 4 ? 32 : 16) k_sho
             if (MODEL && !(A.aflag[slot] & 1)) A.lj[atom] = vec4<T>{T(0), T(0), T(0), T(0)};
         }
     }
+}
+
+// ------------------------------------------------------------- i groups
+
+// One warp per column of cw x cw cells: its atom count over all cell layers, as
+// whole groups of 32.
+template <bool LJ>
+__global__ void __launch_bounds__(128) k_grp_count(const Batch bt, const int *__restrict__ start,
+                                                   int *__restrict__ gcnt, const int *__restrict__ status)
+{
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int cw = LJ ? D.lgp_cw : D.gp_cw, ncx = LJ ? D.lgp_nc[0] : D.gp_nc[0], ncy = LJ ? D.lgp_nc[1] : D.gp_nc[1];
+    const int col = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (col >= ncx * ncy || failed(status)) return;
+    const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
+    const int cx0 = (col % ncx) * cw, cx1 = min(cx0 + cw, nx), cy0 = (col / ncx) * cw, cy1 = min(cy0 + cw, ny);
+    const int *__restrict__ st = start + D.cell_off;
+    int c = 0;
+    for (int cz = lane; cz < nz; cz += 32)
+        for (int cy = cy0; cy < cy1; cy++) {
+            const int rb = (cz * ny + cy) * nx;
+            c += st[rb + cx1] - st[rb + cx0];
+        }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) gcnt[(LJ ? D.lgp_col_off : D.gp_col_off) + col] = (c + 31) / 32;
+}
+
+// One warp per column: the slots of its atoms in cell-sort order (layer z, then
+// row y, then slot) into its groups, -1 after the last atom.
+template <bool LJ>
+__global__ void __launch_bounds__(128) k_grp_fill(const Batch bt, const int *__restrict__ start,
+                                                  const int *__restrict__ gcol, int *__restrict__ gslot,
+                                                  const int *__restrict__ status)
+{
+    const SysDesc &D = bt.sd[blockIdx.y];
+    const int lane = threadIdx.x & 31;
+    const int cw = LJ ? D.lgp_cw : D.gp_cw, ncx = LJ ? D.lgp_nc[0] : D.gp_nc[0], ncy = LJ ? D.lgp_nc[1] : D.gp_nc[1];
+    const int col = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (col >= ncx * ncy || failed(status)) return;
+    const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
+    const int cx0 = (col % ncx) * cw, cx1 = min(cx0 + cw, nx), cy0 = (col / ncx) * cw, cy1 = min(cy0 + cw, ny);
+    const int *__restrict__ st = start + D.cell_off;
+    const int gcl = (LJ ? D.lgp_col_off : D.gp_col_off) + col;
+    int *out = gslot + 32 * (size_t)gcol[gcl];
+    const int ntot = 32 * (gcol[gcl + 1] - gcol[gcl]);
+    int carry = 0;
+    for (int z0 = 0; z0 < nz; z0 += 32) {
+        const int cz = z0 + lane;
+        int c = 0;
+        if (cz < nz)
+            for (int cy = cy0; cy < cy1; cy++) {
+                const int rb = (cz * ny + cy) * nx;
+                c += st[rb + cx1] - st[rb + cx0];
+            }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int r = carry + incl - c;
+        if (cz < nz)
+            for (int cy = cy0; cy < cy1; cy++) {
+                const int rb = (cz * ny + cy) * nx;
+                for (int s = st[rb + cx0]; s < st[rb + cx1]; s++) out[r++] = s;
+            }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    for (int r = carry + lane; r < ntot; r += 32) out[r] = -1;
+}
+
+int launch_groups(const Batch &bt, bool lj, int max_cols, int n_cols, const int *start, int *gcnt, int *gcol,
+                  int *bsum, int *gslot, const int *status, cudaStream_t st)
+{
+    if (max_cols <= 0) return MSM_OK;
+    const dim3 grid((max_cols + 3) / 4, bt.B);
+    if (lj) k_grp_count<true><<<grid, 128, 0, st>>>(bt, start, gcnt, status);
+    else k_grp_count<false><<<grid, 128, 0, st>>>(bt, start, gcnt, status);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    const int rc = launch_scan(n_cols, gcnt, gcol, bsum, status, st);
+    if (rc != MSM_OK) return rc;
+    if (lj) k_grp_fill<true><<<grid, 128, 0, st>>>(bt, start, gcol, gslot, status);
+    else k_grp_fill<false><<<grid, 128, 0, st>>>(bt, start, gcol, gslot, status);
+    count_launch();
+    CUDA_TRY(cudaGetLastError());
+    return MSM_OK;
 }
 
 template <typename T>

@@ -70,7 +70,16 @@ template <typename T> struct ShortArgs {
     const int *vl_ctl;     // Verlet-list flags (nullable): skip when the list path ran
     const int *status;
     bool scalar_pairs;     // FP32 pair passes: one queued j per step instead of packed pairs
+    // i groups (nullable: bricks): per global column the first group (scan of the group
+    // counts, columns + 1 entries), and 32 sorted slots per group (-1: no atom)
+    const int *gcol;
+    const int *gslot;
 };
+// i groups of the pair passes: each column of cw x cw cells (SysDesc::gp_* or, lj,
+// lgp_*) has ceil(atoms / 32) groups, its atoms in cell-sort order (z, y, x, slot)
+// cut into runs of 32.  gcnt, gcol: columns + 1 entries; bsum: scan scratch.
+int launch_groups(const Batch &bt, bool lj, int max_cols, int n_cols, const int *start, int *gcnt, int *gcol,
+                  int *bsum, int *gslot, const int *status, cudaStream_t st);
 // model = true: skip pairs of the same molecule (their smooth part is removed by
 // the exclusion kernel) and write a zero LJ output for atoms that are not LJ
 // sites; the LJ term itself is the separate pass below.

@@ -237,6 +237,10 @@ struct msm_handle {
     long long g_kernels = 0;                            // kernels per replayed step
     // Verlet lists (md_run with list_skin > 0, single systems)
     bool list_on = false;
+    // i groups of the pair passes (off with MSM_FLAG_BRICKS); lgp_*: the LJ-site pass
+    bool gp_on = false;
+    int gp_cols = 0, gp_max_cols = 0, gp_max_groups = 0, lgp_cols = 0, lgp_max_cols = 0, lgp_max_groups = 0;
+    DevBuf gp_cnt, gp_col, gp_bsum, gp_slot, lgp_cnt, lgp_col, lgp_bsum, lgp_slot;
     // cluster pairs (MSM_FLAG_CLUSTER_PAIRS)
     bool cp_on = false;
     int cp_cols = 0, cp_max_cols = 0, cp_max_icl = 0;
@@ -334,7 +338,8 @@ static int check_params(const msm_params *p)
     if (p->precision != MSM_FP32 && p->precision != MSM_FP64) return fail_msg(MSM_EINVAL, "unknown precision");
     if (p->gamma_kind != 0 || p->basis_kind != 0) return fail_msg(MSM_EINVAL, "only gamma_kind 0 and basis_kind 0 exist");
     if (p->model != MSM_MODEL_CHARGES && p->model != MSM_MODEL_WATER) return fail_msg(MSM_EINVAL, "unknown model");
-    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE | MSM_FLAG_SCALAR_PAIRS | MSM_FLAG_CLUSTER_PAIRS))
+    if (p->flags & ~(MSM_FLAG_GRAPHS | MSM_FLAG_AUTOTUNE | MSM_FLAG_SCALAR_PAIRS | MSM_FLAG_CLUSTER_PAIRS |
+                     MSM_FLAG_BRICKS))
         return fail_msg(MSM_EINVAL, "unknown flags");
     if (!(p->wall_k >= 0) || !(p->wall_width >= 0)) return fail_msg(MSM_EINVAL, "wall_k and wall_width must be >= 0");
     if (!(p->list_skin >= 0) || !(p->list_skin < p->a)) return fail_msg(MSM_EINVAL, "list_skin must be in [0, a)");
@@ -391,7 +396,8 @@ extern "C" void msm_destroy(msm_handle *h)
                      &h->vl_perm, &h->vl_start, &h->vl_xref, &h->vl_pos, &h->vl_rtab, &h->vl_rtn,
                      &h->vl_cnt, &h->vl_cntlj, &h->vl_nbr, &h->vl_nbr_lj, &h->vl_ctl,
                      &h->cp_coln, &h->cp_colcl, &h->cp_bsum, &h->cp_zc, &h->cp_pos, &h->cp_mol, &h->cp_slot,
-                     &h->cp_box};
+                     &h->cp_box, &h->gp_cnt, &h->gp_col, &h->gp_bsum, &h->gp_slot, &h->lgp_cnt, &h->lgp_col,
+                     &h->lgp_bsum, &h->lgp_slot};
     for (DevBuf *b : all) release(*b);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -509,6 +515,12 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     std::vector<std::array<int, 4>> tops;          // (nx, ny, nz, table offset)
     int64_t N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, ST = 0;
     int64_t CC = 0, CZ = 0, CK = 0, CI = 0, CMAX = 0;    // cluster pairs: columns, layer tables, clusters of 4
+    int64_t GC = 0, GK = 0, GI = 0, GMAX = 0, LC = 0, LK = 0, LI = 0, LMAX = 0;   // i groups: columns, groups
+    // i groups: columns of cw x cw cells with cw^3 cells holding ~32 atoms at the mean density
+    auto group_width = [](double per_cell) {
+        const int cw = (int)lround(cbrt(32.0 / std::max(per_cell, 1e-3)));
+        return std::min(std::max(cw, 1), 8);
+    };
     bool pending = false;
     h->h_blk.clear();
     for (int s = 0; s < B; s++) {
@@ -583,11 +595,33 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             CI = std::max(CI, n / 8 + nco);                 // i clusters: at most n/8 + 1 per column
             CMAX = std::max(CMAX, nco);
         }
+        {
+            const int64_t n = (int64_t)S.n, n_lj = (int64_t)(S.n_mol + (S.n - 3 * S.n_mol));
+            D.gp_cw = group_width((double)n / (double)ncells);
+            D.gp_nc[0] = (D.g.nc[0] + D.gp_cw - 1) / D.gp_cw;
+            D.gp_nc[1] = (D.g.nc[1] + D.gp_cw - 1) / D.gp_cw;
+            const int64_t ng = (int64_t)D.gp_nc[0] * D.gp_nc[1];
+            D.gp_col_off = (int)GC;
+            GC += ng;
+            GK += n / 32 + ng;                             // groups: at most n/32 + 1 per column
+            GI = std::max(GI, n / 32 + ng);
+            GMAX = std::max(GMAX, ng);
+            D.lgp_cw = group_width((double)n_lj / (double)ncells);
+            D.lgp_nc[0] = (D.g.nc[0] + D.lgp_cw - 1) / D.lgp_cw;
+            D.lgp_nc[1] = (D.g.nc[1] + D.lgp_cw - 1) / D.lgp_cw;
+            const int64_t nl = (int64_t)D.lgp_nc[0] * D.lgp_nc[1];
+            D.lgp_col_off = (int)LC;
+            LC += nl;
+            LK += n_lj / 32 + nl;
+            LI = std::max(LI, n_lj / 32 + nl);
+            LMAX = std::max(LMAX, nl);
+        }
         const Tuned *t = (h->p.flags & MSM_FLAG_AUTOTUNE) ? find_tuned(h, S.n, D.g) : nullptr;
         if (t) set_bricks(D, t->bd);
         else {
             set_bricks(D, kBrickShapes[brick_heuristic(S.n, D.g)]);
-            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && S.n > 0) pending = true;
+            // the brick shapes are timed only where bricks serve the pair passes
+            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && (h->p.flags & MSM_FLAG_BRICKS) && S.n > 0) pending = true;
         }
         if (h->p.model == MSM_MODEL_WATER) {
             // LJ pass: the O sites and single sites of the water completion
@@ -630,6 +664,19 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
         TRY(ensure(h->lj_start, sizeof(int) * (size_t)(M + 1)));
     }
     TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints((int)M)));
+    h->gp_on = !(h->p.flags & MSM_FLAG_BRICKS);
+    if (h->gp_on) {
+        TRY(ensure(h->gp_cnt, sizeof(int) * (size_t)(GC + 1)));
+        TRY(ensure(h->gp_col, sizeof(int) * (size_t)(GC + 1)));
+        TRY(ensure(h->gp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)GC)));
+        TRY(ensure(h->gp_slot, sizeof(int) * 32 * (size_t)(GK + 1)));
+        if (h->p.model == MSM_MODEL_WATER) {
+            TRY(ensure(h->lgp_cnt, sizeof(int) * (size_t)(LC + 1)));
+            TRY(ensure(h->lgp_col, sizeof(int) * (size_t)(LC + 1)));
+            TRY(ensure(h->lgp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)LC)));
+            TRY(ensure(h->lgp_slot, sizeof(int) * 32 * (size_t)(LK + 1)));
+        }
+    }
     h->cp_on = (h->p.flags & MSM_FLAG_CLUSTER_PAIRS) && h->precision == MSM_FP32 &&
                h->p.method != MSM_METHOD_WOLF && !(h->p.flags & MSM_FLAG_SCALAR_PAIRS);
     if (h->cp_on) {
@@ -713,6 +760,8 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     h->N = (int)N; h->M = (int)M; h->G = (int)G; h->UT = (int)UT; h->TT = (int)TT; h->PB = (int)PB;
     h->stiles = (int)ST;
     h->cp_cols = (int)CC;
+    h->gp_cols = (int)GC; h->gp_max_cols = (int)GMAX; h->gp_max_groups = (int)GI;
+    h->lgp_cols = (int)LC; h->lgp_max_cols = (int)LMAX; h->lgp_max_groups = (int)LI;
     h->cp_max_cols = (int)CMAX;
     h->cp_max_icl = (int)CI;
     h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = h->max_lj_bricks = 0;
@@ -802,6 +851,8 @@ static ShortArgs<T> short_args(msm_handle *h)
     s.vl_ctl = nullptr;
     s.status = h->status.as<int>();
     s.scalar_pairs = (h->p.flags & MSM_FLAG_SCALAR_PAIRS) != 0;
+    s.gcol = nullptr;
+    s.gslot = nullptr;
     return s;
 }
 
@@ -1032,6 +1083,14 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
 
     // step 1: short range
     ShortArgs<T> s = short_args<T>(h);
+    if (h->gp_on) {
+        // i groups of the Coulomb pass (after the binning: they read the cell starts)
+        TRY(launch_groups(s.bt, false, h->gp_max_cols, h->gp_cols, s.start, h->gp_cnt.as<int>(),
+                          h->gp_col.as<int>(), h->gp_bsum.as<int>(), h->gp_slot.as<int>(), s.status, st));
+        s.gcol = h->gp_col.as<int>();
+        s.gslot = h->gp_slot.as<int>();
+        s.max_bricks = h->gp_max_groups;
+    }
     // the lists address the bricks they were built for: never use them on another brick set
     if (h->list_on && h->nbricks != h->vl_nbricks) h->list_on = false;
     s.vl_ctl = h->list_on ? h->vl_ctl.as<int>() : nullptr;
@@ -1086,6 +1145,13 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             sl.max_bricks = h->max_lj_bricks;
             sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
             sl.perm = h->lj_perm.as<int>();
+            if (h->gp_on) {
+                TRY(launch_groups(sl.bt, true, h->lgp_max_cols, h->lgp_cols, sl.start, h->lgp_cnt.as<int>(),
+                                  h->lgp_col.as<int>(), h->lgp_bsum.as<int>(), h->lgp_slot.as<int>(), status, st));
+                sl.gcol = h->lgp_col.as<int>();
+                sl.gslot = h->lgp_slot.as<int>();
+                sl.max_bricks = h->lgp_max_groups;
+            }
             TRY(launch_short_lj<T>(sl, st));
         }
     }

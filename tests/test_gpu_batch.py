@@ -154,10 +154,11 @@ def test_graph_reused_across_calls_and_refreshed_when_inputs_move(api, torch):
 
 
 def test_autotuned_bricks_change_no_result(api, torch):
+    """The brick shapes are timed only on the brick path (MSM_FLAG_BRICKS)."""
     s = inputs.water_box(3000, 3.1, margin=0.6, seed=74, vel_seed=75)
     res = {}
     for tune in (False, True):
-        m = api.MSM(a=A, h=H, levels=3, precision="fp32", model="water", autotune=tune)
+        m = api.MSM(a=A, h=H, levels=3, precision="fp32", model="water", autotune=tune, bricks=True)
         e, f, p = m.system_forces(_dev(torch, s))
         res[tune] = (float(e), f, p)
     assert res[True][0] == res[False][0]

@@ -57,7 +57,7 @@ def test_default_params_and_validation_without_gpu(L):
     bad = api.make_params(a=5.0, h=0.25)          # 2a/h = 40: lattice-cutoff radius too large
     assert L.msm_create(C.byref(bad), C.byref(h)) == -1
     bad = api.make_params()
-    bad.flags = 16                                # no such flag
+    bad.flags = 32                                # no such flag
     assert L.msm_create(C.byref(bad), C.byref(h)) == -1
     assert b"unknown flags" in L.msm_last_error()
 
@@ -67,7 +67,7 @@ def test_flag_values_match_the_header():
     hdr = (ROOT / "include" / "msm.h").read_text()
     defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define MSM_FLAG_(\w+)\s+(\d+)", hdr)}
     assert defs == {"GRAPHS": api.FLAG_GRAPHS, "AUTOTUNE": api.FLAG_AUTOTUNE, "SCALAR_PAIRS": api.FLAG_SCALAR_PAIRS,
-                    "CLUSTER_PAIRS": api.FLAG_CLUSTER_PAIRS}
+                    "CLUSTER_PAIRS": api.FLAG_CLUSTER_PAIRS, "BRICKS": api.FLAG_BRICKS}
     assert api.make_params().flags == api.FLAG_GRAPHS | api.FLAG_AUTOTUNE
     assert api.make_params(scalar_pairs=True, graphs=False, autotune=False).flags == api.FLAG_SCALAR_PAIRS
 
