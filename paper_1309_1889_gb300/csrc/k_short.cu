@@ -9,8 +9,9 @@
 // Layout: atoms sorted by finest-grid cell (x fastest), so a run of cells
 // along x is one contiguous slot range.  One warp owns one group of 32 i atoms
 // (one per lane): the cells are grouped into columns of cw x cw cells (cw^3
-// cells hold ~32 atoms at the mean density), and each column's atoms, in
-// cell-sort order, are cut into runs of 32 (k_grp_count, k_grp_fill).  Every
+// cells hold ~32 atoms at the mean density), and each column's atoms, layer by
+// layer and in ascending z inside a layer, are cut into runs of 32
+// (k_grp_count, k_grp_fill).  Every
 // lane has an atom, and the groups' bounding boxes are compact: ~2.7 candidate
 // evaluations per pair within a on water, against ~3.3 for bricks.  With
 // MSM_FLAG_BRICKS the warp owns a brick of bd[0] x bd[1] x bd[2] cells instead
@@ -459,52 +460,93 @@ __global__ void __launch_bounds__(128) k_grp_count(const Batch bt, const int *__
     if (lane == 0) gcnt[(LJ ? D.lgp_col_off : D.gp_col_off) + col] = (c + 31) / 32;
 }
 
-// One warp per column: the slots of its atoms in cell-sort order (layer z, then
-// row y, then slot) into its groups, -1 after the last atom.
-template <bool LJ>
+// One warp per (column, chunk of 32 cell layers), lane = layer: the slots of the
+// column's atoms, layer by layer, each layer's atoms in ascending z (ties by
+// slot), into its groups, -1 after the last atom.  Ordering by z inside a layer
+// gives the groups that cut a layer thinner boxes.  A lane loads its layer's z
+// values into its own column of shared memory (entry e of lane l at [e][l]: no
+// bank is shared) and sorts them there by insertion; a layer of more than
+// GF_MAXL atoms keeps the cell order (the grouping changes no result).
+constexpr int GF_MAXL = 24;
+template <typename T, bool LJ>
 __global__ void __launch_bounds__(128) k_grp_fill(const Batch bt, const int *__restrict__ start,
-                                                  const int *__restrict__ gcol, int *__restrict__ gslot,
-                                                  const int *__restrict__ status)
+                                                  const vec4<T> *__restrict__ apos, const int *__restrict__ gcol,
+                                                  int *__restrict__ gslot, const int *__restrict__ status)
 {
+    __shared__ float skey[4][GF_MAXL][32];
+    __shared__ int sslot[4][GF_MAXL][32];
     const SysDesc &D = bt.sd[blockIdx.y];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int cw = LJ ? D.lgp_cw : D.gp_cw, ncx = LJ ? D.lgp_nc[0] : D.gp_nc[0], ncy = LJ ? D.lgp_nc[1] : D.gp_nc[1];
-    const int col = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (col >= ncx * ncy || failed(status)) return;
     const int nx = D.g.nc[0], ny = D.g.nc[1], nz = D.g.nc[2];
+    const int nchunk = (nz + 31) / 32;
+    const int idx = blockIdx.x * 4 + w, col = idx / nchunk, z0 = 32 * (idx % nchunk);
+    if (col >= ncx * ncy || failed(status)) return;
     const int cx0 = (col % ncx) * cw, cx1 = min(cx0 + cw, nx), cy0 = (col / ncx) * cw, cy1 = min(cy0 + cw, ny);
     const int *__restrict__ st = start + D.cell_off;
     const int gcl = (LJ ? D.lgp_col_off : D.gp_col_off) + col;
     int *out = gslot + 32 * (size_t)gcol[gcl];
-    const int ntot = 32 * (gcol[gcl + 1] - gcol[gcl]);
-    int carry = 0;
-    for (int z0 = 0; z0 < nz; z0 += 32) {
-        const int cz = z0 + lane;
+    auto layer_count = [&](int cz) {
         int c = 0;
-        if (cz < nz)
-            for (int cy = cy0; cy < cy1; cy++) {
-                const int rb = (cz * ny + cy) * nx;
-                c += st[rb + cx1] - st[rb + cx0];
-            }
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+        for (int cy = cy0; cy < cy1; cy++) {
+            const int rb = (cz * ny + cy) * nx;
+            c += st[rb + cx1] - st[rb + cx0];
         }
-        int r = carry + incl - c;
-        if (cz < nz)
-            for (int cy = cy0; cy < cy1; cy++) {
-                const int rb = (cz * ny + cy) * nx;
-                for (int s = st[rb + cx0]; s < st[rb + cx1]; s++) out[r++] = s;
-            }
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+        return c;
+    };
+    // atoms of the column below this chunk
+    int below = 0;
+    for (int cz = lane; cz < z0; cz += 32) below += layer_count(cz);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+    const int cz = z0 + lane;
+    const int c = cz < nz ? layer_count(cz) : 0;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    for (int r = carry + lane; r < ntot; r += 32) out[r] = -1;
+    int r = below + incl - c;
+    if (c > 0 && c <= GF_MAXL) {
+        int n = 0;
+        for (int cy = cy0; cy < cy1; cy++) {
+            const int rb = (cz * ny + cy) * nx;
+            for (int s = st[rb + cx0]; s < st[rb + cx1]; s++, n++) {
+                skey[w][n][lane] = (float)apos[s].z;
+                sslot[w][n][lane] = s;
+            }
+        }
+        // insertion by (z, slot): slots were loaded in ascending order, so ties stay in order
+        for (int e = 1; e < n; e++) {
+            const float zk = skey[w][e][lane];
+            const int sk = sslot[w][e][lane];
+            int k = e;
+            while (k > 0 && skey[w][k - 1][lane] > zk) {
+                skey[w][k][lane] = skey[w][k - 1][lane];
+                sslot[w][k][lane] = sslot[w][k - 1][lane];
+                k--;
+            }
+            skey[w][k][lane] = zk;
+            sslot[w][k][lane] = sk;
+        }
+        for (int e = 0; e < n; e++) out[r++] = sslot[w][e][lane];
+    } else if (c > 0) {
+        for (int cy = cy0; cy < cy1; cy++) {
+            const int rb = (cz * ny + cy) * nx;
+            for (int s = st[rb + cx0]; s < st[rb + cx1]; s++) out[r++] = s;
+        }
+    }
+    if (z0 + 32 >= nz) {                       // the column's last chunk pads its last group
+        const int total = below + __shfl_sync(0xffffffffu, incl, 31);
+        const int ntot = 32 * (gcol[gcl + 1] - gcol[gcl]);
+        for (int q = total + lane; q < ntot; q += 32) out[q] = -1;
+    }
 }
 
-int launch_groups(const Batch &bt, bool lj, int max_cols, int n_cols, const int *start, int *gcnt, int *gcol,
-                  int *bsum, int *gslot, const int *status, cudaStream_t st)
+template <typename T>
+int launch_groups(const Batch &bt, bool lj, int max_cols, int max_nz, int n_cols, const int *start,
+                  const vec4<T> *apos, int *gcnt, int *gcol, int *bsum, int *gslot, const int *status, cudaStream_t st)
 {
     if (max_cols <= 0) return MSM_OK;
     const dim3 grid((max_cols + 3) / 4, bt.B);
@@ -514,8 +556,10 @@ int launch_groups(const Batch &bt, bool lj, int max_cols, int n_cols, const int 
     CUDA_TRY(cudaGetLastError());
     const int rc = launch_scan(n_cols, gcnt, gcol, bsum, status, st);
     if (rc != MSM_OK) return rc;
-    if (lj) k_grp_fill<true><<<grid, 128, 0, st>>>(bt, start, gcol, gslot, status);
-    else k_grp_fill<false><<<grid, 128, 0, st>>>(bt, start, gcol, gslot, status);
+    // fill: one warp per (column, chunk of 32 layers)
+    const dim3 gfill((max_cols * ((max_nz + 31) / 32) + 3) / 4, bt.B);
+    if (lj) k_grp_fill<T, true><<<gfill, 128, 0, st>>>(bt, start, apos, gcol, gslot, status);
+    else k_grp_fill<T, false><<<gfill, 128, 0, st>>>(bt, start, apos, gcol, gslot, status);
     count_launch();
     CUDA_TRY(cudaGetLastError());
     return MSM_OK;
@@ -632,6 +676,10 @@ int launch_lj_compact(int m_total, const int *start, const int *lj_start, const 
     return MSM_OK;
 }
 
+template int launch_groups<float>(const Batch &, bool, int, int, int, const int *, const vec4<float> *, int *,
+                                  int *, int *, int *, const int *, cudaStream_t);
+template int launch_groups<double>(const Batch &, bool, int, int, int, const int *, const vec4<double> *, int *,
+                                   int *, int *, int *, const int *, cudaStream_t);
 template int launch_short<float>(const ShortArgs<float> &, bool, cudaStream_t);
 template int launch_short<double>(const ShortArgs<double> &, bool, cudaStream_t);
 template int launch_count_pairs<float>(const ShortArgs<float> &, cudaStream_t);

@@ -76,10 +76,13 @@ template <typename T> struct ShortArgs {
     const int *gslot;
 };
 // i groups of the pair passes: each column of cw x cw cells (SysDesc::gp_* or, lj,
-// lgp_*) has ceil(atoms / 32) groups, its atoms in cell-sort order (z, y, x, slot)
-// cut into runs of 32.  gcnt, gcol: columns + 1 entries; bsum: scan scratch.
-int launch_groups(const Batch &bt, bool lj, int max_cols, int n_cols, const int *start, int *gcnt, int *gcol,
-                  int *bsum, int *gslot, const int *status, cudaStream_t st);
+// lgp_*) has ceil(atoms / 32) groups, its atoms taken layer by layer (each layer
+// in ascending z) and cut into runs of 32.  gcnt, gcol: columns + 1 entries;
+// bsum: scan scratch; apos: the sorted positions the cell starts index; max_cols,
+// max_nz: columns and cell layers of the largest system.
+template <typename T>
+int launch_groups(const Batch &bt, bool lj, int max_cols, int max_nz, int n_cols, const int *start,
+                  const vec4<T> *apos, int *gcnt, int *gcol, int *bsum, int *gslot, const int *status, cudaStream_t st);
 // model = true: skip pairs of the same molecule (their smooth part is removed by
 // the exclusion kernel) and write a zero LJ output for atoms that are not LJ
 // sites; the LJ term itself is the separate pass below.

@@ -240,6 +240,7 @@ struct msm_handle {
     // i groups of the pair passes (off with MSM_FLAG_BRICKS); lgp_*: the LJ-site pass
     bool gp_on = false;
     int gp_cols = 0, gp_max_cols = 0, gp_max_groups = 0, lgp_cols = 0, lgp_max_cols = 0, lgp_max_groups = 0;
+    int gp_max_nz = 0;                                  // cell layers of the largest system
     DevBuf gp_cnt, gp_col, gp_bsum, gp_slot, lgp_cnt, lgp_col, lgp_bsum, lgp_slot;
     // cluster pairs (MSM_FLAG_CLUSTER_PAIRS)
     bool cp_on = false;
@@ -761,6 +762,8 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     h->stiles = (int)ST;
     h->cp_cols = (int)CC;
     h->gp_cols = (int)GC; h->gp_max_cols = (int)GMAX; h->gp_max_groups = (int)GI;
+    h->gp_max_nz = 0;
+    for (const SysDesc &D : h->hsd) h->gp_max_nz = std::max(h->gp_max_nz, D.g.nc[2]);
     h->lgp_cols = (int)LC; h->lgp_max_cols = (int)LMAX; h->lgp_max_groups = (int)LI;
     h->cp_max_cols = (int)CMAX;
     h->cp_max_icl = (int)CI;
@@ -1085,8 +1088,9 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
     ShortArgs<T> s = short_args<T>(h);
     if (h->gp_on) {
         // i groups of the Coulomb pass (after the binning: they read the cell starts)
-        TRY(launch_groups(s.bt, false, h->gp_max_cols, h->gp_cols, s.start, h->gp_cnt.as<int>(),
-                          h->gp_col.as<int>(), h->gp_bsum.as<int>(), h->gp_slot.as<int>(), s.status, st));
+        TRY(launch_groups<T>(s.bt, false, h->gp_max_cols, h->gp_max_nz, h->gp_cols, s.start, s.apos,
+                             h->gp_cnt.as<int>(), h->gp_col.as<int>(), h->gp_bsum.as<int>(), h->gp_slot.as<int>(),
+                             s.status, st));
         s.gcol = h->gp_col.as<int>();
         s.gslot = h->gp_slot.as<int>();
         s.max_bricks = h->gp_max_groups;
@@ -1146,8 +1150,8 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
             sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
             sl.perm = h->lj_perm.as<int>();
             if (h->gp_on) {
-                TRY(launch_groups(sl.bt, true, h->lgp_max_cols, h->lgp_cols, sl.start, h->lgp_cnt.as<int>(),
-                                  h->lgp_col.as<int>(), h->lgp_bsum.as<int>(), h->lgp_slot.as<int>(), status, st));
+                TRY(launch_groups<T>(sl.bt, true, h->lgp_max_cols, h->gp_max_nz, h->lgp_cols, sl.start, sl.apos,
+                                     h->lgp_cnt.as<int>(), h->lgp_col.as<int>(), h->lgp_bsum.as<int>(), h->lgp_slot.as<int>(), status, st));
                 sl.gcol = h->lgp_col.as<int>();
                 sl.gslot = h->lgp_slot.as<int>();
                 sl.max_bricks = h->lgp_max_groups;
