@@ -79,8 +79,9 @@ extern "C" {
 #define MSM_FLAG_GRAPHS   1  /* md_run: steps after the first replay one captured CUDA graph
                                 (the first too, when a previous call captured it for the
                                 same arrays, geometry and buffers)                         */
-#define MSM_FLAG_AUTOTUNE 2  /* time the short-range brick shapes on the first evaluation of
-                                each single-system geometry and keep the fastest           */
+#define MSM_FLAG_AUTOTUNE 2  /* time the pair passes' i-group column widths (with
+                                MSM_FLAG_BRICKS: brick shapes) on the first evaluation of
+                                each geometry and keep the fastest; never changes a result */
 #define MSM_FLAG_SCALAR_PAIRS 4  /* diagnostic, FP32 only: the short-range Coulomb and LJ
                                 passes take their queued neighbours one at a time instead
                                 of two per packed FP32x2 step; the same bits, slower (off

@@ -185,6 +185,7 @@ struct Tuned {
     int nc[3];
     int bd[3];
     int lj_bd[3];          // bricks of the LJ pass (water model; 0 = not tuned)
+    int gcw, lgcw;         // column widths of the i groups, all atoms and LJ sites (0 = not tuned)
 };
 
 struct msm_handle {
@@ -471,6 +472,62 @@ static void set_bricks(SysDesc &D, const int bd[3])
     D.nbricks = D.nb[0] * D.nb[1] * D.nb[2];
 }
 
+// Column width of the i groups: columns of cw x cw cells, cw^3 cells holding ~32
+// atoms at the mean density.
+static int group_width(double per_cell)
+{
+    const int cw = (int)lround(cbrt(32.0 / std::max(per_cell, 1e-3)));
+    return std::min(std::max(cw, 1), 8);
+}
+
+// Column layout of the pair passes' i groups from each system's column widths
+// (SysDesc::gp_cw, lgp_cw): columns per axis, global column offsets, the bounds
+// on the group counts, and (groups on) the buffers.
+static int layout_groups(msm_handle *h, std::vector<SysDesc> &d)
+{
+    int64_t GC = 0, GK = 0, GI = 0, GMAX = 0, LC = 0, LK = 0, LI = 0, LMAX = 0;
+    int mnz = 0;
+    for (SysDesc &D : d) {
+        const int64_t n = D.n, n_lj = (int64_t)D.n_mol + (D.n - 3 * (int64_t)D.n_mol);
+        D.gp_nc[0] = (D.g.nc[0] + D.gp_cw - 1) / D.gp_cw;
+        D.gp_nc[1] = (D.g.nc[1] + D.gp_cw - 1) / D.gp_cw;
+        const int64_t ng = (int64_t)D.gp_nc[0] * D.gp_nc[1];
+        D.gp_col_off = (int)GC;
+        GC += ng;
+        GK += n / 32 + ng;                                 // groups: at most n/32 + 1 per column
+        GI = std::max(GI, n / 32 + ng);
+        GMAX = std::max(GMAX, ng);
+        D.lgp_nc[0] = (D.g.nc[0] + D.lgp_cw - 1) / D.lgp_cw;
+        D.lgp_nc[1] = (D.g.nc[1] + D.lgp_cw - 1) / D.lgp_cw;
+        const int64_t nl = (int64_t)D.lgp_nc[0] * D.lgp_nc[1];
+        D.lgp_col_off = (int)LC;
+        LC += nl;
+        LK += n_lj / 32 + nl;
+        LI = std::max(LI, n_lj / 32 + nl);
+        LMAX = std::max(LMAX, nl);
+        mnz = std::max(mnz, D.g.nc[2]);
+    }
+    const int64_t lim = ((int64_t)1 << 31) - 1;
+    if (GC >= lim || LC >= lim || 32 * (GK + 1) >= lim || 32 * (LK + 1) >= lim)
+        return fail_msg(MSM_EINVAL, "batch too large for 32-bit group offsets");
+    if (h->gp_on) {
+        TRY(ensure(h->gp_cnt, sizeof(int) * (size_t)(GC + 1)));
+        TRY(ensure(h->gp_col, sizeof(int) * (size_t)(GC + 1)));
+        TRY(ensure(h->gp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)GC)));
+        TRY(ensure(h->gp_slot, sizeof(int) * 32 * (size_t)(GK + 1)));
+        if (h->p.model == MSM_MODEL_WATER) {
+            TRY(ensure(h->lgp_cnt, sizeof(int) * (size_t)(LC + 1)));
+            TRY(ensure(h->lgp_col, sizeof(int) * (size_t)(LC + 1)));
+            TRY(ensure(h->lgp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)LC)));
+            TRY(ensure(h->lgp_slot, sizeof(int) * 32 * (size_t)(LK + 1)));
+        }
+    }
+    h->gp_cols = (int)GC; h->gp_max_cols = (int)GMAX; h->gp_max_groups = (int)GI;
+    h->lgp_cols = (int)LC; h->lgp_max_cols = (int)LMAX; h->lgp_max_groups = (int)LI;
+    h->gp_max_nz = mnz;
+    return MSM_OK;
+}
+
 static const Tuned *find_tuned(const msm_handle *h, int64_t n, const CellGeom &g)
 {
     for (const Tuned &t : h->tuned)
@@ -516,12 +573,6 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     std::vector<std::array<int, 4>> tops;          // (nx, ny, nz, table offset)
     int64_t N = 0, M = 0, G = 0, UT = 0, TT = 0, PB = 0, ST = 0;
     int64_t CC = 0, CZ = 0, CK = 0, CI = 0, CMAX = 0;    // cluster pairs: columns, layer tables, clusters of 4
-    int64_t GC = 0, GK = 0, GI = 0, GMAX = 0, LC = 0, LK = 0, LI = 0, LMAX = 0;   // i groups: columns, groups
-    // i groups: columns of cw x cw cells with cw^3 cells holding ~32 atoms at the mean density
-    auto group_width = [](double per_cell) {
-        const int cw = (int)lround(cbrt(32.0 / std::max(per_cell, 1e-3)));
-        return std::min(std::max(cw, 1), 8);
-    };
     bool pending = false;
     h->h_blk.clear();
     for (int s = 0; s < B; s++) {
@@ -596,33 +647,16 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
             CI = std::max(CI, n / 8 + nco);                 // i clusters: at most n/8 + 1 per column
             CMAX = std::max(CMAX, nco);
         }
-        {
-            const int64_t n = (int64_t)S.n, n_lj = (int64_t)(S.n_mol + (S.n - 3 * S.n_mol));
-            D.gp_cw = group_width((double)n / (double)ncells);
-            D.gp_nc[0] = (D.g.nc[0] + D.gp_cw - 1) / D.gp_cw;
-            D.gp_nc[1] = (D.g.nc[1] + D.gp_cw - 1) / D.gp_cw;
-            const int64_t ng = (int64_t)D.gp_nc[0] * D.gp_nc[1];
-            D.gp_col_off = (int)GC;
-            GC += ng;
-            GK += n / 32 + ng;                             // groups: at most n/32 + 1 per column
-            GI = std::max(GI, n / 32 + ng);
-            GMAX = std::max(GMAX, ng);
-            D.lgp_cw = group_width((double)n_lj / (double)ncells);
-            D.lgp_nc[0] = (D.g.nc[0] + D.lgp_cw - 1) / D.lgp_cw;
-            D.lgp_nc[1] = (D.g.nc[1] + D.lgp_cw - 1) / D.lgp_cw;
-            const int64_t nl = (int64_t)D.lgp_nc[0] * D.lgp_nc[1];
-            D.lgp_col_off = (int)LC;
-            LC += nl;
-            LK += n_lj / 32 + nl;
-            LI = std::max(LI, n_lj / 32 + nl);
-            LMAX = std::max(LMAX, nl);
-        }
         const Tuned *t = (h->p.flags & MSM_FLAG_AUTOTUNE) ? find_tuned(h, S.n, D.g) : nullptr;
+        {
+            const int64_t n_lj = (int64_t)(S.n_mol + (S.n - 3 * S.n_mol));
+            D.gp_cw = (t && t->gcw) ? t->gcw : group_width((double)S.n / (double)ncells);
+            D.lgp_cw = (t && t->lgcw) ? t->lgcw : group_width((double)n_lj / (double)ncells);
+        }
         if (t) set_bricks(D, t->bd);
         else {
             set_bricks(D, kBrickShapes[brick_heuristic(S.n, D.g)]);
-            // the brick shapes are timed only where bricks serve the pair passes
-            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && (h->p.flags & MSM_FLAG_BRICKS) && S.n > 0) pending = true;
+            if ((h->p.flags & MSM_FLAG_AUTOTUNE) && S.n > 0) pending = true;
         }
         if (h->p.model == MSM_MODEL_WATER) {
             // LJ pass: the O sites and single sites of the water completion
@@ -666,18 +700,7 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     }
     TRY(ensure(h->bsum, sizeof(int) * (size_t)scan_scratch_ints((int)M)));
     h->gp_on = !(h->p.flags & MSM_FLAG_BRICKS);
-    if (h->gp_on) {
-        TRY(ensure(h->gp_cnt, sizeof(int) * (size_t)(GC + 1)));
-        TRY(ensure(h->gp_col, sizeof(int) * (size_t)(GC + 1)));
-        TRY(ensure(h->gp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)GC)));
-        TRY(ensure(h->gp_slot, sizeof(int) * 32 * (size_t)(GK + 1)));
-        if (h->p.model == MSM_MODEL_WATER) {
-            TRY(ensure(h->lgp_cnt, sizeof(int) * (size_t)(LC + 1)));
-            TRY(ensure(h->lgp_col, sizeof(int) * (size_t)(LC + 1)));
-            TRY(ensure(h->lgp_bsum, sizeof(int) * (size_t)scan_scratch_ints((int)LC)));
-            TRY(ensure(h->lgp_slot, sizeof(int) * 32 * (size_t)(LK + 1)));
-        }
-    }
+    TRY(layout_groups(h, d));
     h->cp_on = (h->p.flags & MSM_FLAG_CLUSTER_PAIRS) && h->precision == MSM_FP32 &&
                h->p.method != MSM_METHOD_WOLF && !(h->p.flags & MSM_FLAG_SCALAR_PAIRS);
     if (h->cp_on) {
@@ -761,10 +784,6 @@ static int set_batch(msm_handle *h, int B, const SysIn *sys, cudaStream_t st)
     h->N = (int)N; h->M = (int)M; h->G = (int)G; h->UT = (int)UT; h->TT = (int)TT; h->PB = (int)PB;
     h->stiles = (int)ST;
     h->cp_cols = (int)CC;
-    h->gp_cols = (int)GC; h->gp_max_cols = (int)GMAX; h->gp_max_groups = (int)GI;
-    h->gp_max_nz = 0;
-    for (const SysDesc &D : h->hsd) h->gp_max_nz = std::max(h->gp_max_nz, D.g.nc[2]);
-    h->lgp_cols = (int)LC; h->lgp_max_cols = (int)LMAX; h->lgp_max_groups = (int)LI;
     h->cp_max_cols = (int)CMAX;
     h->cp_max_icl = (int)CI;
     h->max_n = h->max_mol = h->max_units = h->max_bricks = h->max_atiles = h->max_top = h->max_lj_bricks = 0;
@@ -928,44 +947,110 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
         return MSM_OK;
     };
     const SysDesc &R = h->hsd[(size_t)big];
-    const int h0 = brick_heuristic(R.n, R.g);
-    float best = 1e30f;
-    int best_s = h0;
-    for (int sidx = std::max(0, h0 - 2); sidx <= std::min(kNumShapes - 1, h0 + 2); sidx++) {
-        for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
-        CUDA_TRY(upload());
-        ShortArgs<T> sa = short_args<T>(h);
-        sa.max_bricks = most(false);
-        float ms;
-        TRY(timed(sa, false, &ms));
-        if (ms < best) { best = ms; best_s = sidx; }
-    }
-    for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[best_s]);
-    CUDA_TRY(upload());
-    int best_l = 0;
-    if (model) {
-        // the LJ pass's bricks likewise, on the LJ-site list the evaluation builds next
+    auto build_lj_list = [&]() -> int {
         TRY(launch_lj_count<T>(h->M, h->start.as<int>(), h->aflag.as<int>(), h->lj_count.as<int>(), status, st));
         TRY(launch_scan(h->M, h->lj_count.as<int>(), h->lj_start.as<int>(), h->bsum.as<int>(), status, st));
         TRY(launch_lj_compact<T>(h->M, h->start.as<int>(), h->lj_start.as<int>(), h->apos.as<vec4<T>>(),
                                  h->aflag.as<int>(), h->perm.as<int>(), h->lj_apos.as<vec4<T>>(),
                                  h->lj_flag.as<int>(), h->lj_perm.as<int>(), status, st));
+        return MSM_OK;
+    };
+    auto lj_args = [&]() {
         ShortArgs<T> sl = short_args<T>(h);
         sl.start = h->lj_start.as<int>(); sl.apos = h->lj_apos.as<vec4<T>>(); sl.aflag = h->lj_flag.as<int>();
         sl.perm = h->lj_perm.as<int>();
-        const int l0 = brick_heuristic(R.n_mol + (R.n - 3 * R.n_mol), R.g);
-        float best_lj = 1e30f;
-        best_l = l0;
-        for (int sidx = std::max(0, l0 - 2); sidx <= std::min(kNumShapes - 1, l0 + 2); sidx++) {
-            for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
+        return sl;
+    };
+    if (h->gp_on) {
+        // i groups: the column width of the density heuristic and one narrower and one
+        // wider, each timed with its group build; for the water model likewise the LJ
+        // sites' groups on the LJ-site list
+        auto timed_groups = [&](bool lj, float *ms) -> int {
+            ShortArgs<T> a = lj ? lj_args() : short_args<T>(h);
+            a.gcol = (lj ? h->lgp_col : h->gp_col).template as<int>();
+            a.gslot = (lj ? h->lgp_slot : h->gp_slot).template as<int>();
+            a.max_bricks = lj ? h->lgp_max_groups : h->gp_max_groups;
+            auto run = [&]() -> int {
+                if (lj)
+                    TRY(launch_groups<T>(a.bt, true, h->lgp_max_cols, h->gp_max_nz, h->lgp_cols, a.start, a.apos,
+                                         h->lgp_cnt.as<int>(), h->lgp_col.as<int>(), h->lgp_bsum.as<int>(),
+                                         h->lgp_slot.as<int>(), status, st));
+                else
+                    TRY(launch_groups<T>(a.bt, false, h->gp_max_cols, h->gp_max_nz, h->gp_cols, a.start, a.apos,
+                                         h->gp_cnt.as<int>(), h->gp_col.as<int>(), h->gp_bsum.as<int>(),
+                                         h->gp_slot.as<int>(), status, st));
+                return lj ? launch_short_lj<T>(a, st) : launch_short<T>(a, model, st);
+            };
+            TRY(run());
+            *ms = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                CUDA_TRY(cudaEventRecord(e0, st));
+                TRY(run());
+                CUDA_TRY(cudaEventRecord(e1, st));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float t = 0;
+                CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+                *ms = std::min(*ms, t);
+            }
+            return MSM_OK;
+        };
+        auto tune_width = [&](bool lj) -> int {
+            const SysDesc &Rc = h->hsd[(size_t)big];
+            const int w0 = lj ? Rc.lgp_cw : Rc.gp_cw;
+            float best = 1e30f;
+            int best_w = w0;
+            for (int w = std::max(1, w0 - 1); w <= std::min(8, w0 + 1); w++) {
+                for (int b : todo) (lj ? h->hsd[(size_t)b].lgp_cw : h->hsd[(size_t)b].gp_cw) = w;
+                TRY(layout_groups(h, h->hsd));
+                CUDA_TRY(upload());
+                float ms;
+                TRY(timed_groups(lj, &ms));
+                if (ms < best) { best = ms; best_w = w; }
+            }
+            for (int b : todo) (lj ? h->hsd[(size_t)b].lgp_cw : h->hsd[(size_t)b].gp_cw) = best_w;
+            TRY(layout_groups(h, h->hsd));
             CUDA_TRY(upload());
-            sl.max_bricks = most(true);
-            float ms;
-            TRY(timed(sl, true, &ms));
-            if (ms < best_lj) { best_lj = ms; best_l = sidx; }
+            return MSM_OK;
+        };
+        TRY(tune_width(false));
+        if (model) {
+            TRY(build_lj_list());
+            TRY(tune_width(true));
         }
-        for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[best_l]);
+    } else {
+        const int h0 = brick_heuristic(R.n, R.g);
+        float best = 1e30f;
+        int best_s = h0;
+        for (int sidx = std::max(0, h0 - 2); sidx <= std::min(kNumShapes - 1, h0 + 2); sidx++) {
+            for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
+            CUDA_TRY(upload());
+            ShortArgs<T> sa = short_args<T>(h);
+            sa.max_bricks = most(false);
+            float ms;
+            TRY(timed(sa, false, &ms));
+            if (ms < best) { best = ms; best_s = sidx; }
+        }
+        for (int b : todo) set_bricks(h->hsd[(size_t)b], kBrickShapes[best_s]);
         CUDA_TRY(upload());
+        int best_l = 0;
+        if (model) {
+            // the LJ pass's bricks likewise, on the LJ-site list the evaluation builds next
+            TRY(build_lj_list());
+            ShortArgs<T> sl = lj_args();
+            const int l0 = brick_heuristic(R.n_mol + (R.n - 3 * R.n_mol), R.g);
+            float best_lj = 1e30f;
+            best_l = l0;
+            for (int sidx = std::max(0, l0 - 2); sidx <= std::min(kNumShapes - 1, l0 + 2); sidx++) {
+                for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[sidx]);
+                CUDA_TRY(upload());
+                sl.max_bricks = most(true);
+                float ms;
+                TRY(timed(sl, true, &ms));
+                if (ms < best_lj) { best_lj = ms; best_l = sidx; }
+            }
+            for (int b : todo) set_lj_bricks(h->hsd[(size_t)b], kBrickShapes[best_l]);
+            CUDA_TRY(upload());
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -979,6 +1064,8 @@ static int autotune_bricks(msm_handle *h, cudaStream_t st)
             t.bd[k] = D.bd[k];
             t.lj_bd[k] = model ? D.lj_bd[k] : 0;
         }
+        t.gcw = h->gp_on ? D.gp_cw : 0;
+        t.lgcw = (h->gp_on && model) ? D.lgp_cw : 0;
         h->tuned.push_back(t);
     }
     h->max_bricks = most(false);

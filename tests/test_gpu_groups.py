@@ -99,3 +99,18 @@ def test_groups_and_bricks_give_the_same_bits_at_full_size(api, torch):
         del m
     assert out[0][0] == out[1][0]
     assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotuned_group_widths_change_no_result(api, torch, prec):
+    """The autotuner times the group column widths around the density heuristic on the
+    first evaluation of a geometry (Coulomb and LJ passes); whichever it keeps, the
+    results are the untuned ones, on that evaluation and on the next."""
+    s = inputs.water_box(3000, 3.1, margin=0.6, seed=74, vel_seed=75)
+    res = {}
+    for tune in (False, True):
+        m = api.MSM(a=A, h=H, levels=3, precision=prec, model="water", autotune=tune)
+        res[tune] = [m.system_forces(_sys(torch, s)) for _ in range(2)]
+    for k in range(2):
+        assert float(res[True][k][0]) == float(res[False][k][0])
+        assert torch.equal(res[True][k][1], res[False][k][1]) and torch.equal(res[True][k][2], res[False][k][2])
