@@ -512,10 +512,14 @@ __global__ void __launch_bounds__(128) k_grp_fill(const Batch bt, const int *__r
         int n = 0;
         for (int cy = cy0; cy < cy1; cy++) {
             const int rb = (cz * ny + cy) * nx;
-            for (int s = st[rb + cx0]; s < st[rb + cx1]; s++, n++) {
-                skey[w][n][lane] = (float)apos[s].z;
-                sslot[w][n][lane] = s;
+            const int s0 = st[rb + cx0], s1 = st[rb + cx1];
+            // four position loads in flight at a time
+#pragma unroll 4
+            for (int s = s0; s < s1; s++) {
+                skey[w][n + (s - s0)][lane] = (float)apos[s].z;
+                sslot[w][n + (s - s0)][lane] = s;
             }
+            n += s1 - s0;
         }
         // insertion by (z, slot): slots were loaded in ascending order, so ties stay in order
         for (int e = 1; e < n; e++) {
