@@ -43,13 +43,19 @@ def _sys(torch, s, vel=False):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("case", ["water3k", "cloud_ragged", "cloud_flat", "cloud_one_column", "dense_small"])
+@pytest.mark.parametrize("case", ["water3k", "cloud_ragged", "cloud_flat", "cloud_one_column", "dense_small",
+                                  "dense_layers", "sparse"])
 def test_groups_and_bricks_give_the_same_short_range_bits(api, torch, prec, case):
+    """Besides water and ragged clouds: a cloud dense enough that some cell layers of a
+    column hold more atoms than a lane sorts by z (they keep the cell order), and a
+    sparse box whose column width reaches its upper bound of 8 cells."""
     s = {"water3k": lambda: inputs.water_box(3000, 3.1, margin=0.5, with_velocities=False),
          "cloud_ragged": lambda: inputs.random_cloud(5003, (2.7, 3.3, 1.9), seed=8, margin=0.0),
          "cloud_flat": lambda: inputs.random_cloud(900, (5.0, 4.0, 0.2), seed=10, margin=0.0),
          "cloud_one_column": lambda: inputs.random_cloud(700, (0.4, 0.45, 6.0), seed=9, margin=0.0),
-         "dense_small": lambda: inputs.random_cloud(400, (0.9, 0.8, 0.7), seed=11, margin=0.0)}[case]()
+         "dense_small": lambda: inputs.random_cloud(400, (0.9, 0.8, 0.7), seed=11, margin=0.0),
+         "dense_layers": lambda: inputs.random_cloud(6000, (1.5, 1.5, 1.5), seed=12, margin=0.0),
+         "sparse": lambda: inputs.random_cloud(150, (6.0, 6.0, 6.0), seed=13, margin=0.0)}[case]()
     out = []
     for bricks in (False, True):
         m = api.MSM(a=A, h=H, levels=3, precision=prec, bricks=bricks)
