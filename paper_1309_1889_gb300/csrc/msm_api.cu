@@ -1173,8 +1173,9 @@ static int evaluate_t(msm_handle *h, const EvalIO &io, cudaStream_t st)
 
     // step 1: short range
     ShortArgs<T> s = short_args<T>(h);
-    if (h->gp_on) {
-        // i groups of the Coulomb pass (after the binning: they read the cell starts)
+    if (h->gp_on && !(sizeof(T) == sizeof(float) && h->cp_on)) {
+        // i groups of the Coulomb pass (after the binning: they read the cell starts; the
+        // cluster-pair pass, when on, replaces it)
         TRY(launch_groups<T>(s.bt, false, h->gp_max_cols, h->gp_max_nz, h->gp_cols, s.start, s.apos,
                              h->gp_cnt.as<int>(), h->gp_col.as<int>(), h->gp_bsum.as<int>(), h->gp_slot.as<int>(),
                              s.status, st));
