@@ -363,3 +363,24 @@ def test_water_model_fp32_energy_relaxed_full_size(api, torch):
     print(f"relaxed: U64 {e64:.6f}, |dU| {abs(e32 - e64):.4f} kJ/mol = {abs(e32 - e64) / abs(e64):.2e} of |U|")
     assert abs(e32 - e64) <= 1e-6 * abs(e64)
     check_atoms(f32, p32, f64, p64, TOL["fp32"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_repeats_are_bitwise_identical(api, torch, prec):
+    """1,000,000 atoms, 5 levels: two evaluations give the same bits, the lattice-cutoff
+    grids of levels 0..3 included.  The lattice cutoff splits each tile's input planes
+    between two blocks that add their partial sums into the zeroed output with atomic
+    adds (hundreds of tiles in flight); two addends onto zero commute, so the order in
+    which they land cannot show."""
+    cfg = inputs.WORKLOADS["water1M"]
+    s = inputs.water_box(cfg["n_atoms"], cfg["region"], margin=0.5, with_velocities=False)
+    pos, q = _dev(torch, s.pos), _dev(torch, s.q)
+    m = api.MSM(a=A, h=H, levels=cfg["levels"], precision=prec)
+    runs = []
+    for _ in range(2):
+        e, f, p = m.energy_forces(pos, q, s.box)
+        runs.append((float(e), f.clone(), p.clone(), [m.stage_grid(k, "ucut") for k in range(cfg["levels"] - 1)]))
+    assert runs[0][0] == runs[1][0]
+    assert torch.equal(runs[0][1], runs[1][1]) and torch.equal(runs[0][2], runs[1][2])
+    for g0, g1 in zip(runs[0][3], runs[1][3]):
+        assert np.array_equal(g0, g1)
