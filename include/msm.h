@@ -89,9 +89,10 @@ extern "C" {
 #define MSM_FLAG_CLUSTER_PAIRS 8  /* FP32, MSM or simple cutoff: the short-range Coulomb pass
                                 on cluster pairs (8 i atoms x 4 j atoms from columns of
                                 2 x 2 cells, clusters culled by bounding box) instead of
-                                cell bricks; the same sums in another order: agrees with
-                                the brick pass to rounding, not bitwise; ignored for FP64,
-                                Wolf summation and MSM_FLAG_SCALAR_PAIRS                    */
+                                32-atom groups; the same sums in another order: agrees
+                                with the default pass to rounding, not bitwise; ignored
+                                for FP64, Wolf summation and MSM_FLAG_SCALAR_PAIRS (off by
+                                default: measured no faster)                               */
 #define MSM_FLAG_BRICKS 16  /* diagnostic: the short-range and LJ passes give each warp a brick
                                 of cells (~20 atoms) instead of a group of 32 atoms cut from a
                                 column of cells; the same bits, slower (off by default)      */

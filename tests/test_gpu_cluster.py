@@ -2,7 +2,7 @@
 against the FP64 oracle (Sec. 3, step 1: the g* sum over pairs within a), and its
 own invariants, through the C ABI.
 
-Bars as for the brick pass in test_gpu_msm.py: relative RMS <= 1e-4 for the
+Bars as for the default pass in test_gpu_msm.py: relative RMS <= 1e-4 for the
 short-range potentials and forces, each atom within 2e-3 of the RMS magnitude,
 whole-MSM energy within 1e-6 |U|.  Batching, repetition and graph replay are
 bitwise.
@@ -135,8 +135,8 @@ def test_cluster_simple_cutoff_matches_oracle(api, torch):
     assert rel_rms(f, ref["forces"]) <= TOL["f"] and max_rel(f, ref["forces"]) <= TOL["fmax"]
 
 
-def test_cluster_and_brick_passes_agree_to_rounding(api, torch):
-    """The two layouts sum the same terms in different orders."""
+def test_cluster_and_default_passes_agree_to_rounding(api, torch):
+    """The cluster pairs and the default 32-atom groups sum the same terms in different orders."""
     s = inputs.water_box(3000, 3.1, margin=0.5, with_velocities=False)
     out = []
     for cp in (False, True):
@@ -198,3 +198,17 @@ def test_cluster_full_size_rows_match_oracle(api, torch):
     assert abs(float(e32) - float(e64)) <= 1e-6 * abs(float(e64))
     f32, f64 = f32.cpu().numpy(), f64.cpu().numpy()
     assert rel_rms(f32, f64) <= 1e-4 and max_rel(f32, f64) <= TOL["fmax"]
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp64"), dict(precision="fp32", method="wolf", wolf_alpha=2.0),
+                                dict(precision="fp32", scalar_pairs=True)])
+def test_cluster_flag_is_ignored_where_documented(api, torch, kw):
+    """FP64, Wolf summation and the scalar pair loop keep the default pass: the flag
+    changes no bit there."""
+    s = inputs.water_box(1500, 2.5, margin=0.5, with_velocities=False)
+    out = []
+    for cp in (False, True):
+        m = api.MSM(a=A, h=H, levels=3, cluster_pairs=cp, **kw)
+        out.append(m.energy_forces(_dev(torch, s.pos), _dev(torch, s.q), s.box))
+    assert float(out[0][0]) == float(out[1][0])
+    assert torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][2], out[1][2])
