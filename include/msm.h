@@ -113,12 +113,13 @@ extern "C" {
  *              keeps atoms inside the open domain; an atom closer than
  *              wall_width to a box face feels 1/2 wall_k (wall_width - d)^2
  *              (kJ/mol/nm^2, nm; wall_k = 0 disables it)
- *   flags      MSM_FLAG_* bits (default: GRAPHS | AUTOTUNE).  None changes a
- *              result bit: a graph replays exactly the launches of an eager
- *              step, the short-range sum adds each atom's neighbours in
- *              ascending sorted order whatever the brick shape, and the packed
- *              and scalar pair steps do the same IEEE operations.  Graphs are
- *              not used while the profiler is on.
+ *   flags      MSM_FLAG_* bits (default: GRAPHS | AUTOTUNE).  None but
+ *              CLUSTER_PAIRS changes a result bit: a graph replays exactly the
+ *              launches of an eager step, the short-range sum adds each atom's
+ *              neighbours in ascending sorted order whatever the i grouping
+ *              (32-atom groups of any column width, or bricks of any shape),
+ *              and the packed and scalar pair steps do the same IEEE
+ *              operations.  Graphs are not used while the profiler is on.
  *   list_skin  md_run only: Verlet-list skin (nm) of the short-range sum;
  *              lists hold pairs within a + list_skin and are rebuilt when an
  *              atom has moved more than list_skin/2 (0 = cell search every
